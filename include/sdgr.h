@@ -1,0 +1,240 @@
+/*
+ * sdgr.h -- C ABI of the B300 (sm_103a) SAR Differentiable Gaussian
+ * Rasterizer (SDGR) of SAR-GS (arXiv 2506.21633).
+ *
+ * Problem statement (Section II, Fig. "SARGSflow"): scene Gaussians plus
+ * radar geometry (azimuth angle, grazing angle, range / azimuth resolution)
+ * in; SAR intensity images and the gradients of an image loss with respect
+ * to every Gaussian parameter out.
+ *
+ * Conventions shared by every call
+ *  - Pointers named "device" are CUDA device pointers on the current device;
+ *    pointers named "host" are host memory.  The library never allocates
+ *    device memory: the caller allocates every device buffer, including the
+ *    workspace of sdgr_workspace_size() bytes, and owns it.  Host memory the
+ *    library needs for its own bookkeeping is allocated in sdgr_ws_create()
+ *    and freed in sdgr_ws_destroy().
+ *  - Every compute call enqueues work on `stream` (a cudaStream_t; NULL =
+ *    the legacy default stream) and returns without waiting for it.  No
+ *    compute call synchronises the host, so a sequence of them can be
+ *    captured into a CUDA graph.
+ *  - Return codes report host-side validation and launch errors.  Conditions
+ *    only the device can see (instance capacity exceeded) are written to the
+ *    workspace's status word and read back with sdgr_read_status() once the
+ *    stream has finished.  No call aborts, traps or prints.
+ *  - Gaussian parameters, float32, row-major [N][12] (three float4 per
+ *    Gaussian, 16-byte aligned):
+ *        { mu_x, mu_y, mu_z, opacity_logit },
+ *        { log_s_x, log_s_y, log_s_z, P },
+ *        { q_w, q_x, q_y, q_z }
+ *    mu = mean (world metres), s = exp(log_s) the axis scales, q an
+ *    unnormalised rotation quaternion (Sigma = R(q/|q|) diag(s^2) R^T,
+ *    eq. G(x)), opacity o = sigmoid(opacity_logit) standing for the two-way
+ *    extinction 1 - E+ E- of eq. I_i, P the scattering coefficient.
+ *    Gradients use the same layout.
+ *  - Images: float32, one NR x NA block per view, views concatenated in view
+ *    order; row = slant-range bin (near range first), column = azimuth bin;
+ *    pixel (m, n) has its centre at pixel coordinates (m, n).
+ */
+#ifndef SDGR_H
+#define SDGR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SDGR_OK = 0,
+    SDGR_ERR_INVALID = 1,  /* an argument failed host-side validation */
+    SDGR_ERR_CUDA = 2,     /* a CUDA runtime call or launch failed */
+    SDGR_ERR_CAPACITY = 3, /* instance capacity exceeded (device status) */
+    SDGR_ERR_TIMEOUT = 4,  /* a bounded device wait gave up (device status) */
+    SDGR_ERR_STATE = 5     /* calls made out of order on a workspace */
+} sdgr_status;
+
+/* One radar view (Section II-A-1, eqs. W and R_r).
+ * phi   radar azimuth angle (rad); theta grazing angle (rad), 0 < theta < pi/2
+ * dA    azimuth pixel size (m) > 0;  dR slant-range pixel size (m) > 0
+ * NA    image columns (azimuth) > 0; NR image rows (slant range) > 0
+ * scene index of the scene (a contiguous range of Gaussians) this view sees
+ * center the world point the beam is centred on (m); it maps to the image
+ *        centre, pixel coordinates (NA/2 - 1/2, NR/2 - 1/2). */
+typedef struct {
+    double phi, theta;
+    double dA, dR;
+    int32_t NA, NR;
+    int32_t scene, reserved;
+    double center[3];
+} sdgr_view;
+
+/* Renderer options (readings of passages the paper leaves open).
+ * cutoff_K      contributions with Mahalanobis distance > K are zero on both
+ *               planes (default 5)
+ * dilation_eps  added to both 2D covariances, px^2 (default 0.3)
+ * T_min         a ray stops once its transmittance drops below T_min
+ *               (default 0: never; values below 2^-100 act as 2^-100, where
+ *               the remaining contributions are below float32 resolution)
+ * norm_mode     0: beta = exp(-delta/2) / (2 pi sqrt(det Sigma'_I)), so a
+ *               Gaussian deposits its intensity in the image (default);
+ *               1: beta = exp(-delta/2) (peak-normalised) */
+typedef struct {
+    float cutoff_K;
+    float dilation_eps;
+    float T_min;
+    int32_t norm_mode;
+} sdgr_cfg;
+
+/* Workspace capacities.  A workspace created for these capacities accepts
+ * any call whose totals do not exceed them.
+ * max_views       number of views per call
+ * max_scenes      number of scenes per call
+ * max_gaussians   total Gaussians over all scenes
+ * max_view_gauss  sum over views of the Gaussian count of the view's scene
+ * max_pixels      sum over views of NA * NR
+ * max_tiles       sum over views of ceil(NA/16) * ceil(NR/16)
+ * max_instances   (tile, Gaussian) pairs over both planes of all views */
+typedef struct {
+    int32_t max_views;
+    int32_t max_scenes;
+    int64_t max_gaussians;
+    int64_t max_view_gauss;
+    int64_t max_pixels;
+    int64_t max_tiles;
+    int64_t max_instances;
+} sdgr_caps;
+
+/* Opaque workspace handle: host-side plan plus the caller's device buffer. */
+typedef struct sdgr_ws sdgr_ws;
+
+/* Capacities that exactly fit one call (host only, no CUDA call).
+ * scene_offsets: host, n_scenes + 1 increasing entries; scene s owns
+ * Gaussians [scene_offsets[s], scene_offsets[s+1]).  instances: the
+ * max_instances to reserve (>= 0; see sdgr_read_status for the exact need).
+ * Returns SDGR_ERR_INVALID on a malformed view or scene table. */
+sdgr_status sdgr_caps_for(const sdgr_view *views, int32_t V, const int64_t *scene_offsets, int32_t n_scenes,
+                          int64_t instances, sdgr_caps *out);
+
+/* Device bytes a workspace of these capacities needs (host only).  Returns
+ * SDGR_ERR_INVALID for negative or overflowing capacities. */
+sdgr_status sdgr_workspace_size(const sdgr_cfg *cfg, const sdgr_caps *caps, size_t *bytes);
+
+/* Binds a caller-allocated device buffer (256-byte aligned, at least
+ * sdgr_workspace_size() bytes) to a new workspace handle.  The buffer must
+ * stay allocated until sdgr_ws_destroy(); one workspace serves one stream at
+ * a time.  Queries the current device's attributes (no allocation).
+ * Errors: SDGR_ERR_INVALID (NULL, misaligned or too small buffer, bad cfg). */
+sdgr_status sdgr_ws_create(sdgr_ws **out, void *device_buffer, size_t bytes, const sdgr_cfg *cfg,
+                           const sdgr_caps *caps);
+sdgr_status sdgr_ws_destroy(sdgr_ws *ws);
+
+/* Step a1-a5: Mapping and Projection Algorithm (Section II-A-1: eqs. G(x),
+ * W, R_r, Sigmaprime, x_r, x_C, x_i).  For every (view, Gaussian of the
+ * view's scene): activations, 3D covariance, world->radar transform,
+ * computation-plane and imaging-plane centre and conic, imaging
+ * normaliser, float32 slant-range depth key, and the 16x16-tile rectangles
+ * the K-ellipse touches on each plane.
+ * params: device [max_gaussians][12] float32 (layout above); it must stay
+ *   unchanged until sdgr_render_bwd() of this step has run.
+ * scene_offsets: host [n_scenes + 1]; views: host [V].
+ * Errors: SDGR_ERR_INVALID on bad views / scenes / capacities exceeded. */
+sdgr_status sdgr_preprocess(sdgr_ws *ws, const float *params, const int64_t *scene_offsets, int32_t n_scenes,
+                            const sdgr_view *views, int32_t V, void *stream);
+
+/* Step a6: bins and sorts.  Per view, a stable radix sort of the depth keys
+ * (ties by Gaussian index, the depth-indexed lists of Section II-A); then
+ * the (plane, view, tile) instances are emitted in depth order and radix
+ * sorted by tile, which keeps depth order within each computation-plane
+ * tile; per-tile [start, end) ranges.  If the instances exceed
+ * max_instances the status word gets SDGR_ERR_CAPACITY and the required
+ * count, and the later kernels of the step skip their work.
+ * Errors: SDGR_ERR_STATE if sdgr_preprocess() has not run. */
+sdgr_status sdgr_bin_sort(sdgr_ws *ws, void *stream);
+
+/* Steps a7-a8: the scattering-intensity pass on the computation plane
+ * (Section II-A-2, eq. I_i: rays from the cell centres, front-to-back
+ * compositing with two-way attenuation) and the imaging splat on the
+ * range-azimuth plane (Section II-A-3, eq. S_{n,m}: the layover sum).
+ * images: device, sum over views of NR*NA float32, overwritten.
+ * intensity: device [max_view_gauss] float32 or NULL; if given, receives
+ *   I_i per (view, Gaussian) in view order (view v's block starts at the sum
+ *   of the earlier views' scene sizes).
+ * Errors: SDGR_ERR_STATE if sdgr_bin_sort() has not run. */
+sdgr_status sdgr_render_fwd(sdgr_ws *ws, float *images, float *intensity, void *stream);
+
+/* Steps a10-a12: adjoint of the imaging splat (Section II-B-1), of the
+ * intensity pass (Section II-B-2; per-ray transmittance is recomputed back
+ * to front, not stored per pair) and of the projections (Section II-B-3),
+ * summed over the views of each scene.
+ * dL_dimages: device, laid out like `images`.
+ * grads: device [max_gaussians][12] float32, 16-byte aligned.  accumulate =
+ *   0: overwritten for every Gaussian of every scene listed in the last
+ *   sdgr_preprocess() call (zero for scenes without views); accumulate = 1:
+ *   the gradient is added to what grads holds (e.g. views rendered in
+ *   separate calls).
+ * Errors: SDGR_ERR_STATE if sdgr_render_fwd() has not run on this workspace
+ * since the last sdgr_preprocess(). */
+sdgr_status sdgr_render_bwd(sdgr_ws *ws, const float *dL_dimages, float *grads, int32_t accumulate, void *stream);
+
+/* Step a13: one Adam step (Kingma & Ba; bias-corrected, eps added to the
+ * square root of the corrected second moment, torch.optim.Adam semantics,
+ * no weight decay) over N Gaussians.  params, grads, m, v: device
+ * [N][12] float32, 16-byte aligned; params, m, v updated in place.  lr: host
+ * [5] learning rates for the groups {means, log-scales, quaternions,
+ * opacity logit, P}.  step: 1-based step count.
+ * Errors: SDGR_ERR_INVALID (N < 0, step < 1, misaligned pointers). */
+sdgr_status sdgr_adam_step(float *params, const float *grads, float *m, float *v, int64_t N, const float *lr,
+                           float b1, float b2, float eps, int32_t step, void *stream);
+
+/* Step a9: L1 loss, mean over npix pixels, and dL/dS = sign(S - S*)/npix
+ * (sign(0) = 0).  images, targets, dL_dimages: device [npix] float32; loss:
+ * device float32 scalar, overwritten.  Errors: SDGR_ERR_INVALID. */
+sdgr_status sdgr_l1_loss(const float *images, const float *targets, int64_t npix, float *dL_dimages, float *loss,
+                         void *stream);
+
+/* Reads the workspace's device status word (a synchronous device-to-host
+ * copy: call after the stream has finished).  Returns SDGR_OK or the device
+ * status (SDGR_ERR_CAPACITY / SDGR_ERR_TIMEOUT); *required_instances (may be
+ * NULL) receives the instance count the last sdgr_bin_sort() needed. */
+sdgr_status sdgr_read_status(sdgr_ws *ws, int64_t *required_instances);
+
+/* Stage timing.  With profiling enabled, the workspace brackets each
+ * kernel stage of sdgr_preprocess / sdgr_bin_sort / sdgr_render_fwd /
+ * sdgr_render_bwd with CUDA events recorded on the launching stream (the
+ * events are created by sdgr_profile_enable; no device memory is
+ * allocated).  sdgr_profile_read waits for the recorded events, and adds
+ * up, per stage, the elapsed milliseconds and the number of launches since
+ * the last reset.  ms and launches: host arrays of SDGR_NUM_STAGES entries.
+ * Errors: SDGR_ERR_INVALID (NULL ws / arrays), SDGR_ERR_CUDA. */
+enum {
+    SDGR_STAGE_PREPROCESS = 0,   /* step a1-a5 */
+    SDGR_STAGE_DEPTH_SORT = 1,   /* step a6: per-view depth radix sort */
+    SDGR_STAGE_BIN = 2,          /* step a6: counts, emission, tile sort, ranges */
+    SDGR_STAGE_INTENSITY_FWD = 3,/* step a7 */
+    SDGR_STAGE_SPLAT_FWD = 4,    /* step a8 */
+    SDGR_STAGE_SPLAT_BWD = 5,    /* step a10 */
+    SDGR_STAGE_INTENSITY_BWD = 6,/* step a11 */
+    SDGR_STAGE_PARAM_BWD = 7,    /* step a12 */
+    SDGR_NUM_STAGES = 8
+};
+sdgr_status sdgr_profile_enable(sdgr_ws *ws, int32_t enable);
+sdgr_status sdgr_profile_read(sdgr_ws *ws, double *ms, int64_t *launches, int32_t reset);
+
+/* Diagnostics.  sdgr_count_pairs counts, for the current sorted lists, the
+ * (pixel, Gaussian) pairs inside the cutoff ellipse on the computation plane
+ * (pairs[0]) and on the imaging plane (pairs[1]); it is synchronous (waits
+ * for `stream`).  sdgr_launch_count returns the number of kernels the
+ * library has launched in this process. */
+sdgr_status sdgr_count_pairs(sdgr_ws *ws, int64_t *pairs, void *stream);
+int64_t sdgr_launch_count(void);
+
+/* Static, NUL-terminated description of a status code. */
+const char *sdgr_status_string(sdgr_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SDGR_H */

@@ -73,6 +73,9 @@ def lib():
                                ctypes.c_double, ctypes.c_int32]
         L.orc_l1.argtypes = [dp, dp, ctypes.c_int64, dp]
         L.orc_l1.restype = ctypes.c_double
+        L.orc_step.argtypes = [dp, ctypes.c_int32, ctypes.POINTER(OrcView), ctypes.c_int32,
+                               ctypes.POINTER(OrcCfg), ctypes.c_int32, dp, dp, dp]
+        L.orc_step.restype = ctypes.c_double
         L.orc_set_threads.argtypes = [ctypes.c_int]
         L.orc_set_threads.restype = ctypes.c_int
         _lib = L
@@ -145,6 +148,21 @@ def grad(params, views, dLdS, c=None, culled=False):
     if rc:
         raise ValueError("oracle: invalid arguments")
     return out[:N], dI[:, :N]
+
+
+def step(params, views, targets, c=None, culled=True):
+    """Forward, L1 against targets, adjoint.  Returns (loss, images list,
+    grads [N,12])."""
+    c = c or cfg()
+    p = _params(params)
+    N, V = p.shape[0], len(views)
+    t = np.ascontiguousarray(np.concatenate([np.asarray(x, dtype=np.float64).ravel() for x in targets]))
+    img = np.zeros(t.size)
+    out = np.zeros((max(N, 1), 12))
+    loss = lib().orc_step(_dp(p), N, _views(views), V, ctypes.byref(c), int(culled), _dp(t), _dp(img), _dp(out))
+    if loss != loss:
+        raise ValueError("oracle: invalid arguments")
+    return loss, split_images(img, views), out[:N]
 
 
 PROJ_FIELDS = ["uCx", "uCy", "SCxx", "SCxy", "SCyy", "uIx", "uIy", "SIxx", "SIxy", "SIyy",

@@ -245,43 +245,71 @@ static void depth_order(const orc_gauss *g, int N, int *order) {
     qsort(order, (size_t)N, sizeof(int), cmp_depth);
 }
 
-/* Per-row candidate lists: the Gaussians (in the given order) that may reach
- * row n on plane pl.  Brute-force mode lists every Gaussian on every row. */
+/* Candidate lists for the brute-force loops.  Brute-force mode: every pixel
+ * visits every Gaussian (in the given order).  Culled mode: the image is cut
+ * into 8x8-pixel cells and each cell lists, in the given order, the
+ * Gaussians whose K-ellipse bounding box reaches it; a pixel then visits its
+ * cell's list and skips the Gaussians whose box misses the pixel.  Every
+ * skipped pair has delta > K^2, so both modes add the same terms in the same
+ * order. */
+#define ORC_CELL 8
 typedef struct {
-    int64_t *start; /* NR + 1 */
+    int culled;
+    int N;
+    int cx; /* cells per row */
+    int64_t *start;
     int *idx;
-} row_lists;
+} cand_lists;
 
-static void build_rows(const orc_gauss *g, int N, const int *order, int NR, int pl, int culled, row_lists *rl) {
-    int n, k;
-    rl->start = (int64_t *)calloc((size_t)NR + 1, sizeof(int64_t));
+static void build_cands(const orc_gauss *g, int N, const int *order, const orc_view *v, int pl, int culled,
+                        cand_lists *cl) {
+    int k;
+    cl->culled = culled;
+    cl->N = N;
+    cl->cx = (v->NA + ORC_CELL - 1) / ORC_CELL;
     if (!culled) {
-        rl->idx = (int *)malloc(sizeof(int) * (size_t)(N > 0 ? N : 1));
-        for (k = 0; k < N; ++k) rl->idx[k] = order[k];
-        for (n = 0; n <= NR; ++n) rl->start[n] = 0; /* every row shares the one list */
+        cl->start = NULL;
+        cl->idx = (int *)malloc(sizeof(int) * (size_t)(N > 0 ? N : 1));
+        for (k = 0; k < N; ++k) cl->idx[k] = order[k];
         return;
     }
+    int cy = (v->NR + ORC_CELL - 1) / ORC_CELL;
+    int64_t ncell = (int64_t)cl->cx * cy, c;
+    cl->start = (int64_t *)calloc((size_t)ncell + 1, sizeof(int64_t));
     for (k = 0; k < N; ++k) {
         const orc_gauss *q = &g[order[k]];
-        for (n = q->bb[pl][2]; n <= q->bb[pl][3]; ++n) rl->start[n + 1]++;
+        if (q->bb[pl][0] > q->bb[pl][1] || q->bb[pl][2] > q->bb[pl][3]) continue;
+        int a, b;
+        for (b = q->bb[pl][2] / ORC_CELL; b <= q->bb[pl][3] / ORC_CELL; ++b)
+            for (a = q->bb[pl][0] / ORC_CELL; a <= q->bb[pl][1] / ORC_CELL; ++a) cl->start[(int64_t)b * cl->cx + a + 1]++;
     }
-    for (n = 0; n < NR; ++n) rl->start[n + 1] += rl->start[n];
-    int64_t *fill = (int64_t *)malloc(sizeof(int64_t) * (size_t)NR);
-    for (n = 0; n < NR; ++n) fill[n] = rl->start[n];
-    rl->idx = (int *)malloc(sizeof(int) * (size_t)(rl->start[NR] > 0 ? rl->start[NR] : 1));
+    for (c = 0; c < ncell; ++c) cl->start[c + 1] += cl->start[c];
+    int64_t *fill = (int64_t *)malloc(sizeof(int64_t) * (size_t)(ncell > 0 ? ncell : 1));
+    for (c = 0; c < ncell; ++c) fill[c] = cl->start[c];
+    cl->idx = (int *)malloc(sizeof(int) * (size_t)(cl->start[ncell] > 0 ? cl->start[ncell] : 1));
     for (k = 0; k < N; ++k) {
         const orc_gauss *q = &g[order[k]];
-        for (n = q->bb[pl][2]; n <= q->bb[pl][3]; ++n) rl->idx[fill[n]++] = order[k];
+        if (q->bb[pl][0] > q->bb[pl][1] || q->bb[pl][2] > q->bb[pl][3]) continue;
+        int a, b;
+        for (b = q->bb[pl][2] / ORC_CELL; b <= q->bb[pl][3] / ORC_CELL; ++b)
+            for (a = q->bb[pl][0] / ORC_CELL; a <= q->bb[pl][1] / ORC_CELL; ++a)
+                cl->idx[fill[(int64_t)b * cl->cx + a]++] = order[k];
     }
     free(fill);
 }
 
-static void row_range(const row_lists *rl, int culled, int N, int n, int64_t *b, int64_t *e) {
-    if (!culled) { *b = 0; *e = N; }
-    else { *b = rl->start[n]; *e = rl->start[n + 1]; }
+static void cand_range(const cand_lists *cl, int m, int n, int64_t *b, int64_t *e) {
+    if (!cl->culled) { *b = 0; *e = cl->N; return; }
+    int64_t c = (int64_t)(n / ORC_CELL) * cl->cx + m / ORC_CELL;
+    *b = cl->start[c];
+    *e = cl->start[c + 1];
 }
 
-static void free_rows(row_lists *rl) { free(rl->start); free(rl->idx); }
+static int outside_box(const orc_gauss *q, int pl, int m, int n) {
+    return m < q->bb[pl][0] || m > q->bb[pl][1] || n < q->bb[pl][2] || n > q->bb[pl][3];
+}
+
+static void free_cands(cand_lists *cl) { free(cl->start); free(cl->idx); }
 
 /* Section II-A-2: scattering intensities.  For every ray (cell centre (m, n))
  * of the computation plane the Gaussians are visited front to back; the ray
@@ -292,22 +320,21 @@ static void intensity_pass(const orc_gauss *g, int N, const int *order, const or
     int nt = n_threads();
     double K2 = cutoff2(cfg);
     double *part = (double *)calloc((size_t)nt * (size_t)(N > 0 ? N : 1), sizeof(double));
-    row_lists rl;
-    build_rows(g, N, order, v->NR, 0, culled, &rl);
+    cand_lists cl;
+    build_cands(g, N, order, v, 0, culled, &cl);
     int n;
 #pragma omp parallel for schedule(static)
     for (n = 0; n < v->NR; ++n) {
         double *Ap = part + (size_t)thread_id() * (size_t)N;
-        int64_t b, e;
-        row_range(&rl, culled, N, n, &b, &e);
         int m;
         for (m = 0; m < v->NA; ++m) {
             double T = 1.0;
-            int64_t k;
+            int64_t k, b, e;
+            cand_range(&cl, m, n, &b, &e);
             for (k = b; k < e; ++k) {
-                int i = rl.idx[k];
+                int i = cl.idx[k];
                 const orc_gauss *q = &g[i];
-                if (culled && (m < q->bb[0][0] || m > q->bb[0][1])) continue;
+                if (culled && outside_box(q, 0, m, n)) continue;
                 double dx = m - q->u[0][0], dy = n - q->u[0][1];
                 double delta = mahal(q->C2[0], dx, dy);
                 if (delta > K2) continue;
@@ -324,7 +351,7 @@ static void intensity_pass(const orc_gauss *g, int N, const int *order, const or
     for (t = 0; t < nt; ++t)
         for (i = 0; i < N; ++i) A[i] += part[(size_t)t * N + i];
     free(part);
-    free_rows(&rl);
+    free_cands(&cl);
 }
 
 /* Section II-A-3: imaging.  S_{n,m} = sum_i beta_i^{n,m} I_i (order-free). */
@@ -334,20 +361,19 @@ static void imaging_pass(const orc_gauss *g, int N, const double *I, const orc_v
     int *ident = (int *)malloc(sizeof(int) * (size_t)(N > 0 ? N : 1));
     int i, n;
     for (i = 0; i < N; ++i) ident[i] = i;
-    row_lists rl;
-    build_rows(g, N, ident, v->NR, 1, culled, &rl);
+    cand_lists cl;
+    build_cands(g, N, ident, v, 1, culled, &cl);
 #pragma omp parallel for schedule(static)
     for (n = 0; n < v->NR; ++n) {
-        int64_t b, e;
-        row_range(&rl, culled, N, n, &b, &e);
         int m;
         for (m = 0; m < v->NA; ++m) {
             double acc = 0.0;
-            int64_t k;
+            int64_t k, b, e;
+            cand_range(&cl, m, n, &b, &e);
             for (k = b; k < e; ++k) {
-                int j = rl.idx[k];
+                int j = cl.idx[k];
                 const orc_gauss *q = &g[j];
-                if (culled && (m < q->bb[1][0] || m > q->bb[1][1])) continue;
+                if (culled && outside_box(q, 1, m, n)) continue;
                 double dx = m - q->u[1][0], dy = n - q->u[1][1];
                 double delta = mahal(q->C2[1], dx, dy);
                 if (delta > K2) continue;
@@ -356,7 +382,7 @@ static void imaging_pass(const orc_gauss *g, int N, const double *I, const orc_v
             S[(size_t)n * v->NA + m] = acc;
         }
     }
-    free_rows(&rl);
+    free_cands(&cl);
     free(ident);
 }
 
@@ -470,15 +496,13 @@ typedef struct {
     double o;        /* dL/do */
 } orc_adj;
 
-static int view_backward(const double *params, int N, const orc_view *v, const orc_cfg *cfg, int culled,
-                         const double *dLdS, double *grads, double *dLdI_out) {
+/* Adjoint of one view, given its forward state (projections g, depth order,
+ * ray sums A, intensities I); adds the view's gradient into grads. */
+static int view_adjoint(int N, const orc_view *v, const orc_cfg *cfg, int culled, const orc_gauss *g,
+                        const int *order, const double *A, const double *I, const double *dLdS, double *grads,
+                        double *dLdI_out) {
     double K2 = cutoff2(cfg);
-    orc_gauss *g = (orc_gauss *)malloc(sizeof(orc_gauss) * (size_t)(N > 0 ? N : 1));
-    int *order = (int *)malloc(sizeof(int) * (size_t)(N > 0 ? N : 1));
-    double *A = (double *)malloc(sizeof(double) * (size_t)(N > 0 ? N : 1));
-    double *I = (double *)malloc(sizeof(double) * (size_t)(N > 0 ? N : 1));
     orc_adj *adj = (orc_adj *)calloc((size_t)(N > 0 ? N : 1), sizeof(orc_adj));
-    view_forward(params, N, v, cfg, culled, g, order, A, I, NULL, NULL);
     int i;
 
     /* Gradient of the imaging process: S = sum_i c_i e_i I_i with
@@ -519,27 +543,26 @@ static int view_backward(const double *params, int N, const orc_view *v, const o
     for (i = 0; i < N; ++i) chat[i] = adj[i].gI * g[i].P;
     int nt = n_threads();
     double *part = (double *)calloc((size_t)nt * (size_t)(N > 0 ? N : 1) * 7, sizeof(double));
-    row_lists rl;
-    build_rows(g, N, order, v->NR, 0, culled, &rl);
+    cand_lists cl;
+    build_cands(g, N, order, v, 0, culled, &cl);
     int n;
 #pragma omp parallel for schedule(static)
     for (n = 0; n < v->NR; ++n) {
         double *Pp = part + (size_t)thread_id() * (size_t)N * 7;
-        int64_t b, e;
-        row_range(&rl, culled, N, n, &b, &e);
-        int64_t cap = e - b;
-        int *hit = (int *)malloc(sizeof(int) * (size_t)(cap > 0 ? cap : 1));
-        double *al = (double *)malloc(sizeof(double) * (size_t)(cap > 0 ? cap : 1));
-        double *Ts = (double *)malloc(sizeof(double) * (size_t)(cap > 0 ? cap : 1));
+        int64_t cap = N > 0 ? N : 1;
+        int *hit = (int *)malloc(sizeof(int) * (size_t)cap);
+        double *al = (double *)malloc(sizeof(double) * (size_t)cap);
+        double *Ts = (double *)malloc(sizeof(double) * (size_t)cap);
         int m;
         for (m = 0; m < v->NA; ++m) {
             /* front to back: the Gaussians this ray meets, their alpha and T */
-            int64_t cnt = 0, k;
+            int64_t cnt = 0, k, b, e;
             double T = 1.0;
+            cand_range(&cl, m, n, &b, &e);
             for (k = b; k < e; ++k) {
-                int j = rl.idx[k];
+                int j = cl.idx[k];
                 const orc_gauss *q = &g[j];
-                if (culled && (m < q->bb[0][0] || m > q->bb[0][1])) continue;
+                if (culled && outside_box(q, 0, m, n)) continue;
                 double dx = m - q->u[0][0], dy = n - q->u[0][1];
                 double delta = mahal(q->C2[0], dx, dy);
                 if (delta > K2) continue;
@@ -580,7 +603,7 @@ static int view_backward(const double *params, int N, const orc_view *v, const o
             adj[i].CC[1][0] += acc[5]; adj[i].CC[1][1] += acc[6];
         }
     free(part);
-    free_rows(&rl);
+    free_cands(&cl);
 
     /* Gradient of the Gaussian parameters: conic -> 2D covariance ->
      * Sigma_r -> Sigma -> (scale, rotation); pixel centres -> x_r -> mean. */
@@ -651,7 +674,19 @@ static int view_backward(const double *params, int N, const orc_view *v, const o
         for (k = 0; k < 4; ++k) gr[8 + k] += dq[k];
         if (dLdI_out) dLdI_out[i] = ad->gI;
     }
-    free(chat); free(g); free(order); free(A); free(I); free(adj);
+    free(chat); free(adj);
+    return 0;
+}
+
+static int view_backward(const double *params, int N, const orc_view *v, const orc_cfg *cfg, int culled,
+                         const double *dLdS, double *grads, double *dLdI_out) {
+    orc_gauss *g = (orc_gauss *)malloc(sizeof(orc_gauss) * (size_t)(N > 0 ? N : 1));
+    int *order = (int *)malloc(sizeof(int) * (size_t)(N > 0 ? N : 1));
+    double *A = (double *)malloc(sizeof(double) * (size_t)(N > 0 ? N : 1));
+    double *I = (double *)malloc(sizeof(double) * (size_t)(N > 0 ? N : 1));
+    view_forward(params, N, v, cfg, culled, g, order, A, I, NULL, NULL);
+    view_adjoint(N, v, cfg, culled, g, order, A, I, dLdS, grads, dLdI_out);
+    free(g); free(order); free(A); free(I);
     return 0;
 }
 
@@ -667,6 +702,44 @@ int orc_grad(const double *params, int32_t N, const orc_view *views, int32_t V, 
         pix += (size_t)views[v].NA * views[v].NR;
     }
     return 0;
+}
+
+/* One optimisation step's rendering work for V views of one scene: forward
+ * (images), the L1 loss against targets (mean over all pixels of all views),
+ * and the adjoint reusing each view's forward state.  images: out, laid out
+ * as in orc_render; grads: out [N][12].  Returns the loss (NaN on bad
+ * arguments). */
+double orc_l1(const double *S, const double *target, int64_t npix, double *dLdS);
+
+double orc_step(const double *params, int32_t N, const orc_view *views, int32_t V, const orc_cfg *cfg, int32_t culled,
+                const double *targets, double *images, double *grads) {
+    if (check_args(params, N, views, V, cfg) || !targets || !images || !grads) return NAN;
+    if (cfg->K <= 0.0) culled = 0;
+    size_t n1 = (size_t)(N > 0 ? N : 1);
+    orc_gauss **g = (orc_gauss **)malloc(sizeof(orc_gauss *) * (size_t)(V > 0 ? V : 1));
+    int **order = (int **)malloc(sizeof(int *) * (size_t)(V > 0 ? V : 1));
+    double **A = (double **)malloc(sizeof(double *) * (size_t)(V > 0 ? V : 1));
+    double **I = (double **)malloc(sizeof(double *) * (size_t)(V > 0 ? V : 1));
+    size_t pix = 0, *poff = (size_t *)malloc(sizeof(size_t) * (size_t)(V + 1));
+    int v;
+    for (v = 0; v < V; ++v) {
+        g[v] = (orc_gauss *)malloc(sizeof(orc_gauss) * n1);
+        order[v] = (int *)malloc(sizeof(int) * n1);
+        A[v] = (double *)malloc(sizeof(double) * n1);
+        I[v] = (double *)malloc(sizeof(double) * n1);
+        poff[v] = pix;
+        view_forward(params, N, &views[v], cfg, culled, g[v], order[v], A[v], I[v], images + pix, NULL);
+        pix += (size_t)views[v].NA * views[v].NR;
+    }
+    double *dLdS = (double *)malloc(sizeof(double) * (pix > 0 ? pix : 1));
+    double loss = orc_l1(images, targets, (int64_t)pix, dLdS);
+    memset(grads, 0, sizeof(double) * 12 * (size_t)N);
+    for (v = 0; v < V; ++v) {
+        view_adjoint(N, &views[v], cfg, culled, g[v], order[v], A[v], I[v], dLdS + poff[v], grads, NULL);
+        free(g[v]); free(order[v]); free(A[v]); free(I[v]);
+    }
+    free(g); free(order); free(A); free(I); free(poff); free(dLdS);
+    return loss;
 }
 
 /* Adam (Kingma & Ba), with the bias corrections and eps added to the square

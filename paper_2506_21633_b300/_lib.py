@@ -1,0 +1,217 @@
+"""ctypes binding of libsdgr.so (the C ABI in include/sdgr.h).
+
+Argument marshalling only: every step of the renderer runs in the CUDA
+kernels of libsdgr.so.  Device pointers are passed as integers (e.g.
+`tensor.data_ptr()`), streams as integers (`torch.cuda.Stream.cuda_stream`).
+Loading fails loudly (ImportError) if the library has not been built; there
+is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libsdgr.so")
+
+SDGR_OK, SDGR_ERR_INVALID, SDGR_ERR_CUDA, SDGR_ERR_CAPACITY, SDGR_ERR_TIMEOUT, SDGR_ERR_STATE = range(6)
+
+# every function the header declares (checked by tests/test_abi.py)
+EXPORTS = (
+    "sdgr_caps_for", "sdgr_workspace_size", "sdgr_ws_create", "sdgr_ws_destroy", "sdgr_preprocess",
+    "sdgr_bin_sort", "sdgr_render_fwd", "sdgr_render_bwd", "sdgr_adam_step", "sdgr_l1_loss",
+    "sdgr_read_status", "sdgr_status_string", "sdgr_profile_enable", "sdgr_profile_read",
+    "sdgr_count_pairs", "sdgr_launch_count",
+)
+
+STAGES = ("preprocess", "depth_sort", "bin", "intensity_fwd", "splat_fwd", "splat_bwd", "intensity_bwd",
+          "param_bwd")
+
+
+class SdgrView(ctypes.Structure):
+    _fields_ = [
+        ("phi", ctypes.c_double), ("theta", ctypes.c_double),
+        ("dA", ctypes.c_double), ("dR", ctypes.c_double),
+        ("NA", ctypes.c_int32), ("NR", ctypes.c_int32),
+        ("scene", ctypes.c_int32), ("reserved", ctypes.c_int32),
+        ("center", ctypes.c_double * 3),
+    ]
+
+
+class SdgrCfg(ctypes.Structure):
+    _fields_ = [
+        ("cutoff_K", ctypes.c_float), ("dilation_eps", ctypes.c_float),
+        ("T_min", ctypes.c_float), ("norm_mode", ctypes.c_int32),
+    ]
+
+
+class SdgrCaps(ctypes.Structure):
+    _fields_ = [
+        ("max_views", ctypes.c_int32), ("max_scenes", ctypes.c_int32),
+        ("max_gaussians", ctypes.c_int64), ("max_view_gauss", ctypes.c_int64),
+        ("max_pixels", ctypes.c_int64), ("max_tiles", ctypes.c_int64),
+        ("max_instances", ctypes.c_int64),
+    ]
+
+
+class SdgrError(RuntimeError):
+    def __init__(self, fn, code):
+        self.code = code
+        super().__init__("%s: %s (%d)" % (fn, status_string(code), code))
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError("libsdgr.so is not built (run `python -m paper_2506_21633_b300.build`)")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i32, i64, f32 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_float
+        P = ctypes.POINTER
+        L.sdgr_caps_for.argtypes = [P(SdgrView), i32, P(ctypes.c_int64), i32, i64, P(SdgrCaps)]
+        L.sdgr_workspace_size.argtypes = [P(SdgrCfg), P(SdgrCaps), P(ctypes.c_size_t)]
+        L.sdgr_ws_create.argtypes = [P(vp), vp, ctypes.c_size_t, P(SdgrCfg), P(SdgrCaps)]
+        L.sdgr_ws_destroy.argtypes = [vp]
+        L.sdgr_preprocess.argtypes = [vp, vp, P(ctypes.c_int64), i32, P(SdgrView), i32, vp]
+        L.sdgr_bin_sort.argtypes = [vp, vp]
+        L.sdgr_render_fwd.argtypes = [vp, vp, vp, vp]
+        L.sdgr_render_bwd.argtypes = [vp, vp, vp, i32, vp]
+        L.sdgr_count_pairs.argtypes = [vp, P(ctypes.c_int64), vp]
+        L.sdgr_launch_count.argtypes = []
+        L.sdgr_adam_step.argtypes = [vp, vp, vp, vp, i64, P(ctypes.c_float), f32, f32, f32, i32, vp]
+        L.sdgr_l1_loss.argtypes = [vp, vp, i64, vp, vp, vp]
+        L.sdgr_read_status.argtypes = [vp, P(ctypes.c_int64)]
+        L.sdgr_profile_enable.argtypes = [vp, i32]
+        L.sdgr_profile_read.argtypes = [vp, P(ctypes.c_double), P(ctypes.c_int64), i32]
+        L.sdgr_status_string.argtypes = [ctypes.c_int]
+        L.sdgr_status_string.restype = ctypes.c_char_p
+        for name in EXPORTS:
+            if name != "sdgr_status_string":
+                getattr(L, name).restype = ctypes.c_int
+        L.sdgr_launch_count.restype = ctypes.c_int64
+        _lib = L
+    return _lib
+
+
+def status_string(code: int) -> str:
+    return lib().sdgr_status_string(int(code)).decode()
+
+
+def _check(fn, code):
+    if code != SDGR_OK:
+        raise SdgrError(fn, code)
+
+
+def make_views(views):
+    arr = (SdgrView * max(1, len(views)))()
+    for k, v in enumerate(views):
+        a = arr[k]
+        a.phi, a.theta, a.dA, a.dR = v["phi"], v["theta"], v["dA"], v["dR"]
+        a.NA, a.NR = v["NA"], v["NR"]
+        a.scene = int(v.get("scene", 0))
+        for j in range(3):
+            a.center[j] = float(v["center"][j])
+    return arr
+
+
+def make_offsets(scene_offsets):
+    arr = (ctypes.c_int64 * len(scene_offsets))()
+    for k, o in enumerate(scene_offsets):
+        arr[k] = int(o)
+    return arr
+
+
+def make_cfg(cutoff_K=5.0, dilation_eps=0.3, T_min=0.0, norm_mode=0):
+    return SdgrCfg(cutoff_K=cutoff_K, dilation_eps=dilation_eps, T_min=T_min, norm_mode=norm_mode)
+
+
+# -- thin wrappers with the C names ------------------------------------------
+
+def sdgr_caps_for(views_arr, V, offsets_arr, n_scenes, instances):
+    caps = SdgrCaps()
+    _check("sdgr_caps_for", lib().sdgr_caps_for(views_arr, V, offsets_arr, n_scenes, int(instances),
+                                                ctypes.byref(caps)))
+    return caps
+
+
+def sdgr_workspace_size(cfg, caps):
+    n = ctypes.c_size_t()
+    _check("sdgr_workspace_size", lib().sdgr_workspace_size(ctypes.byref(cfg), ctypes.byref(caps), ctypes.byref(n)))
+    return n.value
+
+
+def sdgr_ws_create(device_ptr, nbytes, cfg, caps):
+    h = ctypes.c_void_p()
+    _check("sdgr_ws_create", lib().sdgr_ws_create(ctypes.byref(h), ctypes.c_void_p(device_ptr), nbytes,
+                                                  ctypes.byref(cfg), ctypes.byref(caps)))
+    return h
+
+
+def sdgr_ws_destroy(ws):
+    _check("sdgr_ws_destroy", lib().sdgr_ws_destroy(ws))
+
+
+def sdgr_preprocess(ws, params_ptr, offsets_arr, n_scenes, views_arr, V, stream):
+    _check("sdgr_preprocess", lib().sdgr_preprocess(ws, ctypes.c_void_p(params_ptr), offsets_arr, n_scenes,
+                                                    views_arr, V, ctypes.c_void_p(stream)))
+
+
+def sdgr_bin_sort(ws, stream):
+    _check("sdgr_bin_sort", lib().sdgr_bin_sort(ws, ctypes.c_void_p(stream)))
+
+
+def sdgr_render_fwd(ws, images_ptr, intensity_ptr, stream):
+    _check("sdgr_render_fwd", lib().sdgr_render_fwd(ws, ctypes.c_void_p(images_ptr),
+                                                    ctypes.c_void_p(intensity_ptr or None),
+                                                    ctypes.c_void_p(stream)))
+
+
+def sdgr_render_bwd(ws, dLdS_ptr, grads_ptr, accumulate, stream):
+    _check("sdgr_render_bwd", lib().sdgr_render_bwd(ws, ctypes.c_void_p(dLdS_ptr), ctypes.c_void_p(grads_ptr),
+                                                    int(bool(accumulate)), ctypes.c_void_p(stream)))
+
+
+def sdgr_count_pairs(ws, stream):
+    out = (ctypes.c_int64 * 2)()
+    _check("sdgr_count_pairs", lib().sdgr_count_pairs(ws, out, ctypes.c_void_p(stream)))
+    return int(out[0]), int(out[1])
+
+
+def sdgr_launch_count():
+    return int(lib().sdgr_launch_count())
+
+
+def sdgr_adam_step(p, g, m, v, N, lr, b1, b2, eps, step, stream):
+    lr_arr = (ctypes.c_float * 5)(*[float(x) for x in lr])
+    _check("sdgr_adam_step", lib().sdgr_adam_step(ctypes.c_void_p(p), ctypes.c_void_p(g), ctypes.c_void_p(m),
+                                                  ctypes.c_void_p(v), int(N), lr_arr, b1, b2, eps, int(step),
+                                                  ctypes.c_void_p(stream)))
+
+
+def sdgr_l1_loss(images, targets, npix, dLdS, loss, stream):
+    _check("sdgr_l1_loss", lib().sdgr_l1_loss(ctypes.c_void_p(images), ctypes.c_void_p(targets), int(npix),
+                                              ctypes.c_void_p(dLdS), ctypes.c_void_p(loss), ctypes.c_void_p(stream)))
+
+
+def sdgr_read_status(ws):
+    req = ctypes.c_int64()
+    code = lib().sdgr_read_status(ws, ctypes.byref(req))
+    if code not in (SDGR_OK, SDGR_ERR_CAPACITY, SDGR_ERR_TIMEOUT):
+        raise SdgrError("sdgr_read_status", code)
+    return code, req.value
+
+
+def sdgr_profile_enable(ws, enable=True):
+    _check("sdgr_profile_enable", lib().sdgr_profile_enable(ws, int(bool(enable))))
+
+
+def sdgr_profile_read(ws, reset=True):
+    """{stage name: (total ms, launches)} since the last reset."""
+    n = len(STAGES)
+    ms = (ctypes.c_double * n)()
+    cnt = (ctypes.c_int64 * n)()
+    _check("sdgr_profile_read", lib().sdgr_profile_read(ws, ms, cnt, int(bool(reset))))
+    return {STAGES[k]: (ms[k], cnt[k]) for k in range(n)}

@@ -1,0 +1,541 @@
+// api.cu -- host side of the C ABI declared in include/sdgr.h: argument
+// validation, the per-call plan (view / scene tables), the workspace layout
+// inside the caller's device buffer, and the launch sequence of each step.
+#include <math.h>
+#include <string.h>
+
+#include <atomic>
+#include <new>
+#include <vector>
+
+#include "sdgr_internal.cuh"
+
+using namespace sdgr;
+
+static std::atomic<long long> g_launches{0};
+
+void sdgr::note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+namespace {
+
+constexpr size_t ALIGN = 256;
+constexpr int64_t MAX_INSTANCES = (int64_t)0x7fffffff;  // instance indices are 32-bit
+
+struct Layout {
+    size_t views, scenes, scene_views, status;
+    size_t comp, img, rectC, rectI, cntC, cntI;
+    size_t dk0, dv0, dk1, dv1;
+    size_t scnt, soff, scan64;
+    size_t ik0, iv0, ik1, iv1;
+    size_t hist, scan32, ranges;
+    size_t A, Tstop, last, accI, accC;
+    size_t total;
+};
+
+size_t align_up(size_t x) { return (x + ALIGN - 1) / ALIGN * ALIGN; }
+
+bool caps_ok(const sdgr_caps *c) {
+    return c && c->max_views >= 0 && c->max_scenes >= 0 && c->max_gaussians >= 0 && c->max_view_gauss >= 0 &&
+           c->max_pixels >= 0 && c->max_tiles >= 0 && c->max_instances >= 0 && c->max_instances <= MAX_INSTANCES &&
+           c->max_view_gauss < ((int64_t)1 << 32) && c->max_tiles < ((int64_t)1 << 30) &&
+           c->max_views < (1 << 24) && c->max_pixels < ((int64_t)1 << 40) && c->max_gaussians < ((int64_t)1 << 34);
+}
+
+int64_t depth_sort_blocks_cap(const sdgr_caps *c) { return c->max_view_gauss / SORT_IPB + c->max_views + 1; }
+
+Layout make_layout(const sdgr_caps *c) {
+    Layout L;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        size_t o = off;
+        off += align_up(bytes > 0 ? bytes : 1);
+        return o;
+    };
+    const size_t VG = (size_t)c->max_view_gauss, V = (size_t)c->max_views, S = (size_t)c->max_scenes;
+    const size_t NI = (size_t)c->max_instances, NP = (size_t)c->max_pixels, NT = (size_t)c->max_tiles;
+    L.views = take(V * sizeof(ViewDev));
+    L.scenes = take(S * sizeof(SceneDev));
+    L.scene_views = take(V * sizeof(int32_t));
+    L.status = take(sizeof(StatusDev));
+    L.comp = take(VG * sizeof(CompRec));
+    L.img = take(VG * sizeof(ImgRec));
+    L.rectC = take(VG * sizeof(uint2));
+    L.rectI = take(VG * sizeof(uint2));
+    L.cntC = take(VG * 4);
+    L.cntI = take(VG * 4);
+    L.dk0 = take(VG * 4);
+    L.dv0 = take(VG * 4);
+    L.dk1 = take(VG * 4);
+    L.dv1 = take(VG * 4);
+    L.scnt = take(2 * VG * 8);
+    L.soff = take(2 * VG * 8);
+    L.scan64 = take(scan_scratch_elems((int64_t)(2 * VG)) * 8);
+    L.ik0 = take(NI * 4);
+    L.iv0 = take(NI * 4);
+    L.ik1 = take(NI * 4);
+    L.iv1 = take(NI * 4);
+    int64_t hb = depth_sort_blocks_cap(c);
+    int64_t ib = (c->max_instances + SORT_IPB - 1) / SORT_IPB;
+    int64_t hn = (hb > ib ? hb : ib) * RADIX;
+    L.hist = take((size_t)hn * 4);
+    L.scan32 = take(scan_scratch_elems(hn) * 4);
+    L.ranges = take(2 * NT * sizeof(uint2));
+    L.A = take(VG * 4);
+    L.Tstop = take(NP * 4);
+    L.last = take(NP * 4);
+    L.accI = take(VG * 2 * sizeof(float4));
+    L.accC = take(VG * 2 * sizeof(float4));
+    L.total = off;
+    return L;
+}
+
+bool cfg_ok(const sdgr_cfg *cfg) {
+    return cfg && cfg->cutoff_K > 0.f && isfinite(cfg->cutoff_K) && cfg->dilation_eps >= 0.f &&
+           isfinite(cfg->dilation_eps) && cfg->T_min >= 0.f && cfg->T_min < 1.f &&
+           (cfg->norm_mode == 0 || cfg->norm_mode == 1);
+}
+
+bool view_ok(const sdgr_view &v) {
+    const double half_pi = 1.5707963267948966;
+    return v.theta > 0.0 && v.theta < half_pi && v.dA > 0.0 && v.dR > 0.0 && isfinite(v.phi) && isfinite(v.dA) &&
+           isfinite(v.dR) && v.NA > 0 && v.NR > 0 && v.NA <= (1 << 20) && v.NR <= (1 << 20) &&
+           isfinite(v.center[0]) && isfinite(v.center[1]) && isfinite(v.center[2]);
+}
+
+int tiles_of(int n) { return (n + TILE - 1) / TILE; }
+
+}  // namespace
+
+struct sdgr_ws {
+    char *base = nullptr;
+    size_t bytes = 0;
+    sdgr_cfg cfg;
+    sdgr_caps caps;
+    Layout L;
+    int sms = 148;
+    // plan of the last sdgr_preprocess()
+    int V = 0, n_scenes = 0;
+    int64_t VG = 0, npix = 0, n_gauss = 0;
+    int tiles = 0, sort_blocks = 0, key_bits = 0;
+    const float *params = nullptr;
+    int stage = 0;  // 1 preprocessed, 2 sorted, 3 forward done
+    uint32_t *inst_keys = nullptr, *inst_vals = nullptr;
+    // stage timing (sdgr_profile_enable / sdgr_profile_read)
+    bool prof_on = false;
+    std::vector<cudaEvent_t> prof_ev;      // pool, two per recorded launch
+    std::vector<int> prof_stage;           // stage of each recorded pair
+    int prof_used = 0;
+    double prof_ms[SDGR_NUM_STAGES] = {0};
+    int64_t prof_n[SDGR_NUM_STAGES] = {0};
+    std::vector<ViewDev> hviews;
+    std::vector<SceneDev> hscenes;
+    std::vector<int32_t> hscene_views;
+
+    template <typename T>
+    T *at(size_t off) const {
+        return reinterpret_cast<T *>(base + off);
+    }
+};
+
+namespace {
+
+constexpr int PROF_PAIRS = 2048;
+
+cudaError_t prof_harvest(sdgr_ws *ws) {
+    if (ws->prof_used == 0) return cudaSuccess;
+    cudaError_t e = cudaEventSynchronize(ws->prof_ev[2 * (ws->prof_used - 1) + 1]);
+    if (e != cudaSuccess) return e;
+    for (int k = 0; k < ws->prof_used; ++k) {
+        float ms = 0.f;
+        e = cudaEventElapsedTime(&ms, ws->prof_ev[2 * k], ws->prof_ev[2 * k + 1]);
+        if (e != cudaSuccess) return e;
+        ws->prof_ms[ws->prof_stage[k]] += ms;
+        ws->prof_n[ws->prof_stage[k]] += 1;
+    }
+    ws->prof_used = 0;
+    return cudaSuccess;
+}
+
+// Records the start event of a stage; returns the pair index or -1.
+int prof_begin(sdgr_ws *ws, int stage, cudaStream_t s) {
+    if (!ws->prof_on) return -1;
+    if (ws->prof_used == PROF_PAIRS && prof_harvest(ws) != cudaSuccess) return -1;
+    const int k = ws->prof_used++;
+    ws->prof_stage[k] = stage;
+    cudaEventRecord(ws->prof_ev[2 * k], s);
+    return k;
+}
+
+void prof_end(sdgr_ws *ws, int k, cudaStream_t s) {
+    if (k >= 0) cudaEventRecord(ws->prof_ev[2 * k + 1], s);
+}
+
+}  // namespace
+
+#define CK(call)                                      \
+    do {                                              \
+        cudaError_t e_ = (call);                      \
+        if (e_ != cudaSuccess) return SDGR_ERR_CUDA;  \
+    } while (0)
+
+extern "C" {
+
+const char *sdgr_status_string(sdgr_status s) {
+    switch (s) {
+        case SDGR_OK: return "ok";
+        case SDGR_ERR_INVALID: return "invalid argument";
+        case SDGR_ERR_CUDA: return "CUDA runtime error";
+        case SDGR_ERR_CAPACITY: return "instance capacity exceeded";
+        case SDGR_ERR_TIMEOUT: return "bounded device wait timed out";
+        case SDGR_ERR_STATE: return "calls out of order on this workspace";
+    }
+    return "unknown status";
+}
+
+sdgr_status sdgr_caps_for(const sdgr_view *views, int32_t V, const int64_t *scene_offsets, int32_t n_scenes,
+                          int64_t instances, sdgr_caps *out) {
+    if (!out || V < 0 || n_scenes < 0 || (V > 0 && !views) || !scene_offsets || instances < 0 ||
+        instances > MAX_INSTANCES)
+        return SDGR_ERR_INVALID;
+    if (scene_offsets[0] != 0) return SDGR_ERR_INVALID;
+    for (int s = 0; s < n_scenes; ++s)
+        if (scene_offsets[s + 1] < scene_offsets[s]) return SDGR_ERR_INVALID;
+    int64_t vg = 0, pix = 0, tiles = 0;
+    for (int v = 0; v < V; ++v) {
+        if (!view_ok(views[v]) || views[v].scene < 0 || views[v].scene >= n_scenes) return SDGR_ERR_INVALID;
+        vg += scene_offsets[views[v].scene + 1] - scene_offsets[views[v].scene];
+        pix += (int64_t)views[v].NA * views[v].NR;
+        tiles += (int64_t)tiles_of(views[v].NA) * tiles_of(views[v].NR);
+    }
+    out->max_views = V;
+    out->max_scenes = n_scenes;
+    out->max_gaussians = scene_offsets[n_scenes];
+    out->max_view_gauss = vg;
+    out->max_pixels = pix;
+    out->max_tiles = tiles;
+    out->max_instances = instances;
+    return caps_ok(out) ? SDGR_OK : SDGR_ERR_INVALID;
+}
+
+sdgr_status sdgr_workspace_size(const sdgr_cfg *cfg, const sdgr_caps *caps, size_t *bytes) {
+    if (!bytes || !cfg_ok(cfg) || !caps_ok(caps)) return SDGR_ERR_INVALID;
+    *bytes = make_layout(caps).total;
+    return SDGR_OK;
+}
+
+sdgr_status sdgr_ws_create(sdgr_ws **out, void *device_buffer, size_t bytes, const sdgr_cfg *cfg,
+                           const sdgr_caps *caps) {
+    if (!out || !device_buffer || !cfg_ok(cfg) || !caps_ok(caps)) return SDGR_ERR_INVALID;
+    if (((uintptr_t)device_buffer) % ALIGN != 0) return SDGR_ERR_INVALID;
+    Layout L = make_layout(caps);
+    if (bytes < L.total) return SDGR_ERR_INVALID;
+    sdgr_ws *ws = new (std::nothrow) sdgr_ws();
+    if (!ws) return SDGR_ERR_INVALID;
+    ws->base = static_cast<char *>(device_buffer);
+    ws->bytes = bytes;
+    ws->cfg = *cfg;
+    ws->caps = *caps;
+    ws->L = L;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&ws->sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        delete ws;
+        return SDGR_ERR_CUDA;
+    }
+    *out = ws;
+    return SDGR_OK;
+}
+
+sdgr_status sdgr_ws_destroy(sdgr_ws *ws) {
+    if (!ws) return SDGR_ERR_INVALID;
+    for (cudaEvent_t e : ws->prof_ev) cudaEventDestroy(e);
+    delete ws;
+    return SDGR_OK;
+}
+
+sdgr_status sdgr_preprocess(sdgr_ws *ws, const float *params, const int64_t *scene_offsets, int32_t n_scenes,
+                            const sdgr_view *views, int32_t V, void *stream) {
+    if (!ws || !scene_offsets || n_scenes < 0 || V < 0 || (V > 0 && !views)) return SDGR_ERR_INVALID;
+    if (n_scenes > ws->caps.max_scenes || V > ws->caps.max_views) return SDGR_ERR_INVALID;
+    if (scene_offsets[0] != 0) return SDGR_ERR_INVALID;
+    for (int s = 0; s < n_scenes; ++s)
+        if (scene_offsets[s + 1] < scene_offsets[s]) return SDGR_ERR_INVALID;
+    const int64_t n_gauss = scene_offsets[n_scenes];
+    if (n_gauss > ws->caps.max_gaussians) return SDGR_ERR_INVALID;
+    if (n_gauss > 0 && (!params || ((uintptr_t)params) % 16 != 0)) return SDGR_ERR_INVALID;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+
+    // plan: per-view offsets and constants
+    ws->hviews.assign((size_t)V, ViewDev());
+    int64_t vg = 0, pix = 0;
+    int64_t tiles = 0, sblk = 0;
+    for (int v = 0; v < V; ++v) {
+        const sdgr_view &in = views[v];
+        if (!view_ok(in) || in.scene < 0 || in.scene >= n_scenes) return SDGR_ERR_INVALID;
+        ViewDev &d = ws->hviews[v];
+        memset(&d, 0, sizeof(d));
+        const double sp = sin(in.phi), cp = cos(in.phi), st = sin(in.theta), ct = cos(in.theta);
+        // R_r of eq. R_r: azimuth axis, elevation axis, line of sight
+        const double Rr[3][3] = {{-sp, -cp, 0.0}, {-st * cp, st * sp, ct}, {-ct * cp, ct * sp, -st}};
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) d.r[a][b] = (float)Rr[a][b];
+        for (int b = 0; b < 3; ++b) {
+            d.r2d[b] = Rr[2][b];
+            d.cd[b] = in.center[b];
+            d.c[b] = (float)in.center[b];
+        }
+        d.inv_dA = (float)(1.0 / in.dA);
+        d.inv_cy = (float)(1.0 / (in.dR * tan(in.theta)));
+        d.inv_dR = (float)(1.0 / in.dR);
+        d.offx = (float)(in.NA * 0.5 - 0.5);
+        d.offy = (float)(in.NR * 0.5 - 0.5);
+        d.NA = in.NA;
+        d.NR = in.NR;
+        d.tiles_x = tiles_of(in.NA);
+        d.tiles_y = tiles_of(in.NR);
+        d.scene = in.scene;
+        const int64_t N = scene_offsets[in.scene + 1] - scene_offsets[in.scene];
+        d.N = (int32_t)N;
+        d.g_off = scene_offsets[in.scene];
+        d.vg_off = vg;
+        d.pix_off = pix;
+        d.tile_off = (int32_t)tiles;
+        d.sblk_off = (int32_t)sblk;
+        d.sblk_n = (int32_t)((N + SORT_IPB - 1) / SORT_IPB);
+        vg += N;
+        pix += (int64_t)in.NA * in.NR;
+        tiles += (int64_t)d.tiles_x * d.tiles_y;
+        sblk += d.sblk_n;
+        if (N >= ((int64_t)1 << 31)) return SDGR_ERR_INVALID;
+    }
+    if (vg > ws->caps.max_view_gauss || pix > ws->caps.max_pixels || tiles > ws->caps.max_tiles ||
+        sblk > depth_sort_blocks_cap(&ws->caps))
+        return SDGR_ERR_INVALID;
+    // scenes and their view lists
+    ws->hscenes.assign((size_t)n_scenes, SceneDev());
+    ws->hscene_views.clear();
+    for (int sc = 0; sc < n_scenes; ++sc) {
+        SceneDev &d = ws->hscenes[sc];
+        memset(&d, 0, sizeof(d));
+        d.g_off = scene_offsets[sc];
+        d.N = (int32_t)(scene_offsets[sc + 1] - scene_offsets[sc]);
+        d.vstart = (int32_t)ws->hscene_views.size();
+        for (int v = 0; v < V; ++v)
+            if (views[v].scene == sc) ws->hscene_views.push_back(v);
+        d.vcount = (int32_t)ws->hscene_views.size() - d.vstart;
+    }
+    while (ws->hscene_views.size() % 4) ws->hscene_views.push_back(0);
+
+    ws->V = V;
+    ws->n_scenes = n_scenes;
+    ws->VG = vg;
+    ws->npix = pix;
+    ws->n_gauss = n_gauss;
+    ws->tiles = (int)tiles;
+    ws->sort_blocks = (int)sblk;
+    int bits = 1;
+    while (((int64_t)1 << bits) < 2 * tiles) ++bits;
+    ws->key_bits = bits;
+    ws->params = params;
+    ws->stage = 0;
+
+    const Layout &L = ws->L;
+    if (V > 0) CK(launch_upload(ws->hviews.data(), (size_t)V * sizeof(ViewDev), ws->base + L.views, s));
+    if (n_scenes > 0) CK(launch_upload(ws->hscenes.data(), (size_t)n_scenes * sizeof(SceneDev), ws->base + L.scenes, s));
+    if (!ws->hscene_views.empty())
+        CK(launch_upload(ws->hscene_views.data(), ws->hscene_views.size() * 4, ws->base + L.scene_views, s));
+    CK(cudaMemsetAsync(ws->base + L.status, 0, sizeof(StatusDev), s));
+    const sdgr_cfg &c = ws->cfg;
+    const int pk = prof_begin(ws, SDGR_STAGE_PREPROCESS, s);
+    CK(launch_preprocess(reinterpret_cast<const float4 *>(params), ws->at<ViewDev>(L.views), V, vg, c.cutoff_K,
+                         c.dilation_eps, c.norm_mode, ws->at<CompRec>(L.comp), ws->at<ImgRec>(L.img),
+                         ws->at<uint2>(L.rectC), ws->at<uint2>(L.rectI), ws->at<uint32_t>(L.cntC),
+                         ws->at<uint32_t>(L.cntI), ws->at<uint32_t>(L.dk0), ws->at<uint32_t>(L.dv0), ws->sms, s));
+    prof_end(ws, pk, s);
+    ws->stage = 1;
+    return SDGR_OK;
+}
+
+sdgr_status sdgr_bin_sort(sdgr_ws *ws, void *stream) {
+    if (!ws) return SDGR_ERR_INVALID;
+    if (ws->stage < 1) return SDGR_ERR_STATE;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const Layout &L = ws->L;
+    StatusDev *st = ws->at<StatusDev>(L.status);
+    const ViewDev *views = ws->at<ViewDev>(L.views);
+    // depth order per view: stable radix sort of the keys, values = slot index
+    const int pk0 = prof_begin(ws, SDGR_STAGE_DEPTH_SORT, s);
+    CK(launch_depth_sort(views, ws->V, ws->sort_blocks, ws->at<uint32_t>(L.dk0), ws->at<uint32_t>(L.dv0),
+                         ws->at<uint32_t>(L.dk1), ws->at<uint32_t>(L.dv1), ws->at<uint32_t>(L.hist),
+                         ws->at<uint32_t>(L.scan32), s));
+    prof_end(ws, pk0, s);
+    const int pk1 = prof_begin(ws, SDGR_STAGE_BIN, s);
+    const uint32_t *sorted_vg = ws->at<uint32_t>(L.dv0);
+    unsigned long long *scnt = ws->at<unsigned long long>(L.scnt);
+    unsigned long long *soff = ws->at<unsigned long long>(L.soff);
+    CK(launch_gather_counts(sorted_vg, ws->at<uint32_t>(L.cntC), ws->at<uint32_t>(L.cntI), ws->VG, scnt, ws->sms,
+                            s));
+    CK(launch_scan_u64(scnt, soff, 2 * ws->VG, ws->at<unsigned long long>(L.scan64), s));
+    CK(launch_check_capacity(scnt, soff, ws->VG, ws->caps.max_instances, st, s));
+    CK(launch_emit(sorted_vg, soff, ws->at<uint2>(L.rectC), ws->at<uint2>(L.rectI), views, ws->V, ws->VG, ws->tiles,
+                   st, ws->at<uint32_t>(L.ik0), ws->at<uint32_t>(L.iv0), ws->sms, s));
+    int final1 = 0;
+    CK(launch_inst_sort(st, ws->caps.max_instances, ws->key_bits, ws->at<uint32_t>(L.ik0), ws->at<uint32_t>(L.iv0),
+                        ws->at<uint32_t>(L.ik1), ws->at<uint32_t>(L.iv1), ws->at<uint32_t>(L.hist),
+                        ws->at<uint32_t>(L.scan32), &final1, s));
+    ws->inst_keys = ws->at<uint32_t>(final1 ? L.ik1 : L.ik0);
+    ws->inst_vals = ws->at<uint32_t>(final1 ? L.iv1 : L.iv0);
+    uint2 *ranges = ws->at<uint2>(L.ranges);
+    CK(cudaMemsetAsync(ranges, 0, (size_t)2 * ws->tiles * sizeof(uint2), s));
+    CK(launch_ranges(ws->inst_keys, st, ws->caps.max_instances, ranges, ws->sms, s));
+    prof_end(ws, pk1, s);
+    ws->stage = 2;
+    return SDGR_OK;
+}
+
+static float exp2_cut(float K) { return -0.5f * LOG2E * K * K; }
+
+static float t_floor(float T_min) {
+    const float f = 7.888609052210118e-31f;  // 2^-100
+    return T_min > f ? T_min : f;
+}
+
+sdgr_status sdgr_render_fwd(sdgr_ws *ws, float *images, float *intensity, void *stream) {
+    if (!ws) return SDGR_ERR_INVALID;
+    if (ws->stage < 2) return SDGR_ERR_STATE;
+    if (ws->npix > 0 && !images) return SDGR_ERR_INVALID;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const Layout &L = ws->L;
+    const StatusDev *st = ws->at<StatusDev>(L.status);
+    const ViewDev *views = ws->at<ViewDev>(L.views);
+    const uint2 *ranges = ws->at<uint2>(L.ranges);
+    const float cut = exp2_cut(ws->cfg.cutoff_K);
+    float *A = ws->at<float>(L.A);
+    if (ws->VG > 0) CK(cudaMemsetAsync(A, 0, (size_t)ws->VG * 4, s));
+    int pk = prof_begin(ws, SDGR_STAGE_INTENSITY_FWD, s);
+    CK(launch_intensity_fwd(ranges, ws->inst_vals, ws->at<CompRec>(L.comp), views, ws->V, ws->tiles, cut,
+                            t_floor(ws->cfg.T_min), st, A, ws->at<float>(L.Tstop), ws->at<int32_t>(L.last), s));
+    prof_end(ws, pk, s);
+    pk = prof_begin(ws, SDGR_STAGE_SPLAT_FWD, s);
+    CK(launch_splat_fwd(ranges + ws->tiles, ws->inst_vals, ws->at<ImgRec>(L.img), ws->at<CompRec>(L.comp), A, views,
+                        ws->V, ws->tiles, cut, st, images, s));
+    prof_end(ws, pk, s);
+    if (intensity) CK(launch_intensity_out(ws->at<CompRec>(L.comp), A, ws->VG, intensity, ws->sms, s));
+    ws->stage = 3;
+    return SDGR_OK;
+}
+
+sdgr_status sdgr_render_bwd(sdgr_ws *ws, const float *dL_dimages, float *grads, int32_t accumulate, void *stream) {
+    if (!ws) return SDGR_ERR_INVALID;
+    if (ws->stage < 3) return SDGR_ERR_STATE;
+    if ((ws->npix > 0 && !dL_dimages) || (ws->n_gauss > 0 && (!grads || ((uintptr_t)grads) % 16 != 0)))
+        return SDGR_ERR_INVALID;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const Layout &L = ws->L;
+    const StatusDev *st = ws->at<StatusDev>(L.status);
+    const ViewDev *views = ws->at<ViewDev>(L.views);
+    const uint2 *ranges = ws->at<uint2>(L.ranges);
+    const float cut = exp2_cut(ws->cfg.cutoff_K);
+    float4 *accI = ws->at<float4>(L.accI), *accC = ws->at<float4>(L.accC);
+    if (ws->VG > 0) {
+        CK(cudaMemsetAsync(accI, 0, (size_t)ws->VG * 2 * sizeof(float4), s));
+        CK(cudaMemsetAsync(accC, 0, (size_t)ws->VG * 2 * sizeof(float4), s));
+    }
+    if (ws->n_gauss > 0 && !accumulate) CK(cudaMemsetAsync(grads, 0, (size_t)ws->n_gauss * 12 * 4, s));
+    int pk = prof_begin(ws, SDGR_STAGE_SPLAT_BWD, s);
+    CK(launch_splat_bwd(ranges + ws->tiles, ws->inst_vals, ws->at<ImgRec>(L.img), dL_dimages, views, ws->V, ws->tiles,
+                        cut, st, accI, s));
+    prof_end(ws, pk, s);
+    pk = prof_begin(ws, SDGR_STAGE_INTENSITY_BWD, s);
+    CK(launch_intensity_bwd(ranges, ws->inst_vals, ws->at<CompRec>(L.comp), ws->at<ImgRec>(L.img), accI,
+                            ws->at<float>(L.Tstop), ws->at<int32_t>(L.last), views, ws->V, ws->tiles, cut, st, accC,
+                            s));
+    prof_end(ws, pk, s);
+    pk = prof_begin(ws, SDGR_STAGE_PARAM_BWD, s);
+    CK(launch_param_bwd(reinterpret_cast<const float4 *>(ws->params), views, ws->at<SceneDev>(L.scenes),
+                        ws->at<int32_t>(L.scene_views), ws->n_scenes, ws->n_gauss, ws->cfg.dilation_eps,
+                        ws->cfg.norm_mode, ws->at<float>(L.A), accI, accC, st, reinterpret_cast<float4 *>(grads),
+                        ws->sms, s));
+    prof_end(ws, pk, s);
+    return SDGR_OK;
+}
+
+sdgr_status sdgr_adam_step(float *params, const float *grads, float *m, float *v, int64_t N, const float *lr,
+                           float b1, float b2, float eps, int32_t step, void *stream) {
+    if (N < 0 || step < 1 || !lr) return SDGR_ERR_INVALID;
+    if (N == 0) return SDGR_OK;
+    if (!params || !grads || !m || !v) return SDGR_ERR_INVALID;
+    if (((uintptr_t)params | (uintptr_t)grads | (uintptr_t)m | (uintptr_t)v) % 16 != 0) return SDGR_ERR_INVALID;
+    if (!(b1 >= 0.f && b1 < 1.f && b2 >= 0.f && b2 < 1.f && eps >= 0.f)) return SDGR_ERR_INVALID;
+    int dev = 0, sms = 148;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    CK(launch_adam(reinterpret_cast<float4 *>(params), reinterpret_cast<const float4 *>(grads),
+                   reinterpret_cast<float4 *>(m), reinterpret_cast<float4 *>(v), N * 3, lr, b1, b2, eps, step, sms,
+                   static_cast<cudaStream_t>(stream)));
+    return SDGR_OK;
+}
+
+sdgr_status sdgr_l1_loss(const float *images, const float *targets, int64_t npix, float *dL_dimages, float *loss,
+                         void *stream) {
+    if (npix < 0 || !loss || (npix > 0 && (!images || !targets || !dL_dimages))) return SDGR_ERR_INVALID;
+    int dev = 0, sms = 148;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    CK(launch_l1(images, targets, npix, dL_dimages, loss, sms, static_cast<cudaStream_t>(stream)));
+    return SDGR_OK;
+}
+
+sdgr_status sdgr_count_pairs(sdgr_ws *ws, int64_t *pairs, void *stream) {
+    if (!ws || !pairs) return SDGR_ERR_INVALID;
+    if (ws->stage < 2) return SDGR_ERR_STATE;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    StatusDev *st = ws->at<StatusDev>(ws->L.status);
+    CK(cudaMemsetAsync(st->pairs, 0, sizeof(st->pairs), s));
+    CK(launch_count_pairs(ws->at<uint2>(ws->L.ranges), ws->inst_vals, ws->at<CompRec>(ws->L.comp),
+                          ws->at<ImgRec>(ws->L.img), ws->at<ViewDev>(ws->L.views), ws->V, ws->tiles,
+                          exp2_cut(ws->cfg.cutoff_K), st, s));
+    CK(cudaStreamSynchronize(s));
+    unsigned long long h[2];
+    CK(cudaMemcpy(h, st->pairs, sizeof(h), cudaMemcpyDeviceToHost));
+    pairs[0] = (int64_t)h[0];
+    pairs[1] = (int64_t)h[1];
+    return SDGR_OK;
+}
+
+int64_t sdgr_launch_count(void) { return (int64_t)g_launches.load(); }
+
+sdgr_status sdgr_profile_enable(sdgr_ws *ws, int32_t enable) {
+    if (!ws) return SDGR_ERR_INVALID;
+    if (enable && ws->prof_ev.empty()) {
+        ws->prof_ev.assign(2 * PROF_PAIRS, nullptr);
+        ws->prof_stage.assign(PROF_PAIRS, 0);
+        for (auto &e : ws->prof_ev) CK(cudaEventCreate(&e));
+    }
+    ws->prof_on = enable != 0;
+    return SDGR_OK;
+}
+
+sdgr_status sdgr_profile_read(sdgr_ws *ws, double *ms, int64_t *launches, int32_t reset) {
+    if (!ws || !ms || !launches) return SDGR_ERR_INVALID;
+    CK(prof_harvest(ws));
+    for (int k = 0; k < SDGR_NUM_STAGES; ++k) {
+        ms[k] = ws->prof_ms[k];
+        launches[k] = ws->prof_n[k];
+        if (reset) {
+            ws->prof_ms[k] = 0.0;
+            ws->prof_n[k] = 0;
+        }
+    }
+    return SDGR_OK;
+}
+
+sdgr_status sdgr_read_status(sdgr_ws *ws, int64_t *required_instances) {
+    if (!ws) return SDGR_ERR_INVALID;
+    StatusDev h;
+    CK(cudaMemcpy(&h, ws->base + ws->L.status, sizeof(h), cudaMemcpyDeviceToHost));
+    if (required_instances) *required_instances = h.required;
+    return (sdgr_status)h.code;
+}
+
+}  // extern "C"

@@ -1,0 +1,182 @@
+// k_preprocess.cu -- steps a1-a5 of the rasterizer: activations, 3D
+// covariance, world->radar transform and the projections onto the
+// computation and imaging planes (Mapping and Projection Algorithm,
+// Section II-A-1 of SAR-GS, eqs. G(x), W, R_r, Sigmaprime, x_r, x_C, x_i).
+//
+// One thread per (view, Gaussian).  Reads the three float4 of the Gaussian
+// (48 B, coalesced) and writes two 32-byte plane records, two tile
+// rectangles, two instance counts and the float32 depth key.
+#include "sdgr_internal.cuh"
+
+namespace sdgr {
+
+// ---------------------------------------------------------------------------
+// Plan upload: the per-call view / scene tables travel as kernel parameters
+// (no pageable-memory copy, so the upload can be captured into a graph).
+// ---------------------------------------------------------------------------
+constexpr int BLOB_VEC = 1000;  // 16,000 bytes of payload per launch
+
+struct Blob {
+    uint32_t n;
+    uint32_t pad[3];
+    uint4 data[BLOB_VEC];
+};
+
+__global__ void k_upload(const __grid_constant__ Blob b, uint4 *dst) {
+    for (uint32_t i = threadIdx.x; i < b.n; i += blockDim.x) dst[i] = b.data[i];
+}
+
+cudaError_t launch_upload(const void *host_src, size_t bytes, void *dev_dst, cudaStream_t s) {
+    // bytes is a multiple of 16 (tables are 16-byte aligned structs)
+    const uint4 *src = static_cast<const uint4 *>(host_src);
+    uint4 *dst = static_cast<uint4 *>(dev_dst);
+    size_t nvec = (bytes + 15) / 16;
+    Blob blob;  // host staging only; its contents are copied into each launch
+    for (size_t off = 0; off < nvec; off += BLOB_VEC) {
+        size_t n = nvec - off < (size_t)BLOB_VEC ? nvec - off : (size_t)BLOB_VEC;
+        blob.n = (uint32_t)n;
+        for (size_t k = 0; k < n; ++k) blob.data[k] = src[off + k];
+        k_upload<<<1, 256, 0, s>>>(blob, dst + off);
+        note_launch();
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+// ---------------------------------------------------------------------------
+// Tile rectangle of the K-ellipse of a 2D Gaussian with covariance
+// (sxx, sxy, syy) centred at (ux, uy): the ellipse d^T Sigma^-1 d <= K^2 lies
+// in |dx| <= K sqrt(sxx), |dy| <= K sqrt(syy).  A small margin keeps the
+// float32 box a superset of the pixels the float64 reference includes.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t tile_rect(float ux, float uy, float sxx, float syy, float K, int NA, int NR,
+                                              uint2 &rect) {
+    float rx = K * sqrtf(sxx) * 1.0001f + 1e-3f;
+    float ry = K * sqrtf(syy) * 1.0001f + 1e-3f;
+    float fx0 = ceilf(ux - rx), fx1 = floorf(ux + rx);
+    float fy0 = ceilf(uy - ry), fy1 = floorf(uy + ry);
+    bool bad = !(fx0 <= fx1) || !(fy0 <= fy1) || fx1 < 0.f || fy1 < 0.f || fx0 > (float)(NA - 1) ||
+               fy0 > (float)(NR - 1);
+    if (bad) {
+        rect = make_uint2(0xffffffffu, 0xffffffffu);
+        return 0;
+    }
+    int x0 = (int)fmaxf(fx0, 0.f), x1 = (int)fminf(fx1, (float)(NA - 1));
+    int y0 = (int)fmaxf(fy0, 0.f), y1 = (int)fminf(fy1, (float)(NR - 1));
+    int tx0 = x0 / TILE, tx1 = x1 / TILE, ty0 = y0 / TILE, ty1 = y1 / TILE;
+    rect = make_uint2((uint32_t)tx0 | ((uint32_t)tx1 << 16), (uint32_t)ty0 | ((uint32_t)ty1 << 16));
+    return (uint32_t)((tx1 - tx0 + 1) * (ty1 - ty0 + 1));
+}
+
+__global__ void __launch_bounds__(256)
+k_preprocess(const float4 *__restrict__ params, const ViewDev *__restrict__ views, int V, int64_t VG, float K,
+             float eps, int norm_mode, CompRec *__restrict__ comp, ImgRec *__restrict__ img, uint2 *__restrict__ rectC,
+             uint2 *__restrict__ rectI, uint32_t *__restrict__ cntC, uint32_t *__restrict__ cntI,
+             uint32_t *__restrict__ dkey, uint32_t *__restrict__ dval) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < VG; i += stride) {
+        const int v = view_of_vg(views, V, i);
+        const ViewDev &vd = views[v];
+        const int64_t g = vd.g_off + (i - vd.vg_off);
+        const float4 p0 = __ldg(params + 3 * g);
+        const float4 p1 = __ldg(params + 3 * g + 1);
+        const float4 p2 = __ldg(params + 3 * g + 2);
+
+        // a1: activations and rotation of the Gaussian
+        const float s0 = expf(p1.x), s1 = expf(p1.y), s2 = expf(p1.z);
+        const float qn = 1.0f / sqrtf(p2.x * p2.x + p2.y * p2.y + p2.z * p2.z + p2.w * p2.w);
+        const float w = p2.x * qn, x = p2.y * qn, y = p2.z * qn, z = p2.w * qn;
+        const float o = 1.0f / (1.0f + expf(-p0.w));
+        float R[3][3];
+        R[0][0] = 1.f - 2.f * (y * y + z * z); R[0][1] = 2.f * (x * y - w * z); R[0][2] = 2.f * (x * z + w * y);
+        R[1][0] = 2.f * (x * y + w * z); R[1][1] = 1.f - 2.f * (x * x + z * z); R[1][2] = 2.f * (y * z - w * x);
+        R[2][0] = 2.f * (x * z - w * y); R[2][1] = 2.f * (y * z + w * x); R[2][2] = 1.f - 2.f * (x * x + y * y);
+
+        // a2: Sigma_r = (R_r R) diag(s^2) (R_r R)^T, the entries both planes use
+        float M[3][3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int k = 0; k < 3; ++k) M[a][k] = vd.r[a][0] * R[0][k] + vd.r[a][1] * R[1][k] + vd.r[a][2] * R[2][k];
+        const float q0 = s0 * s0, q1 = s1 * s1, q2 = s2 * s2;
+        const float S00 = M[0][0] * M[0][0] * q0 + M[0][1] * M[0][1] * q1 + M[0][2] * M[0][2] * q2;
+        const float S01 = M[0][0] * M[1][0] * q0 + M[0][1] * M[1][1] * q1 + M[0][2] * M[1][2] * q2;
+        const float S11 = M[1][0] * M[1][0] * q0 + M[1][1] * M[1][1] * q1 + M[1][2] * M[1][2] * q2;
+        const float S02 = M[0][0] * M[2][0] * q0 + M[0][1] * M[2][1] * q1 + M[0][2] * M[2][2] * q2;
+        const float S22 = M[2][0] * M[2][0] * q0 + M[2][1] * M[2][1] * q1 + M[2][2] * M[2][2] * q2;
+
+        // a2: radar coordinates relative to the beam centre
+        const float dx = p0.x - vd.c[0], dy = p0.y - vd.c[1], dz = p0.z - vd.c[2];
+        const float ra = vd.r[0][0] * dx + vd.r[0][1] * dy + vd.r[0][2] * dz;  // azimuth
+        const float re = vd.r[1][0] * dx + vd.r[1][1] * dy + vd.r[1][2] * dz;  // elevation
+        const float rr = vd.r[2][0] * dx + vd.r[2][1] * dy + vd.r[2][2] * dz;  // slant range - R0
+
+        // depth key: float32 rounding of the float64 slant-range offset, the
+        // same operations in the same order as an IEEE double evaluation of
+        // r2 . (mu - c) from left to right
+        const double ddx = __dsub_rn((double)p0.x, vd.cd[0]);
+        const double ddy = __dsub_rn((double)p0.y, vd.cd[1]);
+        const double ddz = __dsub_rn((double)p0.z, vd.cd[2]);
+        const double rho =
+            __dadd_rn(__dadd_rn(__dmul_rn(vd.r2d[0], ddx), __dmul_rn(vd.r2d[1], ddy)), __dmul_rn(vd.r2d[2], ddz));
+        const float key = __double2float_rn(rho) + 0.0f;  // -0 -> +0
+
+        // a3: computation plane (x_r, y_r), cells dA x dR tan(theta)
+        const float uCx = ra * vd.inv_dA + vd.offx;
+        const float uCy = re * vd.inv_cy + vd.offy;
+        const float cxx = S00 * vd.inv_dA * vd.inv_dA + eps;
+        const float cxy = S01 * vd.inv_dA * vd.inv_cy;
+        const float cyy = S11 * vd.inv_cy * vd.inv_cy + eps;
+        const float idC = 1.0f / (cxx * cyy - cxy * cxy);
+        // a4: imaging plane (x_r, z_r - R0), pixels dA x dR
+        const float uIy = rr * vd.inv_dR + vd.offy;
+        const float ixy = S02 * vd.inv_dA * vd.inv_dR;
+        const float iyy = S22 * vd.inv_dR * vd.inv_dR + eps;
+        const float detI = cxx * iyy - ixy * ixy;
+        const float idI = 1.0f / detI;
+        const float cn = norm_mode == 0 ? 0.15915494309189535f / sqrtf(detI) : 1.0f;
+
+        CompRec cr;
+        cr.ux = uCx; cr.uy = uCy;
+        cr.qa = -0.5f * LOG2E * (cyy * idC);
+        cr.qb = -LOG2E * (-cxy * idC);
+        cr.qc = -0.5f * LOG2E * (cxx * idC);
+        cr.o = o; cr.P = p1.w; cr.pad = 0.f;
+        ImgRec ir;
+        ir.ux = uCx; ir.uy = uIy;
+        ir.qa = -0.5f * LOG2E * (iyy * idI);
+        ir.qb = -LOG2E * (-ixy * idI);
+        ir.qc = -0.5f * LOG2E * (cxx * idI);
+        ir.cn = cn; ir.pad0 = 0.f; ir.pad1 = 0.f;
+        comp[i] = cr;
+        img[i] = ir;
+
+        // a5: tile rectangles of the K-ellipse on both planes
+        uint2 rc, ri;
+        uint32_t nc = tile_rect(uCx, uCy, cxx, cyy, K, vd.NA, vd.NR, rc);
+        uint32_t ni = tile_rect(uCx, uIy, cxx, iyy, K, vd.NA, vd.NR, ri);
+        if (!(o > 0.f) && !(o <= 0.f)) { nc = 0; ni = 0; }  // NaN parameters touch no tile
+        rectC[i] = rc;
+        rectI[i] = ri;
+        cntC[i] = nc;
+        cntI[i] = ni;
+        dkey[i] = float_order_key(key);
+        dval[i] = (uint32_t)i;
+    }
+}
+
+cudaError_t launch_preprocess(const float4 *params, const ViewDev *views, int V, int64_t VG, float K, float eps,
+                              int norm_mode, CompRec *comp, ImgRec *img, uint2 *rectC, uint2 *rectI, uint32_t *cntC,
+                              uint32_t *cntI, uint32_t *dkey, uint32_t *dval, int sms, cudaStream_t s) {
+    if (VG <= 0) return cudaSuccess;
+    int64_t blocks = (VG + 255) / 256;
+    int64_t cap = (int64_t)sms * 8;
+    if (blocks > cap) blocks = cap;
+    k_preprocess<<<(unsigned)blocks, 256, 0, s>>>(params, views, V, VG, K, eps, norm_mode, comp, img, rectC, rectI,
+                                                   cntC, cntI, dkey, dval);
+    note_launch();
+    return cudaGetLastError();
+}
+
+}  // namespace sdgr

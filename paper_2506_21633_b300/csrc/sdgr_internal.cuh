@@ -1,0 +1,186 @@
+// sdgr_internal.cuh -- device-side data layout and shared arithmetic of the
+// B300 SAR Gaussian rasterizer.  Internal to libsdgr.so.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "sdgr.h"
+
+namespace sdgr {
+
+constexpr int TILE = 16;         // tile edge (pixels); one CTA per tile
+constexpr int TILE_PIX = TILE * TILE;
+constexpr int RADIX_BITS = 8;
+constexpr int RADIX = 1 << RADIX_BITS;
+constexpr int SORT_IPB = 4096;   // items per radix-sort block
+constexpr int SORT_THREADS = 256;
+constexpr int SCAN_IPB = 4096;   // items per scan block
+constexpr int SCAN_THREADS = 256;
+
+// log2(e)
+constexpr float LOG2E = 1.4426950408889634f;
+
+// Per-view constants, written once per call by the plan upload.
+struct alignas(16) ViewDev {
+    float r[3][4];      // rows of R_r (float32): azimuth axis, elevation axis, line of sight
+    double r2d[3];      // line-of-sight row in float64 (depth key)
+    double cd[3];       // beam centre, float64
+    float c[3];         // beam centre, float32
+    float inv_dA;       // 1 / dA
+    float inv_cy;       // 1 / (dR tan(theta)) : computation-plane cell height
+    float inv_dR;       // 1 / dR
+    float offx, offy;   // NA/2 - 1/2, NR/2 - 1/2
+    int32_t NA, NR, tiles_x, tiles_y;
+    int32_t scene, N;   // scene index and its Gaussian count
+    int64_t g_off;      // first Gaussian of the scene in the parameter array
+    int64_t vg_off;     // first (view, Gaussian) slot of this view
+    int64_t pix_off;    // first pixel of this view in the image array
+    int32_t tile_off;   // first tile of this view (per plane)
+    int32_t sblk_off;   // first depth-sort block of this view
+    int32_t sblk_n;     // depth-sort blocks of this view
+    int32_t pad;
+};
+static_assert(sizeof(ViewDev) == 192, "ViewDev layout");
+
+struct alignas(16) SceneDev {
+    int64_t g_off;      // first Gaussian
+    int32_t N;          // Gaussian count
+    int32_t vstart;     // first entry in the scene->view list
+    int32_t vcount;     // views of this scene
+    int32_t pad[3];
+};
+static_assert(sizeof(SceneDev) == 32, "SceneDev layout");
+
+struct alignas(16) StatusDev {
+    int32_t code;       // sdgr_status of the device side
+    int32_t pad;
+    int64_t required;   // instances the last bin/sort needed
+    int64_t n_inst;     // instances emitted by the last bin/sort (if it fitted)
+    int64_t pad2;
+    unsigned long long pairs[2];  // sdgr_count_pairs: in-cutoff pairs per plane
+};
+
+// Computation-plane record of one (view, Gaussian).  The conic is stored
+// pre-scaled so that exp(-delta/2) = exp2(qa dx^2 + qb dx dy + qc dy^2):
+// qa = -log2e/2 C00, qb = -log2e C01, qc = -log2e/2 C11.
+struct alignas(16) CompRec {
+    float ux, uy, qa, qb;
+    float qc, o, P, pad;
+};
+
+// Imaging-plane record: centre, pre-scaled conic, normaliser c_i.
+struct alignas(16) ImgRec {
+    float ux, uy, qa, qb;
+    float qc, cn, pad0, pad1;
+};
+
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// exp2 argument of the Gaussian weight at offset (dx, dy).  Written with
+// explicit round-to-nearest intrinsics so that every kernel that evaluates a
+// pair obtains the same bits (the backward reconstructs the transmittance by
+// dividing by the very (1 - alpha) factors the forward multiplied by).
+__device__ __forceinline__ float gauss_q(float qa, float qb, float qc, float dx, float dy) {
+    float t = __fmul_rn(qa, dx);
+    t = __fmaf_rn(qb, dy, t);
+    float u = __fmul_rn(qc, dy);
+    u = __fmul_rn(u, dy);
+    return __fmaf_rn(t, dx, u);
+}
+
+// Binary search: last index k in [0, n) with key(k) <= x (keys ascending,
+// key(0) <= x).
+template <typename F>
+__device__ __forceinline__ int upper_index(int n, int64_t x, F key) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (key(mid) <= x) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ int view_of_vg(const ViewDev *views, int V, int64_t vg) {
+    return upper_index(V, vg, [&](int k) { return views[k].vg_off; });
+}
+
+__device__ __forceinline__ int view_of_tile(const ViewDev *views, int V, int64_t tile) {
+    return upper_index(V, tile, [&](int k) { return (int64_t)views[k].tile_off; });
+}
+
+__device__ __forceinline__ int view_of_sblk(const ViewDev *views, int V, int64_t b) {
+    return upper_index(V, b, [&](int k) { return (int64_t)views[k].sblk_off; });
+}
+
+__device__ __forceinline__ uint32_t float_order_key(float f) {
+    uint32_t u = __float_as_uint(f);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+
+// ---------------------------------------------------------------------------
+// Launch wrappers (defined in the kernel translation units).
+// ---------------------------------------------------------------------------
+// Counts kernel launches (sdgr_launch_count); called after every launch.
+void note_launch();
+
+cudaError_t launch_upload(const void *host_src, size_t bytes, void *dev_dst, cudaStream_t s);
+
+cudaError_t launch_preprocess(const float4 *params, const ViewDev *views, int V, int64_t VG, float K, float eps,
+                              int norm_mode, CompRec *comp, ImgRec *img, uint2 *rectC, uint2 *rectI, uint32_t *cntC,
+                              uint32_t *cntI, uint32_t *dkey, uint32_t *dval, int sms, cudaStream_t s);
+
+// exclusive scans (scratch: see scan_scratch_elems)
+size_t scan_scratch_elems(int64_t n);
+cudaError_t launch_scan_u32(const uint32_t *in, uint32_t *out, int64_t n, uint32_t *scratch, cudaStream_t s);
+cudaError_t launch_scan_u64(const unsigned long long *in, unsigned long long *out, int64_t n,
+                            unsigned long long *scratch, cudaStream_t s);
+
+// radix sort passes
+cudaError_t launch_depth_sort(const ViewDev *views, int V, int nblocks, uint32_t *k0, uint32_t *v0, uint32_t *k1,
+                              uint32_t *v1, uint32_t *hist, uint32_t *scan_scratch, cudaStream_t s);
+cudaError_t launch_inst_sort(const StatusDev *st, int64_t cap, int key_bits, uint32_t *k0, uint32_t *v0,
+                             uint32_t *k1, uint32_t *v1, uint32_t *hist, uint32_t *scan_scratch, int *final_in_1,
+                             cudaStream_t s);
+cudaError_t launch_gather_counts(const uint32_t *sorted_vg, const uint32_t *cntC, const uint32_t *cntI, int64_t VG,
+                                 unsigned long long *scnt, int sms, cudaStream_t s);
+cudaError_t launch_check_capacity(const unsigned long long *scnt, const unsigned long long *soff, int64_t VG,
+                                  int64_t cap, StatusDev *st, cudaStream_t s);
+cudaError_t launch_emit(const uint32_t *sorted_vg, const unsigned long long *soff, const uint2 *rectC,
+                        const uint2 *rectI, const ViewDev *views, int V, int64_t VG, int total_tiles,
+                        const StatusDev *st, uint32_t *keys, uint32_t *vals, int sms, cudaStream_t s);
+cudaError_t launch_ranges(const uint32_t *keys, const StatusDev *st, int64_t cap, uint2 *ranges, int sms,
+                          cudaStream_t s);
+
+// raster passes
+cudaError_t launch_intensity_fwd(const uint2 *ranges, const uint32_t *vals, const CompRec *comp, const ViewDev *views,
+                                 int V, int tiles, float cut, float Tfloor, const StatusDev *st, float *A,
+                                 float *Tstop, int32_t *last, cudaStream_t s);
+cudaError_t launch_splat_fwd(const uint2 *rangesI, const uint32_t *vals, const ImgRec *img, const CompRec *comp,
+                             const float *A, const ViewDev *views, int V, int tiles, float cut, const StatusDev *st,
+                             float *images, cudaStream_t s);
+cudaError_t launch_splat_bwd(const uint2 *rangesI, const uint32_t *vals, const ImgRec *img, const float *dLdS,
+                             const ViewDev *views, int V, int tiles, float cut, const StatusDev *st, float4 *accI,
+                             cudaStream_t s);
+cudaError_t launch_intensity_bwd(const uint2 *ranges, const uint32_t *vals, const CompRec *comp, const ImgRec *img,
+                                 const float4 *accI, const float *Tstop, const int32_t *last, const ViewDev *views,
+                                 int V, int tiles, float cut, const StatusDev *st, float4 *accC, cudaStream_t s);
+cudaError_t launch_count_pairs(const uint2 *ranges, const uint32_t *vals, const CompRec *comp, const ImgRec *img,
+                               const ViewDev *views, int V, int tiles, float cut, StatusDev *st, cudaStream_t s);
+cudaError_t launch_intensity_out(const CompRec *comp, const float *A, int64_t VG, float *I, int sms, cudaStream_t s);
+
+// parameter adjoint, optimiser, loss
+cudaError_t launch_param_bwd(const float4 *params, const ViewDev *views, const SceneDev *scenes,
+                             const int32_t *scene_views, int n_scenes, int64_t n_gauss, float eps, int norm_mode,
+                             const float *A, const float4 *accI, const float4 *accC, const StatusDev *st,
+                             float4 *grads, int sms, cudaStream_t s);
+cudaError_t launch_adam(float4 *p, const float4 *g, float4 *m, float4 *v, int64_t n4, const float *lr, float b1,
+                        float b2, float eps, int step, int sms, cudaStream_t s);
+cudaError_t launch_l1(const float *S, const float *T, int64_t npix, float *dLdS, float *loss, int sms,
+                      cudaStream_t s);
+
+}  // namespace sdgr

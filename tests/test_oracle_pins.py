@@ -477,3 +477,18 @@ def test_adam_vs_torch(orc):
         opt.step()
     for k, t in zip(groups.keys(), tp):
         assert np.allclose(p[:, groups[k]], t.detach().numpy(), rtol=1e-12, atol=1e-14)
+
+
+def test_step_matches_render_l1_grad(orc):
+    """The one-call training step equals render + L1 + adjoint."""
+    params, views = sc.config3_small(n=400, n_views=2, size=40, res=0.1)
+    rng = np.random.default_rng(12)
+    targets = [rng.uniform(0, 0.05, size=(v["NR"], v["NA"])) for v in views]
+    loss, imgs, g = orc.step(params, views, targets)
+    ref_imgs, _, _ = orc.render(params, views, culled=True)
+    ref_loss, dLdS = orc.l1(ref_imgs, targets)
+    ref_g, _ = orc.grad(params, views, dLdS, culled=True)
+    assert abs(loss - ref_loss) <= 1e-15 * max(1.0, ref_loss)
+    for a, b in zip(imgs, ref_imgs):
+        assert np.array_equal(a, b)
+    assert np.array_equal(g, ref_g)
