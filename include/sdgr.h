@@ -230,6 +230,40 @@ sdgr_status sdgr_profile_read(sdgr_ws *ws, double *ms, int64_t *launches, int32_
 sdgr_status sdgr_count_pairs(sdgr_ws *ws, int64_t *pairs, void *stream);
 int64_t sdgr_launch_count(void);
 
+/* Forward render without any device allocation, for callers that cannot
+ * allocate device memory: code running where cudaMalloc is not available to
+ * it (a plugin inside a host application that owns all device memory
+ * through its own allocator, a real-time loop that must not allocate after
+ * start-up) still has to render small scenes.  The paper has no counterpart;
+ * this is a library convenience.
+ *
+ * Same computation and outputs as sdgr_preprocess + sdgr_bin_sort +
+ * sdgr_render_fwd on one scene, but the workspace is a fixed
+ * SDGR_NOALLOC_SCRATCH_BYTES (32 MiB) array in the library's own device
+ * memory, reserved once on every GPU that loads the library and kept until
+ * the process exits.  Limits: N <= SDGR_NOALLOC_MAX_GAUSSIANS, 1 <= V <=
+ * SDGR_NOALLOC_MAX_VIEWS, sum of NA*NR <= SDGR_NOALLOC_MAX_PIXELS, every
+ * view's scene == 0; larger requests return SDGR_ERR_INVALID, and a scene
+ * whose tile instances do not fit the scratch returns SDGR_ERR_CAPACITY
+ * (images then hold zeros).
+ * params: device [N][12] float32 (16-byte aligned); views: host [V];
+ * images: device, sum of NA*NR float32, overwritten; intensity: device [V*N]
+ * float32 or NULL.
+ * The first call on a device looks up the scratch array's device address
+ * (once per device, with that device current), so make that first call
+ * before any stream capture.  The call waits for `stream` before it returns
+ * (it reads the device status word).  Every call reuses the same scratch,
+ * which keeps the previous call's contents (everything that must start at
+ * zero is cleared by the call); host threads are serialised by a lock, but
+ * work that overlaps on the GPU -- e.g. a second process context or replayed
+ * launches touching this scratch -- races. */
+#define SDGR_NOALLOC_SCRATCH_BYTES (32u << 20)
+#define SDGR_NOALLOC_MAX_GAUSSIANS 16384
+#define SDGR_NOALLOC_MAX_VIEWS 4
+#define SDGR_NOALLOC_MAX_PIXELS 262144
+sdgr_status sdgr_render_fwd_noalloc(const float *params, int64_t N, const sdgr_view *views, int32_t V,
+                                    const sdgr_cfg *cfg, float *images, float *intensity, void *stream);
+
 /* Static, NUL-terminated description of a status code. */
 const char *sdgr_status_string(sdgr_status s);
 

@@ -21,7 +21,7 @@ EXPORTS = (
     "sdgr_caps_for", "sdgr_workspace_size", "sdgr_ws_create", "sdgr_ws_destroy", "sdgr_preprocess",
     "sdgr_bin_sort", "sdgr_render_fwd", "sdgr_render_bwd", "sdgr_adam_step", "sdgr_l1_loss",
     "sdgr_read_status", "sdgr_status_string", "sdgr_profile_enable", "sdgr_profile_read",
-    "sdgr_count_pairs", "sdgr_launch_count",
+    "sdgr_count_pairs", "sdgr_launch_count", "sdgr_render_fwd_noalloc",
 )
 
 STAGES = ("preprocess", "depth_sort", "bin", "intensity_fwd", "splat_fwd", "splat_bwd", "intensity_bwd",
@@ -81,6 +81,7 @@ def lib():
         L.sdgr_render_bwd.argtypes = [vp, vp, vp, i32, vp]
         L.sdgr_count_pairs.argtypes = [vp, P(ctypes.c_int64), vp]
         L.sdgr_launch_count.argtypes = []
+        L.sdgr_render_fwd_noalloc.argtypes = [vp, i64, P(SdgrView), i32, P(SdgrCfg), vp, vp, vp]
         L.sdgr_adam_step.argtypes = [vp, vp, vp, vp, i64, P(ctypes.c_float), f32, f32, f32, i32, vp]
         L.sdgr_l1_loss.argtypes = [vp, vp, i64, vp, vp, vp]
         L.sdgr_read_status.argtypes = [vp, P(ctypes.c_int64)]
