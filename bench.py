@@ -395,7 +395,8 @@ def run_sdgr(args):
         "config": {"workload": desc, "gaussians": int(params.shape[0]), "views_per_step": V,
                    "image": [views[0]["NR"], views[0]["NA"]], "parallelism": "replicas" if world > 1 else "single",
                    "l2": "inputs larger than L2 (workspace %.1f GB per step)" % (r.workspace_bytes() / 1e9),
-                   "pairs_per_step": {"computation_plane": pairs[0], "imaging_plane": pairs[1]}},
+                   "pairs_per_step": {"computation_plane": pairs[0], "imaging_plane": pairs[1]},
+                   "instances_per_step": int(r.n_inst)},
         "gaussian_pixel_evals_per_s": round((pairs[0] + pairs[1]) * world * args.steps / (ms_max / 1e3), 1),
         "plain": plain, "e2e": e2e, "roofline": roof, "gpu_launches": int(launches), "clocks": clocks,
     }

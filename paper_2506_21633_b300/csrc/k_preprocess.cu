@@ -52,8 +52,8 @@ cudaError_t launch_upload(const void *host_src, size_t bytes, void *dev_dst, cud
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ uint32_t tile_rect(float ux, float uy, float sxx, float syy, float K, int NA, int NR,
                                               uint2 &rect) {
-    float rx = K * sqrtf(sxx) * 1.0001f + 1e-3f;
-    float ry = K * sqrtf(syy) * 1.0001f + 1e-3f;
+    float rx = ellipse_ry(sxx, K);
+    float ry = ellipse_ry(syy, K);
     float fx0 = ceilf(ux - rx), fx1 = floorf(ux + rx);
     float fy0 = ceilf(uy - ry), fy1 = floorf(uy + ry);
     bool bad = !(fx0 <= fx1) || !(fy0 <= fy1) || fx1 < 0.f || fy1 < 0.f || fx0 > (float)(NA - 1) ||
@@ -142,13 +142,13 @@ k_preprocess(const float4 *__restrict__ params, const ViewDev *__restrict__ view
         cr.qa = -0.5f * LOG2E * (cyy * idC);
         cr.qb = -LOG2E * (-cxy * idC);
         cr.qc = -0.5f * LOG2E * (cxx * idC);
-        cr.o = o; cr.P = p1.w; cr.pad = 0.f;
+        cr.o = o; cr.P = p1.w; cr.ry = ellipse_ry(cyy, K);
         ImgRec ir;
         ir.ux = uCx; ir.uy = uIy;
         ir.qa = -0.5f * LOG2E * (iyy * idI);
         ir.qb = -LOG2E * (-ixy * idI);
         ir.qc = -0.5f * LOG2E * (cxx * idI);
-        ir.cn = cn; ir.pad0 = 0.f; ir.pad1 = 0.f;
+        ir.cn = cn; ir.ry = ellipse_ry(iyy, K); ir.pad1 = 0.f;
         comp[i] = cr;
         img[i] = ir;
 

@@ -5,18 +5,29 @@
 //
 // One CTA per 16x16 tile, one thread per pixel (ray).  The tile's instance
 // list is staged through shared memory in batches of 256 Gaussian records.
-// Per-Gaussian sums over the tile's pixels are reduced across each warp with
-// shuffles, then across warps in shared memory, then added to the
-// per-(view, Gaussian) accumulators with one atomic per tile and Gaussian.
+//
+// Sums over the tile's pixels per Gaussian (the ray sums A_i of the intensity
+// pass and the six moments of the adjoints) use a two-phase transpose
+// instead of warp-shuffle reductions: in phase 1 every thread (pixel) walks a
+// sub-batch of 32 Gaussians in list order and writes each pair's weight into
+// a 32 x 256 shared-memory table; in phase 2 eight threads per Gaussian sum
+// that Gaussian's row of the table (two columns each, only over the rows its
+// K-ellipse can reach), and three shuffles combine the eight partial sums.
+// The table's row stride (264 floats) makes both the phase-1 stores and the
+// phase-2 loads free of bank conflicts.  A warp (two pixel rows) skips a
+// Gaussian whose K-ellipse misses both of its rows.
 #include "sdgr_internal.cuh"
 
 namespace sdgr {
 
-constexpr int BATCH = 256;
+constexpr int BATCH = 256;    // Gaussian records staged per batch
+constexpr int SUB = 32;       // Gaussians per weight table
+constexpr int WSTRIDE = 264;  // row stride of the weight table (floats)
 
 struct TileCtx {
     int v;
-    int px, py;
+    int x0, y0;  // pixel coordinates of the tile's first pixel
+    int px, py;  // this thread's pixel
     bool inside;
     int64_t pix;
 };
@@ -26,18 +37,79 @@ __device__ __forceinline__ TileCtx tile_ctx(const ViewDev *views, int V, int til
     c.v = view_of_tile(views, V, tile);
     const ViewDev &vd = views[c.v];
     const int lt = tile - vd.tile_off;
-    const int tx = lt % vd.tiles_x, ty = lt / vd.tiles_x;
-    c.px = tx * TILE + (threadIdx.x & (TILE - 1));
-    c.py = ty * TILE + (threadIdx.x / TILE);
+    c.x0 = (lt % vd.tiles_x) * TILE;
+    c.y0 = (lt / vd.tiles_x) * TILE;
+    c.px = c.x0 + (threadIdx.x & (TILE - 1));
+    c.py = c.y0 + (threadIdx.x / TILE);
     c.inside = c.px < vd.NA && c.py < vd.NR;
     c.pix = vd.pix_off + (int64_t)c.py * vd.NA + c.px;
     return c;
 }
 
-__device__ __forceinline__ float warp_sum(float x) {
+// Tile-local rows [x, y] that the K-ellipse of a Gaussian centred at row uy
+// with bounding-box half-height ry can reach (empty when x > y).
+__device__ __forceinline__ int2 tile_rows(float uy, float ry, int y0) {
+    float lo = ceilf(uy - ry) - (float)y0, hi = floorf(uy + ry) - (float)y0;
+    lo = fminf(fmaxf(lo, 0.f), 16.f);
+    hi = fminf(fmaxf(hi, -1.f), 15.f);
+    if (!(lo <= 16.f)) lo = 0.f;  // NaN centre: keep every row, the pair test decides
+    if (!(hi >= -1.f)) hi = 15.f;
+    return make_int2((int)lo, (int)hi);
+}
+
+// Does the ellipse reach either of the two rows of warp w?
+__device__ __forceinline__ bool warp_rows_hit(int2 rows, int warp) {
+    return rows.y >= 2 * warp && rows.x <= 2 * warp + 1;
+}
+
+// Phase 2, one sum: every lane of the group of eight returns the sum of
+// Gaussian (threadIdx.x / 8)'s table row over the rows [rows.x, rows.y].
+__device__ __forceinline__ float table_sum(const float *W, int2 rows) {
+    const int j = threadIdx.x >> 3, c = threadIdx.x & 7;
+    const float *w = W + j * WSTRIDE + c;
+    float s = 0.f;
+    for (int r = rows.x; r <= rows.y; ++r) s += w[r * TILE] + w[r * TILE + 8];
+    s += __shfl_xor_sync(0xffffffffu, s, 1);
+    s += __shfl_xor_sync(0xffffffffu, s, 2);
+    s += __shfl_xor_sync(0xffffffffu, s, 4);
+    return s;
+}
+
+// Phase 2, six moments of the weights w over the pixels: sum w, w dx, w dy,
+// w dx^2, w dx dy, w dy^2 with (dx, dy) = pixel - centre.  dx0 = offset of
+// the thread's first column (x0 + c - ux), dy0 = y0 - uy.
+__device__ __forceinline__ void table_moments(const float *W, int2 rows, float dx0, float dy0, float m[6]) {
+    const int j = threadIdx.x >> 3, c = threadIdx.x & 7;
+    const float *w = W + j * WSTRIDE + c;
+    const float dx1 = dx0 + 8.f;
+    float m0 = 0.f, mx = 0.f, my = 0.f, mxx = 0.f, mxy = 0.f, myy = 0.f;
+    for (int r = rows.x; r <= rows.y; ++r) {
+        const float dy = dy0 + (float)r;
+        const float w0 = w[r * TILE], w1 = w[r * TILE + 8];
+        const float a0 = w0 * dx0, a1 = w1 * dx1;
+        const float ws = w0 + w1, as = a0 + a1;
+        m0 += ws;
+        mx += as;
+        my = fmaf(ws, dy, my);
+        mxx = fmaf(a0, dx0, fmaf(a1, dx1, mxx));
+        mxy = fmaf(as, dy, mxy);
+        myy = fmaf(ws * dy, dy, myy);
+    }
+    m[0] = m0; m[1] = mx; m[2] = my; m[3] = mxx; m[4] = mxy; m[5] = myy;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-    return x;
+    for (int q = 0; q < 6; ++q) {
+        m[q] += __shfl_xor_sync(0xffffffffu, m[q], 1);
+        m[q] += __shfl_xor_sync(0xffffffffu, m[q], 2);
+        m[q] += __shfl_xor_sync(0xffffffffu, m[q], 4);
+    }
+}
+
+__device__ __forceinline__ void add_moments(float4 *acc, uint32_t vg, const float m[6]) {
+    if (m[0] != 0.f || m[1] != 0.f || m[2] != 0.f || m[3] != 0.f || m[4] != 0.f || m[5] != 0.f) {
+        float *p = reinterpret_cast<float *>(acc + 2 * (size_t)vg);
+#pragma unroll
+        for (int q = 0; q < 6; ++q) atomicAdd(p + q, m[q]);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -52,10 +124,12 @@ k_intensity_fwd(const uint2 *__restrict__ ranges, const uint32_t *__restrict__ v
                 const ViewDev *__restrict__ views, int V, float cut, float Tfloor, const StatusDev *st,
                 float *__restrict__ A, float *__restrict__ Tstop, int32_t *__restrict__ last) {
     if (st->code != SDGR_OK) return;
-    __shared__ float4 sA[BATCH], sB[BATCH];
+    __shared__ float4 sA[BATCH];
+    __shared__ float2 sB[BATCH];
+    __shared__ int2 sR[BATCH];
     __shared__ uint32_t sid[BATCH];
-    __shared__ float sacc[BATCH];
-    const int t = threadIdx.x, lane = t & 31;
+    __shared__ float W[SUB * WSTRIDE];
+    const int t = threadIdx.x, warp = t >> 5;
     const TileCtx c = tile_ctx(views, V, blockIdx.x);
     const uint2 r = ranges[blockIdx.x];
     const float fx = (float)c.px, fy = (float)c.py;
@@ -64,40 +138,45 @@ k_intensity_fwd(const uint2 *__restrict__ ranges, const uint32_t *__restrict__ v
     bool done = !c.inside;
     for (uint32_t base = r.x; base < r.y; base += BATCH) {
         if (__syncthreads_count(done) == (int)blockDim.x) break;
-        const uint32_t j = base + t;
-        if (j < r.y) {
-            const uint32_t vg = vals[j];
+        const uint32_t jload = base + t;
+        if (jload < r.y) {
+            const uint32_t vg = vals[jload];
             const float4 *cp = reinterpret_cast<const float4 *>(comp + vg);
-            sA[t] = cp[0];
-            sB[t] = cp[1];
+            const float4 c0 = cp[0], c1 = cp[1];
+            sA[t] = c0;
+            sB[t] = make_float2(c1.x, c1.y);
+            sR[t] = tile_rows(c0.y, c1.w, c.y0);
             sid[t] = vg;
         }
-        sacc[t] = 0.f;
         __syncthreads();
         const int nb = min(BATCH, (int)(r.y - base));
-        for (int k = 0; k < nb; ++k) {
-            float contrib = 0.f;
-            if (!done) {
-                const float4 a = sA[k];
-                const float4 b = sB[k];
-                const float dx = __fsub_rn(fx, a.x), dy = __fsub_rn(fy, a.y);
-                const float q = gauss_q(a.z, a.w, b.x, dx, dy);
-                if (q >= cut) {
-                    const float alpha = __fmul_rn(b.y, ex2_approx(q));
-                    contrib = __fmul_rn(alpha, T);
-                    Tprev = T;
-                    lastj = (int32_t)(base + k + 1);
-                    T = __fmul_rn(T, __fsub_rn(1.f, alpha));
-                    if (T < Tfloor) done = true;
+        for (int sub = 0; sub < nb; sub += SUB) {
+            const int ns = min(SUB, nb - sub);
+            for (int jj = 0; jj < ns; ++jj) {
+                const int k = sub + jj;
+                float contrib = 0.f;
+                if (warp_rows_hit(sR[k], warp) && !done) {
+                    const float4 a = sA[k];
+                    const float2 b = sB[k];
+                    const float dx = __fsub_rn(fx, a.x), dy = __fsub_rn(fy, a.y);
+                    const float q = gauss_q(a.z, a.w, b.x, dx, dy);
+                    if (q >= cut) {
+                        const float alpha = __fmul_rn(b.y, ex2_approx(q));
+                        contrib = __fmul_rn(alpha, T);
+                        Tprev = T;
+                        lastj = (int32_t)(base + k + 1);
+                        T = __fmul_rn(T, __fsub_rn(1.f, alpha));
+                        if (T < Tfloor) done = true;
+                    }
                 }
+                W[jj * WSTRIDE + t] = contrib;
             }
-            if (__any_sync(0xffffffffu, contrib != 0.f)) {
-                const float s = warp_sum(contrib);
-                if (lane == 0 && s != 0.f) atomicAdd(&sacc[k], s);
-            }
+            __syncthreads();
+            const int j = t >> 3;
+            const float s = table_sum(W, j < ns ? sR[sub + j] : make_int2(0, -1));
+            if ((t & 7) == 0 && j < ns && s != 0.f) atomicAdd(&A[sid[sub + j]], s);
+            __syncthreads();
         }
-        __syncthreads();
-        if (t < nb && sacc[t] != 0.f) atomicAdd(&A[sid[t]], sacc[t]);
     }
     if (c.inside) {
         Tstop[c.pix] = Tprev;
@@ -116,6 +195,7 @@ cudaError_t launch_intensity_fwd(const uint2 *ranges, const uint32_t *vals, cons
 
 // ---------------------------------------------------------------------------
 // a8: imaging splat.  S[pixel] = sum_i c_i exp(-delta_I/2) I_i, I_i = P_i A_i.
+// Each pixel gathers; no reduction is needed.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256)
 k_splat_fwd(const uint2 *__restrict__ rangesI, const uint32_t *__restrict__ vals, const ImgRec *__restrict__ img,
@@ -123,7 +203,8 @@ k_splat_fwd(const uint2 *__restrict__ rangesI, const uint32_t *__restrict__ vals
             float cut, const StatusDev *st, float *__restrict__ images) {
     __shared__ float4 sA[BATCH];
     __shared__ float2 sB[BATCH];
-    const int t = threadIdx.x;
+    __shared__ int2 sR[BATCH];
+    const int t = threadIdx.x, warp = t >> 5;
     const TileCtx c = tile_ctx(views, V, blockIdx.x);
     const bool ok = st->code == SDGR_OK;
     const uint2 r = ok ? rangesI[blockIdx.x] : make_uint2(0u, 0u);
@@ -138,10 +219,12 @@ k_splat_fwd(const uint2 *__restrict__ rangesI, const uint32_t *__restrict__ vals
             const float4 i0 = ip[0], i1 = ip[1];
             sA[t] = i0;
             sB[t] = make_float2(i1.x, i1.y * comp[vg].P * A[vg]);
+            sR[t] = tile_rows(i0.y, i1.z, c.y0);
         }
         __syncthreads();
         const int nb = min(BATCH, (int)(r.y - base));
         for (int k = 0; k < nb; ++k) {
+            if (!warp_rows_hit(sR[k], warp)) continue;
             const float4 a = sA[k];
             const float2 b = sB[k];
             const float q = gauss_q(a.z, a.w, b.x, fx - a.x, fy - a.y);
@@ -161,50 +244,6 @@ cudaError_t launch_splat_fwd(const uint2 *rangesI, const uint32_t *vals, const I
 }
 
 // ---------------------------------------------------------------------------
-// Shared-memory accumulation of six per-Gaussian moments of a per-pair
-// weight w over the tile's pixels: sum w, w dx, w dy, w dx^2, w dx dy, w dy^2.
-// ---------------------------------------------------------------------------
-struct Moments {
-    float m[6];
-};
-
-__device__ __forceinline__ void moments_of(float w, float dx, float dy, Moments &M) {
-    const float wx = w * dx, wy = w * dy;
-    M.m[0] = w;
-    M.m[1] = wx;
-    M.m[2] = wy;
-    M.m[3] = wx * dx;
-    M.m[4] = wx * dy;
-    M.m[5] = wy * dy;
-}
-
-__device__ __forceinline__ void reduce_moments(Moments &M, bool any, int lane, float (*sacc)[BATCH], int k) {
-    if (__any_sync(0xffffffffu, any)) {
-#pragma unroll
-        for (int q = 0; q < 6; ++q) M.m[q] = warp_sum(M.m[q]);
-        if (lane == 0) {
-#pragma unroll
-            for (int q = 0; q < 6; ++q)
-                if (M.m[q] != 0.f) atomicAdd(&sacc[q][k], M.m[q]);
-        }
-    }
-}
-
-__device__ __forceinline__ void flush_moments(float (*sacc)[BATCH], int t, uint32_t vg, float4 *acc) {
-    const float a0 = sacc[0][t], a1 = sacc[1][t], a2 = sacc[2][t], a3 = sacc[3][t], a4 = sacc[4][t],
-                a5 = sacc[5][t];
-    if (a0 != 0.f || a1 != 0.f || a2 != 0.f || a3 != 0.f || a4 != 0.f || a5 != 0.f) {
-        float *p = reinterpret_cast<float *>(acc + 2 * (size_t)vg);
-        atomicAdd(p + 0, a0);
-        atomicAdd(p + 1, a1);
-        atomicAdd(p + 2, a2);
-        atomicAdd(p + 3, a3);
-        atomicAdd(p + 4, a4);
-        atomicAdd(p + 5, a5);
-    }
-}
-
-// ---------------------------------------------------------------------------
 // a10: adjoint of the imaging splat.  Per (view, Gaussian) the moments of
 // w = dL/dS * exp(-delta_I/2); the parameter adjoint turns them into
 // dL/dI = c M0, dL/du_I, dL/dconic_I and dL/dc.
@@ -216,39 +255,50 @@ k_splat_bwd(const uint2 *__restrict__ rangesI, const uint32_t *__restrict__ vals
     if (st->code != SDGR_OK) return;
     __shared__ float4 sA[BATCH];
     __shared__ float sC[BATCH];
+    __shared__ int2 sR[BATCH];
     __shared__ uint32_t sid[BATCH];
-    __shared__ float sacc[6][BATCH];
-    const int t = threadIdx.x, lane = t & 31;
+    __shared__ float W[SUB * WSTRIDE];
+    const int t = threadIdx.x, warp = t >> 5;
     const TileCtx c = tile_ctx(views, V, blockIdx.x);
     const uint2 r = rangesI[blockIdx.x];
     const float fx = (float)c.px, fy = (float)c.py;
     const float g = c.inside ? dLdS[c.pix] : 0.f;
     if (__syncthreads_count(g != 0.f) == 0) return;
+    const float colx = (float)(c.x0 + (t & 7));
     for (uint32_t base = r.x; base < r.y; base += BATCH) {
         __syncthreads();
-        const uint32_t j = base + t;
-        if (j < r.y) {
-            const uint32_t vg = vals[j];
+        const uint32_t jload = base + t;
+        if (jload < r.y) {
+            const uint32_t vg = vals[jload];
             const float4 *ip = reinterpret_cast<const float4 *>(img + vg);
-            sA[t] = ip[0];
-            sC[t] = ip[1].x;
+            const float4 i0 = ip[0], i1 = ip[1];
+            sA[t] = i0;
+            sC[t] = i1.x;
+            sR[t] = tile_rows(i0.y, i1.z, c.y0);
             sid[t] = vg;
         }
-#pragma unroll
-        for (int q = 0; q < 6; ++q) sacc[q][t] = 0.f;
         __syncthreads();
         const int nb = min(BATCH, (int)(r.y - base));
-        for (int k = 0; k < nb; ++k) {
-            const float4 a = sA[k];
-            const float dx = fx - a.x, dy = fy - a.y;
-            const float q = gauss_q(a.z, a.w, sC[k], dx, dy);
-            Moments M;
-            const bool hit = q >= cut && g != 0.f;
-            moments_of(hit ? g * ex2_approx(q) : 0.f, dx, dy, M);
-            reduce_moments(M, hit, lane, sacc, k);
+        for (int sub = 0; sub < nb; sub += SUB) {
+            const int ns = min(SUB, nb - sub);
+            for (int jj = 0; jj < ns; ++jj) {
+                const int k = sub + jj;
+                float w = 0.f;
+                if (warp_rows_hit(sR[k], warp)) {
+                    const float4 a = sA[k];
+                    const float q = gauss_q(a.z, a.w, sC[k], fx - a.x, fy - a.y);
+                    if (q >= cut) w = g * ex2_approx(q);
+                }
+                W[jj * WSTRIDE + t] = w;
+            }
+            __syncthreads();
+            const int j = t >> 3;
+            float m[6];
+            const float4 a = sA[sub + (j < ns ? j : 0)];
+            table_moments(W, j < ns ? sR[sub + j] : make_int2(0, -1), colx - a.x, (float)c.y0 - a.y, m);
+            if ((t & 7) == 0 && j < ns) add_moments(accI, sid[sub + j], m);
+            __syncthreads();
         }
-        __syncthreads();
-        if (t < nb) flush_moments(sacc, t, sid[t], accI);
     }
 }
 
@@ -268,8 +318,9 @@ cudaError_t launch_splat_bwd(const uint2 *rangesI, const uint32_t *vals, const I
 // its list back to front from the last in-cutoff Gaussian the forward pass
 // recorded: B by the suffix recursion B <- chat alpha + (1 - alpha) B, T by
 // undoing the forward products (T_i = T_{i+1} / (1 - alpha_i), with the same
-// float bits of alpha; every factor is > 0 because T_{i+1} >= Tfloor).
-// Per (view, Gaussian) the moments of w = dL/dalpha exp(-delta_C/2).
+// float bits of alpha and the same skipped pairs as the forward; every
+// factor is > 0 because T_{i+1} >= Tfloor).  Per (view, Gaussian) the
+// moments of w = dL/dalpha exp(-delta_C/2).
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256)
 k_intensity_bwd(const uint2 *__restrict__ ranges, const uint32_t *__restrict__ vals, const CompRec *__restrict__ comp,
@@ -277,11 +328,13 @@ k_intensity_bwd(const uint2 *__restrict__ ranges, const uint32_t *__restrict__ v
                 const int32_t *__restrict__ last, const ViewDev *__restrict__ views, int V, float cut,
                 const StatusDev *st, float4 *__restrict__ accC) {
     if (st->code != SDGR_OK) return;
-    __shared__ float4 sA[BATCH], sB[BATCH];
+    __shared__ float4 sA[BATCH];
+    __shared__ float4 sB[BATCH];
+    __shared__ int2 sR[BATCH];
     __shared__ uint32_t sid[BATCH];
-    __shared__ float sacc[6][BATCH];
+    __shared__ float W[SUB * WSTRIDE];
     __shared__ int smax;
-    const int t = threadIdx.x, lane = t & 31;
+    const int t = threadIdx.x, warp = t >> 5;
     const TileCtx c = tile_ctx(views, V, blockIdx.x);
     const uint2 r = ranges[blockIdx.x];
     const float fx = (float)c.px, fy = (float)c.py;
@@ -292,6 +345,7 @@ k_intensity_bwd(const uint2 *__restrict__ ranges, const uint32_t *__restrict__ v
     if (mylast > 0) atomicMax(&smax, mylast);
     __syncthreads();
     const int hi0 = smax;
+    const float colx = (float)(c.x0 + (t & 7));
     float B = 0.f;
     bool first = true;
     for (int hi = hi0; hi > (int)r.x; hi -= BATCH) {
@@ -305,39 +359,42 @@ k_intensity_bwd(const uint2 *__restrict__ ranges, const uint32_t *__restrict__ v
             const float dLdI = accI[2 * (size_t)vg].x * img[vg].cn;
             sA[t] = c0;
             sB[t] = make_float4(c1.x, c1.y, dLdI * c1.z, 0.f);
+            sR[t] = tile_rows(c0.y, c1.w, c.y0);
             sid[t] = vg;
         }
-#pragma unroll
-        for (int q = 0; q < 6; ++q) sacc[q][t] = 0.f;
         __syncthreads();
-        for (int k = nb - 1; k >= 0; --k) {
-            const int j = lo + k;
-            float w = 0.f, dx = 0.f, dy = 0.f;
-            bool hit = false;
-            if (j < mylast) {
-                const float4 a = sA[k];
-                const float4 b = sB[k];
-                dx = __fsub_rn(fx, a.x);
-                dy = __fsub_rn(fy, a.y);
-                const float q = gauss_q(a.z, a.w, b.x, dx, dy);
-                if (q >= cut) {
-                    const float e = ex2_approx(q);
-                    const float alpha = __fmul_rn(b.y, e);
-                    if (!first) T = __fdiv_rn(T, __fsub_rn(1.f, alpha));
-                    first = false;
-                    const float chat = b.z;
-                    const float ga = T * (chat - B);
-                    B = fmaf(chat, alpha, (1.f - alpha) * B);
-                    w = ga * e;
-                    hit = true;
+        for (int send = nb; send > 0; send -= SUB) {
+            const int sub = max(0, send - SUB);
+            const int ns = send - sub;
+            for (int jj = ns - 1; jj >= 0; --jj) {
+                const int k = sub + jj;
+                float w = 0.f;
+                if (warp_rows_hit(sR[k], warp) && lo + k < mylast) {
+                    const float4 a = sA[k];
+                    const float4 b = sB[k];
+                    const float dx = __fsub_rn(fx, a.x), dy = __fsub_rn(fy, a.y);
+                    const float q = gauss_q(a.z, a.w, b.x, dx, dy);
+                    if (q >= cut) {
+                        const float e = ex2_approx(q);
+                        const float alpha = __fmul_rn(b.y, e);
+                        if (!first) T = __fdiv_rn(T, __fsub_rn(1.f, alpha));
+                        first = false;
+                        const float chat = b.z;
+                        const float ga = T * (chat - B);
+                        B = fmaf(chat, alpha, (1.f - alpha) * B);
+                        w = ga * e;
+                    }
                 }
+                W[jj * WSTRIDE + t] = w;
             }
-            Moments M;
-            moments_of(w, dx, dy, M);
-            reduce_moments(M, hit, lane, sacc, k);
+            __syncthreads();
+            const int j = t >> 3;
+            float m[6];
+            const float4 a = sA[sub + (j < ns ? j : 0)];
+            table_moments(W, j < ns ? sR[sub + j] : make_int2(0, -1), colx - a.x, (float)c.y0 - a.y, m);
+            if ((t & 7) == 0 && j < ns) add_moments(accC, sid[sub + j], m);
+            __syncthreads();
         }
-        __syncthreads();
-        if (t < nb) flush_moments(sacc, t, sid[t], accC);
     }
 }
 

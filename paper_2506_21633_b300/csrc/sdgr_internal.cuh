@@ -63,17 +63,23 @@ struct alignas(16) StatusDev {
 
 // Computation-plane record of one (view, Gaussian).  The conic is stored
 // pre-scaled so that exp(-delta/2) = exp2(qa dx^2 + qb dx dy + qc dy^2):
-// qa = -log2e/2 C00, qb = -log2e C01, qc = -log2e/2 C11.
+// qa = -log2e/2 C00, qb = -log2e C01, qc = -log2e/2 C11.  ry is the
+// half-height (pixels) of the K-ellipse's bounding box, with the same margin
+// as the tile rectangles, so a kernel can skip rows the ellipse misses.
 struct alignas(16) CompRec {
     float ux, uy, qa, qb;
-    float qc, o, P, pad;
+    float qc, o, P, ry;
 };
 
-// Imaging-plane record: centre, pre-scaled conic, normaliser c_i.
+// Imaging-plane record: centre, pre-scaled conic, normaliser c_i, ry.
 struct alignas(16) ImgRec {
     float ux, uy, qa, qb;
-    float qc, cn, pad0, pad1;
+    float qc, cn, ry, pad1;
 };
+
+// Half-height of the K-ellipse's bounding box for a 2D covariance whose yy
+// entry is syy (same margin as the tile rectangles).
+__device__ __forceinline__ float ellipse_ry(float syy, float K) { return K * sqrtf(syy) * 1.0001f + 1e-3f; }
 
 __device__ __forceinline__ float ex2_approx(float x) {
     float y;
