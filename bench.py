@@ -58,8 +58,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["sdgr", "reference"], default="sdgr")
-    ap.add_argument("--workload", choices=["config3", "small"], default="config3",
-                    help="small: a reduced scene for quick checks (not a bench line)")
+    ap.add_argument("--workload", choices=["config3", "medium", "small"], default="config3",
+                    help="medium: the config-3 scene with 8 views (profiling); small: a reduced scene for "
+                         "quick checks (neither is a bench line)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -206,7 +207,11 @@ def kernel_traffic(stage):
 # ---------------------------------------------------------------------------
 def workload(name, rank):
     import sdgr_scenes as sc
-    if name == "small":
+    if name == "medium":
+        params, views = sc.config3()
+        views = views[:8]
+        desc = "profiling case: the 300k-Gaussian config-3 scene, 8 of its 64 views (not the headline workload)"
+    elif name == "small":
         params, views = sc.config3(n=30000, n_views=8, size=256, res=0.04)
         desc = "reduced check: 30k Gaussians, 8 views, 256x256 (not the headline workload)"
     else:

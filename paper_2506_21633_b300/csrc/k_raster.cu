@@ -39,8 +39,11 @@ __device__ __forceinline__ TileCtx tile_ctx(const ViewDev *views, int V, int til
     const int lt = tile - vd.tile_off;
     c.x0 = (lt % vd.tiles_x) * TILE;
     c.y0 = (lt / vd.tiles_x) * TILE;
-    c.px = c.x0 + (threadIdx.x & (TILE - 1));
-    c.py = c.y0 + (threadIdx.x / TILE);
+    // warp w covers the 8x4 pixel block (columns 8 (w & 1) .. +7, rows
+    // 4 (w >> 1) .. +3); lane l sits at column l & 7, row l >> 3 of it
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    c.px = c.x0 + 8 * (w & 1) + (l & 7);
+    c.py = c.y0 + 4 * (w >> 1) + (l >> 3);
     c.inside = c.px < vd.NA && c.py < vd.NR;
     c.pix = vd.pix_off + (int64_t)c.py * vd.NA + c.px;
     return c;
@@ -57,18 +60,49 @@ __device__ __forceinline__ int2 tile_rows(float uy, float ry, int y0) {
     return make_int2((int)lo, (int)hi);
 }
 
-// Does the ellipse reach either of the two rows of warp w?
-__device__ __forceinline__ bool warp_rows_hit(int2 rows, int warp) {
-    return rows.y >= 2 * warp && rows.x <= 2 * warp + 1;
+// Tile-local columns the K-ellipse can reach, from its conic: with the
+// pre-scaled conic (qa, qb, qc) and cut = -K^2 log2(e) / 2, the bounding-box
+// half-width is K sqrt(Sigma_xx) = sqrt(4 cut qc / (4 qa qc - qb^2)).
+__device__ __forceinline__ int2 tile_cols(float ux, float qa, float qb, float qc, float cut, int x0) {
+    const float rx = sqrtf(4.f * cut * qc / (4.f * qa * qc - qb * qb)) * 1.0001f + 1e-3f;
+    return tile_rows(ux, rx, x0);
 }
+
+// Bit w set when the K-ellipse's box reaches the pixel block of warp w.
+__device__ __forceinline__ uint32_t warp_mask(int2 rows, int2 cols) {
+    uint32_t m = 0;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) {
+        const int r0 = 4 * (w >> 1), c0 = 8 * (w & 1);
+        if (rows.y >= r0 && rows.x <= r0 + 3 && cols.y >= c0 && cols.x <= c0 + 7) m |= 1u << w;
+    }
+    return m;
+}
+
+__device__ __forceinline__ bool warp_hit(uint32_t mask, int warp) { return (mask >> warp) & 1u; }
+
+// Offset in the weight-table row of tile-local row r, column c (c < 8); the
+// pixel in column c + 8 sits 32 entries further.
+__device__ __forceinline__ int table_idx(int r, int c) { return 64 * (r >> 2) + 8 * (r & 3) + c; }
 
 // Phase 2, one sum: every lane of the group of eight returns the sum of
 // Gaussian (threadIdx.x / 8)'s table row over the rows [rows.x, rows.y].
+// The four groups of a warp loop over the union of their row ranges (rows
+// outside a group's range hold zeros), so every lane reads the same row at
+// the same time: no divergence, no bank conflicts.
+__device__ __forceinline__ int2 warp_union(int2 rows) {
+    return make_int2(__reduce_min_sync(0xffffffffu, rows.x), __reduce_max_sync(0xffffffffu, rows.y));
+}
+
 __device__ __forceinline__ float table_sum(const float *W, int2 rows) {
+    rows = warp_union(rows);
     const int j = threadIdx.x >> 3, c = threadIdx.x & 7;
-    const float *w = W + j * WSTRIDE + c;
+    const float *w = W + j * WSTRIDE + c;  // thread index of pixel (row r, column c) = table_idx(r, c)
     float s = 0.f;
-    for (int r = rows.x; r <= rows.y; ++r) s += w[r * TILE] + w[r * TILE + 8];
+    for (int r = rows.x; r <= rows.y; ++r) {
+        const int i = table_idx(r, 0);
+        s += w[i] + w[i + 32];
+    }
     s += __shfl_xor_sync(0xffffffffu, s, 1);
     s += __shfl_xor_sync(0xffffffffu, s, 2);
     s += __shfl_xor_sync(0xffffffffu, s, 4);
@@ -79,13 +113,15 @@ __device__ __forceinline__ float table_sum(const float *W, int2 rows) {
 // w dx^2, w dx dy, w dy^2 with (dx, dy) = pixel - centre.  dx0 = offset of
 // the thread's first column (x0 + c - ux), dy0 = y0 - uy.
 __device__ __forceinline__ void table_moments(const float *W, int2 rows, float dx0, float dy0, float m[6]) {
+    rows = warp_union(rows);
     const int j = threadIdx.x >> 3, c = threadIdx.x & 7;
     const float *w = W + j * WSTRIDE + c;
     const float dx1 = dx0 + 8.f;
     float m0 = 0.f, mx = 0.f, my = 0.f, mxx = 0.f, mxy = 0.f, myy = 0.f;
     for (int r = rows.x; r <= rows.y; ++r) {
         const float dy = dy0 + (float)r;
-        const float w0 = w[r * TILE], w1 = w[r * TILE + 8];
+        const int i = table_idx(r, 0);
+        const float w0 = w[i], w1 = w[i + 32];
         const float a0 = w0 * dx0, a1 = w1 * dx1;
         const float ws = w0 + w1, as = a0 + a1;
         m0 += ws;
@@ -127,6 +163,7 @@ k_intensity_fwd(const uint2 *__restrict__ ranges, const uint32_t *__restrict__ v
     __shared__ float4 sA[BATCH];
     __shared__ float2 sB[BATCH];
     __shared__ int2 sR[BATCH];
+    __shared__ uint32_t sM[BATCH];
     __shared__ uint32_t sid[BATCH];
     __shared__ float W[SUB * WSTRIDE];
     const int t = threadIdx.x, warp = t >> 5;
@@ -145,17 +182,20 @@ k_intensity_fwd(const uint2 *__restrict__ ranges, const uint32_t *__restrict__ v
             const float4 c0 = cp[0], c1 = cp[1];
             sA[t] = c0;
             sB[t] = make_float2(c1.x, c1.y);
-            sR[t] = tile_rows(c0.y, c1.w, c.y0);
+            const int2 rows = tile_rows(c0.y, c1.w, c.y0);
+            sR[t] = rows;
+            sM[t] = warp_mask(rows, tile_cols(c0.x, c0.z, c0.w, c1.x, cut, c.x0));
             sid[t] = vg;
         }
         __syncthreads();
         const int nb = min(BATCH, (int)(r.y - base));
         for (int sub = 0; sub < nb; sub += SUB) {
             const int ns = min(SUB, nb - sub);
+#pragma unroll 4
             for (int jj = 0; jj < ns; ++jj) {
                 const int k = sub + jj;
                 float contrib = 0.f;
-                if (warp_rows_hit(sR[k], warp) && !done) {
+                if (warp_hit(sM[k], warp) && !done) {
                     const float4 a = sA[k];
                     const float2 b = sB[k];
                     const float dx = __fsub_rn(fx, a.x), dy = __fsub_rn(fy, a.y);
@@ -173,7 +213,7 @@ k_intensity_fwd(const uint2 *__restrict__ ranges, const uint32_t *__restrict__ v
             }
             __syncthreads();
             const int j = t >> 3;
-            const float s = table_sum(W, j < ns ? sR[sub + j] : make_int2(0, -1));
+            const float s = table_sum(W, j < ns ? sR[sub + j] : make_int2(16, -1));
             if ((t & 7) == 0 && j < ns && s != 0.f) atomicAdd(&A[sid[sub + j]], s);
             __syncthreads();
         }
@@ -203,7 +243,7 @@ k_splat_fwd(const uint2 *__restrict__ rangesI, const uint32_t *__restrict__ vals
             float cut, const StatusDev *st, float *__restrict__ images) {
     __shared__ float4 sA[BATCH];
     __shared__ float2 sB[BATCH];
-    __shared__ int2 sR[BATCH];
+    __shared__ uint32_t sM[BATCH];
     const int t = threadIdx.x, warp = t >> 5;
     const TileCtx c = tile_ctx(views, V, blockIdx.x);
     const bool ok = st->code == SDGR_OK;
@@ -219,12 +259,12 @@ k_splat_fwd(const uint2 *__restrict__ rangesI, const uint32_t *__restrict__ vals
             const float4 i0 = ip[0], i1 = ip[1];
             sA[t] = i0;
             sB[t] = make_float2(i1.x, i1.y * comp[vg].P * A[vg]);
-            sR[t] = tile_rows(i0.y, i1.z, c.y0);
+            sM[t] = warp_mask(tile_rows(i0.y, i1.z, c.y0), tile_cols(i0.x, i0.z, i0.w, i1.x, cut, c.x0));
         }
         __syncthreads();
         const int nb = min(BATCH, (int)(r.y - base));
         for (int k = 0; k < nb; ++k) {
-            if (!warp_rows_hit(sR[k], warp)) continue;
+            if (!warp_hit(sM[k], warp)) continue;
             const float4 a = sA[k];
             const float2 b = sB[k];
             const float q = gauss_q(a.z, a.w, b.x, fx - a.x, fy - a.y);
@@ -246,7 +286,12 @@ cudaError_t launch_splat_fwd(const uint2 *rangesI, const uint32_t *vals, const I
 // ---------------------------------------------------------------------------
 // a10: adjoint of the imaging splat.  Per (view, Gaussian) the moments of
 // w = dL/dS * exp(-delta_I/2); the parameter adjoint turns them into
-// dL/dI = c M0, dL/du_I, dL/dconic_I and dL/dc.
+// dL/dI = c M0, dL/du_I, dL/dconic_I and dL/dc.  No pixel depends on
+// another here, so the kernel is Gaussian-parallel: eight threads per
+// Gaussian, each taking two columns (c, c + 8) of the rows its K-ellipse can
+// reach; along a column the exponent is a quadratic in dy evaluated with two
+// FMAs; dL/dS comes from shared memory; three shuffles combine the eight
+// partial moments.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256)
 k_splat_bwd(const uint2 *__restrict__ rangesI, const uint32_t *__restrict__ vals, const ImgRec *__restrict__ img,
@@ -255,16 +300,17 @@ k_splat_bwd(const uint2 *__restrict__ rangesI, const uint32_t *__restrict__ vals
     if (st->code != SDGR_OK) return;
     __shared__ float4 sA[BATCH];
     __shared__ float sC[BATCH];
-    __shared__ int2 sR[BATCH];
+    __shared__ int4 sRC[BATCH];  // tile-local rows (x, y) and columns (z, w) the ellipse can reach
     __shared__ uint32_t sid[BATCH];
-    __shared__ float W[SUB * WSTRIDE];
-    const int t = threadIdx.x, warp = t >> 5;
+    __shared__ float sg[TILE_PIX];  // dL/dS of the tile's pixels, by thread index
+    const int t = threadIdx.x;
     const TileCtx c = tile_ctx(views, V, blockIdx.x);
     const uint2 r = rangesI[blockIdx.x];
-    const float fx = (float)c.px, fy = (float)c.py;
     const float g = c.inside ? dLdS[c.pix] : 0.f;
+    sg[t] = g;
     if (__syncthreads_count(g != 0.f) == 0) return;
-    const float colx = (float)(c.x0 + (t & 7));
+    const int col = t & 7;
+    const float colx = (float)(c.x0 + col);
     for (uint32_t base = r.x; base < r.y; base += BATCH) {
         __syncthreads();
         const uint32_t jload = base + t;
@@ -274,30 +320,51 @@ k_splat_bwd(const uint2 *__restrict__ rangesI, const uint32_t *__restrict__ vals
             const float4 i0 = ip[0], i1 = ip[1];
             sA[t] = i0;
             sC[t] = i1.x;
-            sR[t] = tile_rows(i0.y, i1.z, c.y0);
+            const int2 rows = tile_rows(i0.y, i1.z, c.y0);
+            const int2 cols = tile_cols(i0.x, i0.z, i0.w, i1.x, cut, c.x0);
+            sRC[t] = make_int4(rows.x, rows.y, cols.x, cols.y);
             sid[t] = vg;
         }
         __syncthreads();
         const int nb = min(BATCH, (int)(r.y - base));
-        for (int sub = 0; sub < nb; sub += SUB) {
-            const int ns = min(SUB, nb - sub);
-            for (int jj = 0; jj < ns; ++jj) {
-                const int k = sub + jj;
-                float w = 0.f;
-                if (warp_rows_hit(sR[k], warp)) {
-                    const float4 a = sA[k];
-                    const float q = gauss_q(a.z, a.w, sC[k], fx - a.x, fy - a.y);
-                    if (q >= cut) w = g * ex2_approx(q);
+        for (int j0 = 0; j0 < nb; j0 += 32) {
+            const int k = j0 + (t >> 3);
+            float m0 = 0.f, mx = 0.f, my = 0.f, mxx = 0.f, mxy = 0.f, myy = 0.f;
+            if (k < nb) {
+                const float4 a = sA[k];
+                const float qc = sC[k];
+                const int4 rc = sRC[k];
+                const float dxa = colx - a.x, dxb = dxa + 8.f;
+                // exponent along a column: qa dx^2 + (qb dx) dy + qc dy^2
+                const float Aa = a.z * dxa * dxa, Ba = a.w * dxa;
+                const float Ab = a.z * dxb * dxb, Bb = a.w * dxb;
+                const bool va = col >= rc.z && col <= rc.w, vb = col + 8 >= rc.z && col + 8 <= rc.w;
+                const float dy0 = (float)c.y0 - a.y;
+                for (int rr = rc.x; rr <= rc.y; ++rr) {
+                    const float dy = dy0 + (float)rr;
+                    const int i = table_idx(rr, col);
+                    const float qa_ = fmaf(dy, fmaf(qc, dy, Ba), Aa);
+                    const float qb_ = fmaf(dy, fmaf(qc, dy, Bb), Ab);
+                    const float wa = (va && qa_ >= cut) ? sg[i] * ex2_approx(qa_) : 0.f;
+                    const float wb = (vb && qb_ >= cut) ? sg[i + 32] * ex2_approx(qb_) : 0.f;
+                    const float xa = wa * dxa, xb = wb * dxb;
+                    const float ws = wa + wb, xs = xa + xb;
+                    m0 += ws;
+                    mx += xs;
+                    my = fmaf(ws, dy, my);
+                    mxx = fmaf(xa, dxa, fmaf(xb, dxb, mxx));
+                    mxy = fmaf(xs, dy, mxy);
+                    myy = fmaf(ws * dy, dy, myy);
                 }
-                W[jj * WSTRIDE + t] = w;
             }
-            __syncthreads();
-            const int j = t >> 3;
-            float m[6];
-            const float4 a = sA[sub + (j < ns ? j : 0)];
-            table_moments(W, j < ns ? sR[sub + j] : make_int2(0, -1), colx - a.x, (float)c.y0 - a.y, m);
-            if ((t & 7) == 0 && j < ns) add_moments(accI, sid[sub + j], m);
-            __syncthreads();
+            float m[6] = {m0, mx, my, mxx, mxy, myy};
+#pragma unroll
+            for (int q = 0; q < 6; ++q) {
+                m[q] += __shfl_xor_sync(0xffffffffu, m[q], 1);
+                m[q] += __shfl_xor_sync(0xffffffffu, m[q], 2);
+                m[q] += __shfl_xor_sync(0xffffffffu, m[q], 4);
+            }
+            if (col == 0 && k < nb) add_moments(accI, sid[k], m);
         }
     }
 }
@@ -331,6 +398,7 @@ k_intensity_bwd(const uint2 *__restrict__ ranges, const uint32_t *__restrict__ v
     __shared__ float4 sA[BATCH];
     __shared__ float4 sB[BATCH];
     __shared__ int2 sR[BATCH];
+    __shared__ uint32_t sM[BATCH];
     __shared__ uint32_t sid[BATCH];
     __shared__ float W[SUB * WSTRIDE];
     __shared__ int smax;
@@ -359,17 +427,20 @@ k_intensity_bwd(const uint2 *__restrict__ ranges, const uint32_t *__restrict__ v
             const float dLdI = accI[2 * (size_t)vg].x * img[vg].cn;
             sA[t] = c0;
             sB[t] = make_float4(c1.x, c1.y, dLdI * c1.z, 0.f);
-            sR[t] = tile_rows(c0.y, c1.w, c.y0);
+            const int2 rows = tile_rows(c0.y, c1.w, c.y0);
+            sR[t] = rows;
+            sM[t] = warp_mask(rows, tile_cols(c0.x, c0.z, c0.w, c1.x, cut, c.x0));
             sid[t] = vg;
         }
         __syncthreads();
         for (int send = nb; send > 0; send -= SUB) {
             const int sub = max(0, send - SUB);
             const int ns = send - sub;
+#pragma unroll 4
             for (int jj = ns - 1; jj >= 0; --jj) {
                 const int k = sub + jj;
                 float w = 0.f;
-                if (warp_rows_hit(sR[k], warp) && lo + k < mylast) {
+                if (warp_hit(sM[k], warp) && lo + k < mylast) {
                     const float4 a = sA[k];
                     const float4 b = sB[k];
                     const float dx = __fsub_rn(fx, a.x), dy = __fsub_rn(fy, a.y);
@@ -377,7 +448,9 @@ k_intensity_bwd(const uint2 *__restrict__ ranges, const uint32_t *__restrict__ v
                     if (q >= cut) {
                         const float e = ex2_approx(q);
                         const float alpha = __fmul_rn(b.y, e);
-                        if (!first) T = __fdiv_rn(T, __fsub_rn(1.f, alpha));
+                        // relative error of a few ulp per step; the forward's rounding
+                        // of 1 - alpha is undone exactly because both sides share it
+                        if (!first) T = __fdividef(T, __fsub_rn(1.f, alpha));
                         first = false;
                         const float chat = b.z;
                         const float ga = T * (chat - B);
@@ -391,7 +464,7 @@ k_intensity_bwd(const uint2 *__restrict__ ranges, const uint32_t *__restrict__ v
             const int j = t >> 3;
             float m[6];
             const float4 a = sA[sub + (j < ns ? j : 0)];
-            table_moments(W, j < ns ? sR[sub + j] : make_int2(0, -1), colx - a.x, (float)c.y0 - a.y, m);
+            table_moments(W, j < ns ? sR[sub + j] : make_int2(16, -1), colx - a.x, (float)c.y0 - a.y, m);
             if ((t & 7) == 0 && j < ns) add_moments(accC, sid[sub + j], m);
             __syncthreads();
         }
