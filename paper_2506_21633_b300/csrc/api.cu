@@ -4,6 +4,7 @@
 #include <math.h>
 #include <string.h>
 
+#include <algorithm>
 #include <atomic>
 #include <new>
 #include <vector>
@@ -27,7 +28,7 @@ struct Layout {
     size_t dk0, dv0, dk1, dv1;
     size_t scnt, soff, scan64;
     size_t ik0, iv0, ik1, iv1;
-    size_t hist, scan32, ranges;
+    size_t hist, scan32, ranges, segs;
     size_t A, Tstop, last, accI, accC;
     size_t total;
 };
@@ -75,11 +76,12 @@ Layout make_layout(const sdgr_caps *c) {
     L.ik1 = take(NI * 4);
     L.iv1 = take(NI * 4);
     int64_t hb = depth_sort_blocks_cap(c);
-    int64_t ib = (c->max_instances + SORT_IPB - 1) / SORT_IPB;
+    int64_t ib = (c->max_instances + SORT_IPB - 1) / SORT_IPB + 2 * (int64_t)c->max_views;
     int64_t hn = (hb > ib ? hb : ib) * RADIX;
     L.hist = take((size_t)hn * 4);
     L.scan32 = take(scan_scratch_elems(hn) * 4);
     L.ranges = take(2 * NT * sizeof(uint2));
+    L.segs = take((2 * V + 2) * sizeof(SegDev));
     L.A = take(VG * 4);
     L.Tstop = take(NP * 4);
     L.last = take(NP * 4);
@@ -333,9 +335,12 @@ sdgr_status sdgr_preprocess(sdgr_ws *ws, const float *params, const int64_t *sce
     ws->n_gauss = n_gauss;
     ws->tiles = (int)tiles;
     ws->sort_blocks = (int)sblk;
+    int64_t max_view_tiles = 1;
+    for (int v = 0; v < V; ++v)
+        max_view_tiles = std::max<int64_t>(max_view_tiles, (int64_t)ws->hviews[v].tiles_x * ws->hviews[v].tiles_y);
     int bits = 1;
-    while (((int64_t)1 << bits) < 2 * tiles) ++bits;
-    ws->key_bits = bits;
+    while (((int64_t)1 << bits) < max_view_tiles) ++bits;
+    ws->key_bits = bits;  // tile bits within one view: the instance sort is segmented per (plane, view)
     ws->params = params;
     ws->stage = 0;
 
@@ -365,7 +370,8 @@ sdgr_status sdgr_bin_sort(sdgr_ws *ws, void *stream) {
     const ViewDev *views = ws->at<ViewDev>(L.views);
     // depth order per view: stable radix sort of the keys, values = slot index
     const int pk0 = prof_begin(ws, SDGR_STAGE_DEPTH_SORT, s);
-    CK(launch_depth_sort(views, ws->V, ws->sort_blocks, ws->at<uint32_t>(L.dk0), ws->at<uint32_t>(L.dv0),
+    CK(launch_depth_sort(views, ws->V, ws->sort_blocks, ws->at<SegDev>(L.segs), ws->at<uint32_t>(L.dk0),
+                         ws->at<uint32_t>(L.dv0),
                          ws->at<uint32_t>(L.dk1), ws->at<uint32_t>(L.dv1), ws->at<uint32_t>(L.hist),
                          ws->at<uint32_t>(L.scan32), s));
     prof_end(ws, pk0, s);
@@ -380,7 +386,8 @@ sdgr_status sdgr_bin_sort(sdgr_ws *ws, void *stream) {
     CK(launch_emit(sorted_vg, soff, ws->at<uint2>(L.rectC), ws->at<uint2>(L.rectI), views, ws->V, ws->VG, ws->tiles,
                    st, ws->at<uint32_t>(L.ik0), ws->at<uint32_t>(L.iv0), ws->sms, s));
     int final1 = 0;
-    CK(launch_inst_sort(st, ws->caps.max_instances, ws->key_bits, ws->at<uint32_t>(L.ik0), ws->at<uint32_t>(L.iv0),
+    CK(launch_inst_sort(st, soff, scnt, ws->VG, views, ws->V, ws->tiles, ws->caps.max_instances, ws->key_bits,
+                        ws->at<SegDev>(L.segs), ws->at<uint32_t>(L.ik0), ws->at<uint32_t>(L.iv0),
                         ws->at<uint32_t>(L.ik1), ws->at<uint32_t>(L.iv1), ws->at<uint32_t>(L.hist),
                         ws->at<uint32_t>(L.scan32), &final1, s));
     ws->inst_keys = ws->at<uint32_t>(final1 ? L.ik1 : L.ik0);

@@ -132,200 +132,256 @@ cudaError_t launch_scan_u64(const unsigned long long *in, unsigned long long *ou
 }
 
 // ---------------------------------------------------------------------------
-// LSD radix sort passes.  A block owns SORT_IPB consecutive items of one
-// segment.  Segmented mode (depth sort): segments are views, block -> view
-// by the per-view block offsets; the digit histogram of each view is laid out
-// [digit][block of the view] after the earlier views' histograms, so one
-// device-wide exclusive scan yields every output position.  Single mode
-// (instance sort): one segment whose length is read on the device.
+// Segmented LSD radix sort.  The items of one call form contiguous segments
+// (the views for the depth sort; the (plane, view) groups of the instances,
+// which the emission writes in depth order) and each segment is sorted on
+// its own: a block owns up to SORT_IPB consecutive items of one segment;
+// the digit histogram of each segment is laid out [digit][block of the
+// segment] after the earlier segments' histograms, so one device-wide
+// exclusive scan yields every output position.  The digit of an item is
+// taken from (key - key_base of its segment).
+//
+// Block-local ranking is stable and warp-private: warp w ranks items
+// [512 w, 512 w + 512) of the block with __match_any_sync against its own
+// per-digit counters, then one block-wide pass turns the per-(warp, digit)
+// counts into offsets.  Items are reordered in shared memory and written out
+// coalesced.
 // ---------------------------------------------------------------------------
-struct Seg {
-    int64_t start;
-    int32_t count;
+constexpr int SORT_WARPS = SORT_THREADS / 32;
+constexpr int SORT_PER_WARP = SORT_IPB / SORT_WARPS;       // 512
+constexpr int SORT_ROUNDS = SORT_PER_WARP / 32;            // 16
+constexpr size_t SORT_SMEM = 4 * SORT_IPB * sizeof(uint32_t);
+
+__device__ __forceinline__ int seg_of_block(const SegDev *segs, int nseg, int b) {
+    return upper_index(nseg + 1, b, [&](int k) { return (int64_t)segs[k].blk_start; });
+}
+
+struct BlockSeg {
+    uint32_t start, count, key_base;
     int32_t nb, lb;
     int64_t hbase;
 };
 
-template <bool VIEWS>
-__device__ __forceinline__ Seg seg_of(int b, const ViewDev *views, int V, const StatusDev *st, int64_t cap,
-                                      int nblocks) {
-    Seg s;
-    if (VIEWS) {
-        const int v = view_of_sblk(views, V, b);
-        const ViewDev &vd = views[v];
-        s.lb = b - vd.sblk_off;
-        s.nb = vd.sblk_n;
-        s.start = vd.vg_off + (int64_t)s.lb * SORT_IPB;
-        int64_t rem = (int64_t)vd.N - (int64_t)s.lb * SORT_IPB;
-        s.count = (int32_t)(rem < SORT_IPB ? (rem > 0 ? rem : 0) : SORT_IPB);
-        s.hbase = (int64_t)vd.sblk_off * RADIX;
-    } else {
-        int64_t n = st->code == SDGR_OK ? st->n_inst : 0;
-        if (n > cap) n = cap;
-        s.lb = b;
-        s.nb = nblocks;
-        s.start = (int64_t)b * SORT_IPB;
-        int64_t rem = n - s.start;
-        s.count = (int32_t)(rem < SORT_IPB ? (rem > 0 ? rem : 0) : SORT_IPB);
-        s.hbase = 0;
-    }
-    return s;
+__device__ __forceinline__ bool block_seg(const SegDev *segs, int nseg, int b, BlockSeg &o) {
+    if ((uint32_t)b >= segs[nseg].blk_start) return false;  // sentinel holds the block total
+    const int s = seg_of_block(segs, nseg, b);
+    const SegDev sg = segs[s];
+    o.lb = b - (int)sg.blk_start;
+    o.nb = (int)((sg.len + SORT_IPB - 1) / SORT_IPB);
+    o.start = sg.start + (uint32_t)o.lb * SORT_IPB;
+    const uint32_t rem = sg.len - (uint32_t)o.lb * SORT_IPB;
+    o.count = rem < (uint32_t)SORT_IPB ? rem : (uint32_t)SORT_IPB;
+    o.key_base = sg.key_base;
+    o.hbase = (int64_t)sg.blk_start * RADIX;
+    return true;
 }
 
-template <bool VIEWS>
 __global__ void __launch_bounds__(SORT_THREADS)
-k_radix_hist(const uint32_t *__restrict__ keys, int shift, const ViewDev *views, int V, const StatusDev *st,
-             int64_t cap, int nblocks, uint32_t *__restrict__ hist) {
+k_radix_hist(const uint32_t *__restrict__ keys, int shift, const SegDev *__restrict__ segs, int nseg,
+             uint32_t *__restrict__ hist) {
     __shared__ uint32_t cnt[RADIX];
-    const Seg sg = seg_of<VIEWS>(blockIdx.x, views, V, st, cap, nblocks);
+    BlockSeg bs;
+    if (!block_seg(segs, nseg, blockIdx.x, bs)) return;
     for (int d = threadIdx.x; d < RADIX; d += blockDim.x) cnt[d] = 0;
     __syncthreads();
-    for (int i = threadIdx.x; i < sg.count; i += blockDim.x)
-        atomicAdd(&cnt[(keys[sg.start + i] >> shift) & (RADIX - 1)], 1u);
+    for (uint32_t i = threadIdx.x; i < bs.count; i += blockDim.x)
+        atomicAdd(&cnt[((keys[bs.start + i] - bs.key_base) >> shift) & (RADIX - 1)], 1u);
     __syncthreads();
-    for (int d = threadIdx.x; d < RADIX; d += blockDim.x) hist[sg.hbase + (int64_t)d * sg.nb + sg.lb] = cnt[d];
+    for (int d = threadIdx.x; d < RADIX; d += blockDim.x) hist[bs.hbase + (int64_t)d * bs.nb + bs.lb] = cnt[d];
 }
 
-constexpr int SORT_WARPS = SORT_THREADS / 32;
-constexpr size_t SORT_SMEM = 4 * SORT_IPB * sizeof(uint32_t);
-
-template <bool VIEWS>
 __global__ void __launch_bounds__(SORT_THREADS)
 k_radix_scatter(const uint32_t *__restrict__ kin, const uint32_t *__restrict__ vin, uint32_t *__restrict__ kout,
-                uint32_t *__restrict__ vout, int shift, const ViewDev *views, int V, const StatusDev *st, int64_t cap,
-                int nblocks, const uint32_t *__restrict__ hscan) {
+                uint32_t *__restrict__ vout, int shift, const SegDev *__restrict__ segs, int nseg,
+                const uint32_t *__restrict__ hscan) {
     extern __shared__ uint32_t sm[];
     uint32_t *sk = sm, *sv = sm + SORT_IPB, *ok = sm + 2 * SORT_IPB, *ov = sm + 3 * SORT_IPB;
-    __shared__ uint32_t cnt[RADIX], lstart[RADIX], run[RADIX], gbase[RADIX];
     __shared__ uint32_t wcnt[SORT_WARPS][RADIX];
-
-    const Seg sg = seg_of<VIEWS>(blockIdx.x, views, V, st, cap, nblocks);
-    if (sg.count == 0) return;
+    __shared__ uint32_t dstart[RADIX], gbase[RADIX];
+    BlockSeg bs;
+    if (!block_seg(segs, nseg, blockIdx.x, bs)) return;
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    for (int i = t; i < sg.count; i += SORT_THREADS) {
-        sk[i] = kin[sg.start + i];
-        sv[i] = vin[sg.start + i];
+    const uint32_t n = bs.count;
+    for (uint32_t i = t; i < n; i += SORT_THREADS) {
+        sk[i] = kin[bs.start + i];
+        sv[i] = vin[bs.start + i];
     }
     for (int d = t; d < RADIX; d += SORT_THREADS) {
-        cnt[d] = 0;
-        run[d] = 0;
 #pragma unroll
         for (int w = 0; w < SORT_WARPS; ++w) wcnt[w][d] = 0;
     }
     __syncthreads();
-    for (int i = t; i < sg.count; i += SORT_THREADS) atomicAdd(&cnt[(sk[i] >> shift) & (RADIX - 1)], 1u);
+    // warp-private stable ranking of this warp's 512 items
+    const unsigned lt_mask = (1u << lane) - 1u;
+    uint32_t lr[SORT_ROUNDS];
+#pragma unroll
+    for (int r = 0; r < SORT_ROUNDS; ++r) {
+        const uint32_t i = (uint32_t)(warp * SORT_PER_WARP + r * 32 + lane);
+        const bool valid = i < n;
+        const uint32_t d = valid ? (((sk[i] - bs.key_base) >> shift) & (RADIX - 1)) : (uint32_t)RADIX;
+        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        const bool leader = (__ffs(peers) - 1) == lane;
+        lr[r] = (valid ? wcnt[warp][d] : 0u) + (uint32_t)__popc(peers & lt_mask);
+        __syncwarp();
+        if (valid && leader) wcnt[warp][d] += (uint32_t)__popc(peers);
+        __syncwarp();
+    }
     __syncthreads();
+    // per digit: offsets of each warp, digit totals
+    uint32_t tot = 0;
+    if (t < RADIX) {
+#pragma unroll
+        for (int w = 0; w < SORT_WARPS; ++w) {
+            const uint32_t c = wcnt[w][t];
+            wcnt[w][t] = tot;
+            tot += c;
+        }
+    }
     {
-        uint32_t c = t < RADIX ? cnt[t] : 0u;
-        uint32_t ex = block_exclusive_scan<uint32_t>(c, nullptr);
+        const uint32_t ex = block_exclusive_scan<uint32_t>(t < RADIX ? tot : 0u, nullptr);
         if (t < RADIX) {
-            lstart[t] = ex;
-            gbase[t] = hscan[sg.hbase + (int64_t)t * sg.nb + sg.lb] - ex;
+            dstart[t] = ex;
+            gbase[t] = hscan[bs.hbase + (int64_t)t * bs.nb + bs.lb] - ex;
         }
     }
     __syncthreads();
-    const unsigned lt_mask = (1u << lane) - 1u;
-    for (int r0 = 0; r0 < sg.count; r0 += SORT_THREADS) {
-        const int i = r0 + t;
-        const bool valid = i < sg.count;
-        const uint32_t d = valid ? ((sk[i] >> shift) & (RADIX - 1)) : (uint32_t)RADIX;
-        const unsigned peers = __match_any_sync(0xffffffffu, d);
-        const int rank = __popc(peers & lt_mask);
-        const bool leader = (__ffs(peers) - 1) == lane;
-        if (valid && leader) wcnt[warp][d] = (uint32_t)__popc(peers);
-        __syncthreads();
-        if (t < RADIX) {
-            uint32_t acc = run[t];
 #pragma unroll
-            for (int w = 0; w < SORT_WARPS; ++w) {
-                uint32_t c = wcnt[w][t];
-                wcnt[w][t] = acc;
-                acc += c;
-            }
-            run[t] = acc;
-        }
-        __syncthreads();
-        if (valid) {
-            const uint32_t pos = lstart[d] + wcnt[warp][d] + rank;
-            ok[pos] = sk[i];
+    for (int r = 0; r < SORT_ROUNDS; ++r) {
+        const uint32_t i = (uint32_t)(warp * SORT_PER_WARP + r * 32 + lane);
+        if (i < n) {
+            const uint32_t k = sk[i];
+            const uint32_t d = ((k - bs.key_base) >> shift) & (RADIX - 1);
+            const uint32_t pos = dstart[d] + wcnt[warp][d] + lr[r];
+            ok[pos] = k;
             ov[pos] = sv[i];
         }
-        __syncthreads();
-        if (t < RADIX) {
-#pragma unroll
-            for (int w = 0; w < SORT_WARPS; ++w) wcnt[w][t] = 0;
-        }
-        __syncthreads();
     }
-    for (int p = t; p < sg.count; p += SORT_THREADS) {
+    __syncthreads();
+    for (uint32_t p = t; p < n; p += SORT_THREADS) {
         const uint32_t k = ok[p];
-        const uint32_t d = (k >> shift) & (RADIX - 1);
-        const uint32_t dst = gbase[d] + (uint32_t)p;
+        const uint32_t d = ((k - bs.key_base) >> shift) & (RADIX - 1);
+        const uint32_t dst = gbase[d] + p;
         kout[dst] = k;
         vout[dst] = ov[p];
     }
+}
+
+// Single-block exclusive scan of the segments' block counts; entry nseg is a
+// sentinel whose blk_start is the total.
+__device__ void seg_blocks_scan(SegDev *segs, int nseg) {
+    __shared__ uint32_t carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int base = 0; base < nseg; base += blockDim.x) {
+        const int s = base + threadIdx.x;
+        const uint32_t nb = s < nseg ? (segs[s].len + SORT_IPB - 1) / SORT_IPB : 0u;
+        uint32_t tot;
+        const uint32_t ex = block_exclusive_scan<uint32_t>(nb, &tot);
+        if (s < nseg) segs[s].blk_start = carry + ex;
+        __syncthreads();
+        if (threadIdx.x == 0) carry += tot;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        segs[nseg].start = 0;
+        segs[nseg].len = 0;
+        segs[nseg].key_base = 0;
+        segs[nseg].blk_start = carry;
+    }
+}
+
+// Depth sort: one segment per view.
+__global__ void __launch_bounds__(256) k_seg_views(const ViewDev *views, int V, SegDev *segs) {
+    for (int v = threadIdx.x; v < V; v += blockDim.x) {
+        segs[v].start = (uint32_t)views[v].vg_off;
+        segs[v].len = (uint32_t)views[v].N;
+        segs[v].key_base = 0;
+    }
+    __syncthreads();
+    seg_blocks_scan(segs, V);
+}
+
+// Instance sort: one segment per (plane, view); keys are global tile ids,
+// key_base the segment's first tile.
+__global__ void __launch_bounds__(256)
+k_seg_instances(const unsigned long long *soff, const unsigned long long *scnt, int64_t VG, const ViewDev *views,
+                int V, int tiles, const StatusDev *st, SegDev *segs) {
+    const bool ok = st->code == SDGR_OK;
+    const unsigned long long total = VG > 0 ? soff[2 * VG - 1] + scnt[2 * VG - 1] : 0ull;
+    for (int s = threadIdx.x; s < 2 * V; s += blockDim.x) {
+        const int p = s / V, v = s % V;
+        const int64_t i0 = (int64_t)p * VG + views[v].vg_off;
+        const unsigned long long a = i0 < 2 * VG ? soff[i0] : total;
+        int64_t i1 = i0 + views[v].N;
+        const unsigned long long b = i1 < 2 * VG ? soff[i1] : total;
+        segs[s].start = (uint32_t)a;
+        segs[s].len = ok ? (uint32_t)(b - a) : 0u;
+        segs[s].key_base = (uint32_t)(p * tiles + views[v].tile_off);
+    }
+    __syncthreads();
+    seg_blocks_scan(segs, 2 * V);
 }
 
 static bool g_sort_attr_done = false;
 
 static cudaError_t sort_attrs() {
     if (g_sort_attr_done) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(k_radix_scatter<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)SORT_SMEM);
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_radix_scatter<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SORT_SMEM);
+    cudaError_t e = cudaFuncSetAttribute(k_radix_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SORT_SMEM);
     if (e != cudaSuccess) return e;
     g_sort_attr_done = true;
     return cudaSuccess;
 }
 
-cudaError_t launch_depth_sort(const ViewDev *views, int V, int nblocks, uint32_t *k0, uint32_t *v0, uint32_t *k1,
-                              uint32_t *v1, uint32_t *hist, uint32_t *scan_scratch, cudaStream_t s) {
-    if (nblocks <= 0) return cudaSuccess;
-    cudaError_t e = sort_attrs();
-    if (e != cudaSuccess) return e;
-    uint32_t *kin = k0, *vin = v0, *kout = k1, *vout = v1;
-    const int64_t hn = (int64_t)nblocks * RADIX;
-    for (int shift = 0; shift < 32; shift += RADIX_BITS) {
-        k_radix_hist<true><<<nblocks, SORT_THREADS, 0, s>>>(kin, shift, views, V, nullptr, 0, nblocks, hist);
-        note_launch();
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        if ((e = launch_scan_u32(hist, hist, hn, scan_scratch, s)) != cudaSuccess) return e;
-        k_radix_scatter<true><<<nblocks, SORT_THREADS, SORT_SMEM, s>>>(kin, vin, kout, vout, shift, views, V, nullptr,
-                                                                      0, nblocks, hist);
-        note_launch();
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        uint32_t *tk = kin, *tv = vin;
-        kin = kout; vin = vout; kout = tk; vout = tv;
-    }
-    return cudaSuccess;  // four passes: the result is back in (k0, v0)
-}
-
-cudaError_t launch_inst_sort(const StatusDev *st, int64_t cap, int key_bits, uint32_t *k0, uint32_t *v0,
-                             uint32_t *k1, uint32_t *v1, uint32_t *hist, uint32_t *scan_scratch, int *final_in_1,
-                             cudaStream_t s) {
-    *final_in_1 = 0;
-    const int nblocks = (int)((cap + SORT_IPB - 1) / SORT_IPB);
-    if (nblocks <= 0) return cudaSuccess;
+static cudaError_t radix_passes(int nblocks, int nseg, const SegDev *segs, int bits, uint32_t *k0, uint32_t *v0,
+                                uint32_t *k1, uint32_t *v1, uint32_t *hist, uint32_t *scan_scratch, int *passes_out,
+                                cudaStream_t s) {
     cudaError_t e = sort_attrs();
     if (e != cudaSuccess) return e;
     uint32_t *kin = k0, *vin = v0, *kout = k1, *vout = v1;
     const int64_t hn = (int64_t)nblocks * RADIX;
     int passes = 0;
-    for (int shift = 0; shift < key_bits; shift += RADIX_BITS, ++passes) {
-        k_radix_hist<false><<<nblocks, SORT_THREADS, 0, s>>>(kin, shift, nullptr, 0, st, cap, nblocks, hist);
+    for (int shift = 0; shift < bits; shift += RADIX_BITS, ++passes) {
+        k_radix_hist<<<nblocks, SORT_THREADS, 0, s>>>(kin, shift, segs, nseg, hist);
         note_launch();
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         if ((e = launch_scan_u32(hist, hist, hn, scan_scratch, s)) != cudaSuccess) return e;
-        k_radix_scatter<false><<<nblocks, SORT_THREADS, SORT_SMEM, s>>>(kin, vin, kout, vout, shift, nullptr, 0, st,
-                                                                       cap, nblocks, hist);
+        k_radix_scatter<<<nblocks, SORT_THREADS, SORT_SMEM, s>>>(kin, vin, kout, vout, shift, segs, nseg, hist);
         note_launch();
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         uint32_t *tk = kin, *tv = vin;
         kin = kout; vin = vout; kout = tk; vout = tv;
     }
-    *final_in_1 = passes & 1;
+    *passes_out = passes;
     return cudaSuccess;
+}
+
+cudaError_t launch_depth_sort(const ViewDev *views, int V, int nblocks, SegDev *segs, uint32_t *k0, uint32_t *v0,
+                              uint32_t *k1, uint32_t *v1, uint32_t *hist, uint32_t *scan_scratch, cudaStream_t s) {
+    if (nblocks <= 0 || V <= 0) return cudaSuccess;
+    k_seg_views<<<1, 256, 0, s>>>(views, V, segs);
+    note_launch();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    int passes = 0;
+    return radix_passes(nblocks, V, segs, 32, k0, v0, k1, v1, hist, scan_scratch, &passes, s);
+    // four passes: the result is back in (k0, v0)
+}
+
+cudaError_t launch_inst_sort(const StatusDev *st, const unsigned long long *soff, const unsigned long long *scnt,
+                             int64_t VG, const ViewDev *views, int V, int tiles, int64_t cap, int key_bits,
+                             SegDev *segs, uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t *v1, uint32_t *hist,
+                             uint32_t *scan_scratch, int *final_in_1, cudaStream_t s) {
+    *final_in_1 = 0;
+    if (V <= 0) return cudaSuccess;
+    const int nblocks = (int)((cap + SORT_IPB - 1) / SORT_IPB) + 2 * V;
+    k_seg_instances<<<1, 256, 0, s>>>(soff, scnt, VG, views, V, tiles, st, segs);
+    note_launch();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    int passes = 0;
+    e = radix_passes(nblocks, 2 * V, segs, key_bits, k0, v0, k1, v1, hist, scan_scratch, &passes, s);
+    *final_in_1 = passes & 1;
+    return e;
 }
 
 // ---------------------------------------------------------------------------

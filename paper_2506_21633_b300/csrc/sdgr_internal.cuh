@@ -61,6 +61,12 @@ struct alignas(16) StatusDev {
     unsigned long long pairs[2];  // sdgr_count_pairs: in-cutoff pairs per plane
 };
 
+// One segment of a segmented radix sort: items [start, start + len), digits
+// taken from (key - key_base); blk_start = first block of the segment.
+struct alignas(16) SegDev {
+    uint32_t start, len, key_base, blk_start;
+};
+
 // Computation-plane record of one (view, Gaussian).  The conic is stored
 // pre-scaled so that exp(-delta/2) = exp2(qa dx^2 + qb dx dy + qc dy^2):
 // qa = -log2e/2 C00, qb = -log2e C01, qc = -log2e/2 C11.  ry is the
@@ -147,11 +153,12 @@ cudaError_t launch_scan_u64(const unsigned long long *in, unsigned long long *ou
                             unsigned long long *scratch, cudaStream_t s);
 
 // radix sort passes
-cudaError_t launch_depth_sort(const ViewDev *views, int V, int nblocks, uint32_t *k0, uint32_t *v0, uint32_t *k1,
-                              uint32_t *v1, uint32_t *hist, uint32_t *scan_scratch, cudaStream_t s);
-cudaError_t launch_inst_sort(const StatusDev *st, int64_t cap, int key_bits, uint32_t *k0, uint32_t *v0,
-                             uint32_t *k1, uint32_t *v1, uint32_t *hist, uint32_t *scan_scratch, int *final_in_1,
-                             cudaStream_t s);
+cudaError_t launch_depth_sort(const ViewDev *views, int V, int nblocks, SegDev *segs, uint32_t *k0, uint32_t *v0,
+                              uint32_t *k1, uint32_t *v1, uint32_t *hist, uint32_t *scan_scratch, cudaStream_t s);
+cudaError_t launch_inst_sort(const StatusDev *st, const unsigned long long *soff, const unsigned long long *scnt,
+                             int64_t VG, const ViewDev *views, int V, int tiles, int64_t cap, int key_bits,
+                             SegDev *segs, uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t *v1, uint32_t *hist,
+                             uint32_t *scan_scratch, int *final_in_1, cudaStream_t s);
 cudaError_t launch_gather_counts(const uint32_t *sorted_vg, const uint32_t *cntC, const uint32_t *cntI, int64_t VG,
                                  unsigned long long *scnt, int sms, cudaStream_t s);
 cudaError_t launch_check_capacity(const unsigned long long *scnt, const unsigned long long *soff, int64_t VG,
