@@ -188,6 +188,14 @@ sdgr_status sdgr_render_bwd(sdgr_ws *ws, const float *dL_dimages, float *grads, 
 sdgr_status sdgr_adam_step(float *params, const float *grads, float *m, float *v, int64_t N, const float *lr,
                            float b1, float b2, float eps, int32_t step, void *stream);
 
+/* Step a13, graph-replayable form: as sdgr_adam_step, but the 1-based step
+ * count lives in device memory.  step: device int32; the call increments
+ * *step first and uses the new value, so a captured CUDA graph that
+ * contains this call applies the right bias correction at every replay.
+ * Errors: SDGR_ERR_INVALID (N < 0, NULL step, misaligned pointers). */
+sdgr_status sdgr_adam_step_device(float *params, const float *grads, float *m, float *v, int64_t N, const float *lr,
+                                  float b1, float b2, float eps, int32_t *step, void *stream);
+
 /* Step a9: L1 loss, mean over npix pixels, and dL/dS = sign(S - S*)/npix
  * (sign(0) = 0).  images, targets, dL_dimages: device [npix] float32; loss:
  * device float32 scalar, overwritten.  Errors: SDGR_ERR_INVALID. */

@@ -21,7 +21,7 @@ EXPORTS = (
     "sdgr_caps_for", "sdgr_workspace_size", "sdgr_ws_create", "sdgr_ws_destroy", "sdgr_preprocess",
     "sdgr_bin_sort", "sdgr_render_fwd", "sdgr_render_bwd", "sdgr_adam_step", "sdgr_l1_loss",
     "sdgr_read_status", "sdgr_status_string", "sdgr_profile_enable", "sdgr_profile_read",
-    "sdgr_count_pairs", "sdgr_launch_count", "sdgr_render_fwd_noalloc",
+    "sdgr_count_pairs", "sdgr_launch_count", "sdgr_render_fwd_noalloc", "sdgr_adam_step_device",
 )
 
 STAGES = ("preprocess", "depth_sort", "bin", "intensity_fwd", "splat_fwd", "splat_bwd", "intensity_bwd",
@@ -84,6 +84,7 @@ def lib():
         L.sdgr_render_fwd_noalloc.argtypes = [vp, i64, P(SdgrView), i32, P(SdgrCfg), vp, vp, vp]
         L.sdgr_adam_step.argtypes = [vp, vp, vp, vp, i64, P(ctypes.c_float), f32, f32, f32, i32, vp]
         L.sdgr_l1_loss.argtypes = [vp, vp, i64, vp, vp, vp]
+        L.sdgr_adam_step_device.argtypes = [vp, vp, vp, vp, i64, P(ctypes.c_float), f32, f32, f32, vp, vp]
         L.sdgr_read_status.argtypes = [vp, P(ctypes.c_int64)]
         L.sdgr_profile_enable.argtypes = [vp, i32]
         L.sdgr_profile_read.argtypes = [vp, P(ctypes.c_double), P(ctypes.c_int64), i32]
@@ -190,6 +191,13 @@ def sdgr_adam_step(p, g, m, v, N, lr, b1, b2, eps, step, stream):
     _check("sdgr_adam_step", lib().sdgr_adam_step(ctypes.c_void_p(p), ctypes.c_void_p(g), ctypes.c_void_p(m),
                                                   ctypes.c_void_p(v), int(N), lr_arr, b1, b2, eps, int(step),
                                                   ctypes.c_void_p(stream)))
+
+
+def sdgr_adam_step_device(p, g, m, v, N, lr, b1, b2, eps, step_ptr, stream):
+    lr_arr = (ctypes.c_float * 5)(*[float(x) for x in lr])
+    _check("sdgr_adam_step_device", lib().sdgr_adam_step_device(
+        ctypes.c_void_p(p), ctypes.c_void_p(g), ctypes.c_void_p(m), ctypes.c_void_p(v), int(N), lr_arr, b1, b2, eps,
+        ctypes.c_void_p(step_ptr), ctypes.c_void_p(stream)))
 
 
 def sdgr_l1_loss(images, targets, npix, dLdS, loss, stream):

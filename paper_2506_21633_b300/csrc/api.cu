@@ -483,6 +483,21 @@ sdgr_status sdgr_adam_step(float *params, const float *grads, float *m, float *v
     return SDGR_OK;
 }
 
+sdgr_status sdgr_adam_step_device(float *params, const float *grads, float *m, float *v, int64_t N, const float *lr,
+                                  float b1, float b2, float eps, int32_t *step, void *stream) {
+    if (N < 0 || !lr || !step) return SDGR_ERR_INVALID;
+    if (N > 0 && (!params || !grads || !m || !v)) return SDGR_ERR_INVALID;
+    if (((uintptr_t)params | (uintptr_t)grads | (uintptr_t)m | (uintptr_t)v) % 16 != 0) return SDGR_ERR_INVALID;
+    if (!(b1 >= 0.f && b1 < 1.f && b2 >= 0.f && b2 < 1.f && eps >= 0.f)) return SDGR_ERR_INVALID;
+    int dev = 0, sms = 148;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    CK(launch_adam_dev(reinterpret_cast<float4 *>(params), reinterpret_cast<const float4 *>(grads),
+                       reinterpret_cast<float4 *>(m), reinterpret_cast<float4 *>(v), N * 3, lr, b1, b2, eps, step, sms,
+                       static_cast<cudaStream_t>(stream)));
+    return SDGR_OK;
+}
+
 sdgr_status sdgr_l1_loss(const float *images, const float *targets, int64_t npix, float *dL_dimages, float *loss,
                          void *stream) {
     if (npix < 0 || !loss || (npix > 0 && (!images || !targets || !dL_dimages))) return SDGR_ERR_INVALID;

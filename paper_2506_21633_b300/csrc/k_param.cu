@@ -204,6 +204,52 @@ cudaError_t launch_adam(float4 *p, const float4 *g, float4 *m, float4 *v, int64_
     return cudaGetLastError();
 }
 
+// Device-step variant: one thread advances the step counter, then the update
+// reads it (two launches keep the order on the stream).
+__global__ void k_step_inc(int32_t *step) { *step += 1; }
+
+__global__ void __launch_bounds__(256)
+k_adam_dev(float4 *__restrict__ p, const float4 *__restrict__ g, float4 *__restrict__ m, float4 *__restrict__ v,
+           int64_t n4, float4 lr0, float4 lr1, float4 lr2, float b1, float b2, float eps, const int32_t *step) {
+    const float t = (float)*step;
+    const float inv_bc1 = 1.0f / (1.0f - powf(b1, t));
+    const float inv_sqrt_bc2 = rsqrtf(1.0f - powf(b2, t));
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += stride) {
+        const int slot = (int)(i % 3);
+        const float4 lr = slot == 0 ? lr0 : (slot == 1 ? lr1 : lr2);
+        float4 pp = p[i], gg = g[i], mm = m[i], vv = v[i];
+        float *P = &pp.x, *G = &gg.x, *Mv = &mm.x, *Vv = &vv.x;
+        const float *L = &lr.x;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            Mv[k] = Mv[k] + (1.f - b1) * (G[k] - Mv[k]);
+            Vv[k] = b2 * Vv[k] + (1.f - b2) * G[k] * G[k];
+            const float denom = sqrtf(Vv[k]) * inv_sqrt_bc2 + eps;
+            P[k] = P[k] - (L[k] * inv_bc1) * Mv[k] / denom;
+        }
+        p[i] = pp;
+        m[i] = mm;
+        v[i] = vv;
+    }
+}
+
+cudaError_t launch_adam_dev(float4 *p, const float4 *g, float4 *m, float4 *v, int64_t n4, const float *lr, float b1,
+                            float b2, float eps, int32_t *step, int sms, cudaStream_t s) {
+    k_step_inc<<<1, 1, 0, s>>>(step);
+    note_launch();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || n4 <= 0) return e;
+    int64_t blocks = (n4 + 255) / 256;
+    if (blocks > (int64_t)sms * 16) blocks = (int64_t)sms * 16;
+    const float4 l0 = make_float4(lr[0], lr[0], lr[0], lr[3]);
+    const float4 l1 = make_float4(lr[1], lr[1], lr[1], lr[4]);
+    const float4 l2 = make_float4(lr[2], lr[2], lr[2], lr[2]);
+    k_adam_dev<<<(unsigned)blocks, 256, 0, s>>>(p, g, m, v, n4, l0, l1, l2, b1, b2, eps, step);
+    note_launch();
+    return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------------------
 // a9: L1 loss (mean) and its gradient.
 // ---------------------------------------------------------------------------

@@ -193,6 +193,8 @@ cudaError_t launch_param_bwd(const float4 *params, const ViewDev *views, const S
                              float4 *grads, int sms, cudaStream_t s);
 cudaError_t launch_adam(float4 *p, const float4 *g, float4 *m, float4 *v, int64_t n4, const float *lr, float b1,
                         float b2, float eps, int step, int sms, cudaStream_t s);
+cudaError_t launch_adam_dev(float4 *p, const float4 *g, float4 *m, float4 *v, int64_t n4, const float *lr, float b1,
+                            float b2, float eps, int32_t *step, int sms, cudaStream_t s);
 cudaError_t launch_l1(const float *S, const float *T, int64_t npix, float *dLdS, float *loss, int sms,
                       cudaStream_t s);
 
