@@ -58,7 +58,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["sdgr", "reference"], default="sdgr")
-    ap.add_argument("--workload", choices=["config3", "medium", "small"], default="config3",
+    ap.add_argument("--requests", type=int, default=1000, help="serving: measured requests")
+    ap.add_argument("--workload", choices=["config3", "medium", "small", "config4", "serve"], default="config3",
                     help="medium: the config-3 scene with 8 views (profiling); small: a reduced scene for "
                          "quick checks (neither is a bench line)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -465,8 +466,155 @@ def run_reference(args):
             "e2e": {"value": round(value, 5), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+def run_uneven(args):
+    """Uneven batch: 256 scenes (log-uniform 1k-500k Gaussians, vehicle boxes
+    and buildings alternating), image sizes 256/512/1024, 8 views each; the
+    whole batch is one graph-captured step, against plain per-view calls."""
+    import numpy as np
+    import torch
+    import sdgr_scenes as sc
+    from paper_2506_21633_b300 import _lib
+    from paper_2506_21633_b300.batch import FusedStep, plain_step
+    from paper_2506_21633_b300.render import Renderer, views_npix
+    rank, world, local = rank_info()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    scenes, views = sc.uneven_batch(seed=4 + rank)
+    offs = [0]
+    for p in scenes:
+        offs.append(offs[-1] + p.shape[0])
+    true = np.concatenate(scenes)
+    start = np.concatenate([sc.perturb(p, seed=17 + k) for k, p in enumerate(scenes)])
+    V = len(views)
+    tr = Renderer(device=dev)
+    targets = tr.prepare(torch.from_numpy(true.astype(np.float32)).to(dev), views, offs).forward().clone()
+    torch.cuda.synchronize(dev)
+    del tr
+    p = torch.from_numpy(start.astype(np.float32)).to(dev).contiguous()
+    fs = FusedStep(p, views, targets, offs)
+    fs.capture()
+    for _ in range(max(args.warmup, 1)):
+        fs.step()
+    fs.check()
+    pairs = fs.r.count_pairs()
+    stream = torch.cuda.current_stream(dev)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    l0 = _lib.sdgr_launch_count()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        fs.step()
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    assert fs.check()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    # plain: one view at a time, stream sync after each
+    rp = Renderer(device=dev)
+    rp.prepare(p[offs[0]:offs[1]], [dict(views[0], scene=0)], [0, offs[1]], instances=fs.r.n_inst)
+    grads = torch.zeros_like(p)
+    images = torch.empty(views_npix(views), dtype=torch.float32, device=dev)
+    dLdS = torch.empty_like(images)
+    loss = torch.empty(1, dtype=torch.float32, device=dev)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    plain_step(rp, p, views, targets, grads, images, dLdS, loss, offs)
+    torch.cuda.synchronize(dev)
+    t_plain = time.perf_counter() - t0
+    sizes = sorted({v["NA"] for v in views})
+    return {"metric": "uneven-batch fwd+bwd views/s (batched graph-captured step vs plain per-view calls)",
+            "value": round(V / (ms / 1e3), 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": True, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "uneven batch: %d scenes, %d..%d Gaussians (total %d), images %s, %d views"
+                                   % (len(scenes), min(s.shape[0] for s in scenes), max(s.shape[0] for s in scenes),
+                                      offs[-1], sizes, V),
+                       "pairs_per_step": {"computation_plane": pairs[0], "imaging_plane": pairs[1]},
+                       "instances_per_step": int(fs.r.n_inst)},
+            "plain": {"value": round(V / t_plain, 3), "unit": UNIT, "s_per_step": round(t_plain, 3)},
+            "gpu_launches_per_step": int((_lib.sdgr_launch_count() - l0) / max(args.steps, 1))}
+
+
+def run_serving(args):
+    """Serving: Poisson arrivals (mean 2 ms apart) of render and gradient
+    requests over 32 resident scenes of 10k-1M Gaussians; 1-16 views per
+    request, images of 256..2048 pixels, half render, half gradient."""
+    import numpy as np
+    import torch
+    import sdgr_scenes as sc
+    from paper_2506_21633_b300.serve import Server
+    rank, world, local = rank_info()
+    torch.cuda.set_device(local)
+    rng = np.random.default_rng(5 + rank)
+    scenes, meta = [], []
+    for s in range(32):
+        n = int(math.exp(rng.uniform(math.log(1e4), math.log(1e6))))
+        if s % 2 == 0:
+            scale = (n / 300000.0) ** (1.0 / 3.0)
+            ext = (6.0 * scale, 3.0 * scale, 2.0 * scale)
+            scenes.append(sc.vehicle_box_scene(n, seed=500 + s, extent=ext, center=(0.0, 0.0, ext[2] / 2)))
+            meta.append((1.7 * max(ext), (0.0, 0.0, ext[2] / 2)))
+        else:
+            r2 = np.random.default_rng(500 + s)
+            scenes.append(sc.box_surface_scene(n, sc._place_boxes(r2, 3, 60.0, 5.0, 20.0), r2))
+            meta.append((76.8, (30.0, 30.0, 5.0)))
+    sizes = (256, 512, 1024, 2048)
+    pool = {sz: np.random.default_rng(sz).uniform(0.0, 0.05, size=(sz, sz)).astype(np.float32) for sz in sizes}
+    budget = int(torch.cuda.get_device_properties(local).total_memory * 0.6)
+    srv = Server(scenes, hbm_budget_bytes=budget, n_slots=3, max_batch_views=64, max_batch_pixels=1 << 26)
+    n_warm, n_meas = 50, args.requests
+    futs, t_sched = [], time.perf_counter()
+    nviews, t_sub = [], []
+    for k in range(n_warm + n_meas):
+        t_sched += rng.exponential(0.002)
+        dt = t_sched - time.perf_counter()
+        if dt > 0:
+            time.sleep(dt)
+        t_sub.append(time.perf_counter())
+        s = int(rng.integers(0, 32))
+        nv = int(rng.integers(1, 17))
+        sz = int(rng.choice(sizes))
+        frame, center = meta[s]
+        vs = sc.random_views(nv, seed=10000 + k, size=sz, res=frame / sz, center=center)
+        if rng.uniform() < 0.5:
+            futs.append(srv.submit(s, vs, "render"))
+        else:
+            futs.append(srv.submit(s, vs, "gradient", [pool[sz]] * nv))
+        nviews.append(nv)
+    res = [f.result(timeout=3600) for f in futs]
+    srv.close(timeout=600)
+    meas = res[n_warm:]
+    lat = np.array([r.latency_s for r in meas]) * 1e3
+    done_views = sum(nviews[n_warm:])
+    window = max(t + r.latency_s for t, r in zip(t_sub[n_warm:], meas)) - t_sub[n_warm]
+    stats = srv.stats
+    return {"metric": "serving p50/p99 ms and views/s (continuous batching, Poisson arrivals mean 2 ms)",
+            "value": round(float(np.percentile(lat, 50)), 3), "unit": "ms (p50)",
+            "p99_ms": round(float(np.percentile(lat, 99)), 3), "mean_ms": round(float(lat.mean()), 3),
+            "views_per_s": round(done_views / window, 2), "views": done_views, "requests": n_meas,
+            "warmup_requests": n_warm, "window_s": round(window, 3),
+            "higher_is_better": False, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "32 resident scenes, %d..%d Gaussians; requests 1-16 views, images 256..2048, "
+                                   "render/gradient 1:1, Poisson arrivals mean 2 ms" %
+                                   (min(s.shape[0] for s in scenes), max(s.shape[0] for s in scenes)),
+                       "hbm_budget_bytes": budget, "slots": 3},
+            "batches": stats["batches"], "mean_batch": round(float(np.mean(stats["batch_sizes"])), 2),
+            "max_inflight": stats["max_inflight"], "requeued": stats["requeued"]}
+
+
 def main():
     args = parse()
+    if args.workload == "serve" and args.impl == "sdgr":
+        t0 = time.perf_counter()
+        out = run_serving(args)
+        out["wall_s"] = round(time.perf_counter() - t0, 2)
+        if rank_info()[0] == 0:
+            print(json.dumps(out), flush=True)
+        return 0
+    if args.workload == "config4" and args.impl == "sdgr":
+        out = run_uneven(args)
+        if out is not None and rank_info()[0] == 0:
+            print(json.dumps(out), flush=True)
+        return 0
     if args.impl == "reference":
         out = run_reference(args)
         if out is not None:

@@ -272,6 +272,14 @@ int64_t sdgr_launch_count(void);
 sdgr_status sdgr_render_fwd_noalloc(const float *params, int64_t N, const sdgr_view *views, int32_t V,
                                     const sdgr_cfg *cfg, float *images, float *intensity, void *stream);
 
+/* Asynchronous form of sdgr_read_status: enqueues on `stream` a copy of the
+ * status word into `host_dst` (caller-owned page-locked host memory of at
+ * least 16 bytes): int32 status code, int32 reserved, int64 instances the
+ * last sdgr_bin_sort needed.  Valid once the stream has reached that point
+ * (e.g. after an event recorded behind it has completed).
+ * Errors: SDGR_ERR_INVALID (NULL arguments), SDGR_ERR_CUDA. */
+sdgr_status sdgr_copy_status_async(sdgr_ws *ws, void *host_dst, void *stream);
+
 /* Static, NUL-terminated description of a status code. */
 const char *sdgr_status_string(sdgr_status s);
 

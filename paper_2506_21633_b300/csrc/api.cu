@@ -552,6 +552,13 @@ sdgr_status sdgr_profile_read(sdgr_ws *ws, double *ms, int64_t *launches, int32_
     return SDGR_OK;
 }
 
+sdgr_status sdgr_copy_status_async(sdgr_ws *ws, void *host_dst, void *stream) {
+    if (!ws || !host_dst) return SDGR_ERR_INVALID;
+    CK(cudaMemcpyAsync(host_dst, ws->base + ws->L.status, 16, cudaMemcpyDeviceToHost,
+                       static_cast<cudaStream_t>(stream)));
+    return SDGR_OK;
+}
+
 sdgr_status sdgr_read_status(sdgr_ws *ws, int64_t *required_instances) {
     if (!ws) return SDGR_ERR_INVALID;
     StatusDev h;
