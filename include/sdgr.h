@@ -178,6 +178,25 @@ sdgr_status sdgr_render_fwd(sdgr_ws *ws, float *images, float *intensity, void *
  * since the last sdgr_preprocess(). */
 sdgr_status sdgr_render_bwd(sdgr_ws *ws, const float *dL_dimages, float *grads, int32_t accumulate, void *stream);
 
+/* View-dependent scattering (the phase function "from the centre and the
+ * spherical harmonic coefficients" of Section II-B-3; SH degree schedule of
+ * Section III-B-3).  With plane-wave geometry the direction is the same for
+ * every Gaussian of a view: the unit vector d toward the radar,
+ * d = (cos theta cos phi, -cos theta sin phi, sin theta).  Then
+ *   P_i(view) = P_i + sum_{l=1..degree} sum_m sh_i[l^2 - 1 + l + m] Y_lm(d)
+ * with the real orthonormal spherical harmonics (no Condon-Shortley phase),
+ * ordered per degree as l=1: (y, z, x); l=2: xy, yz, 3z^2-1, xz, x^2-y^2;
+ * l=3: y(3x^2-y^2), xyz, y(5z^2-1), z(5z^2-3), x(5z^2-1), z(x^2-y^2),
+ * x(x^2-3y^2) (each times its normalising constant); P_i (parameter 7) is
+ * the degree-0 term.
+ * sh: device [max_gaussians][16] float32 (entries 15 unused), read by the
+ *   following sdgr_preprocess / sdgr_render_bwd calls; NULL disables.
+ * dsh: device [max_gaussians][16] float32 or NULL; if given, sdgr_render_bwd
+ *   writes dL/dsh there (overwritten or accumulated like grads).
+ * degree: 0..3.  Errors: SDGR_ERR_INVALID (degree out of range, NULL ws,
+ *   misaligned pointers). */
+sdgr_status sdgr_set_sh(sdgr_ws *ws, const float *sh, float *dsh, int32_t degree);
+
 /* Step a13: one Adam step (Kingma & Ba; bias-corrected, eps added to the
  * square root of the corrected second moment, torch.optim.Adam semantics,
  * no weight decay) over N Gaussians.  params, grads, m, v: device

@@ -40,7 +40,8 @@ class OrcView(ctypes.Structure):
 class OrcCfg(ctypes.Structure):
     _fields_ = [
         ("K", ctypes.c_double), ("eps", ctypes.c_double), ("T_min", ctypes.c_double),
-        ("norm_mode", ctypes.c_int32), ("pad", ctypes.c_int32),
+        ("norm_mode", ctypes.c_int32), ("sh_degree", ctypes.c_int32),
+        ("sh", ctypes.POINTER(ctypes.c_double)), ("dsh", ctypes.POINTER(ctypes.c_double)),
     ]
 
 
@@ -76,6 +77,7 @@ def lib():
         L.orc_step.argtypes = [dp, ctypes.c_int32, ctypes.POINTER(OrcView), ctypes.c_int32,
                                ctypes.POINTER(OrcCfg), ctypes.c_int32, dp, dp, dp]
         L.orc_step.restype = ctypes.c_double
+        L.orc_sh_basis.argtypes = [dp, dp]
         L.orc_set_threads.argtypes = [ctypes.c_int]
         L.orc_set_threads.restype = ctypes.c_int
         _lib = L
@@ -86,8 +88,24 @@ def set_threads(n: int) -> int:
     return lib().orc_set_threads(int(n))
 
 
-def cfg(K=5.0, eps=0.3, T_min=0.0, norm_mode=0) -> OrcCfg:
-    return OrcCfg(K=float(K), eps=float(eps), T_min=float(T_min), norm_mode=int(norm_mode))
+def cfg(K=5.0, eps=0.3, T_min=0.0, norm_mode=0, sh=None, sh_degree=0) -> OrcCfg:
+    """sh: optional [N,16] float64 coefficients of the SH degrees 1..3
+    (view-dependent scattering), used up to sh_degree."""
+    c = OrcCfg(K=float(K), eps=float(eps), T_min=float(T_min), norm_mode=int(norm_mode), sh_degree=int(sh_degree))
+    if sh is not None:
+        a = np.ascontiguousarray(sh, dtype=np.float64)
+        assert a.ndim == 2 and a.shape[1] == 16
+        c._sh = a  # keep alive
+        c.sh = _dp(a)
+    return c
+
+
+def sh_basis(d):
+    """The 15 real SH values of degrees 1..3 at unit direction d."""
+    d = np.ascontiguousarray(d, dtype=np.float64)
+    Y = np.zeros(15)
+    lib().orc_sh_basis(_dp(d), _dp(Y))
+    return Y
 
 
 def _views(views):
@@ -148,6 +166,18 @@ def grad(params, views, dLdS, c=None, culled=False):
     if rc:
         raise ValueError("oracle: invalid arguments")
     return out[:N], dI[:, :N]
+
+
+def grad_sh(params, views, dLdS, c, culled=False):
+    """As grad(), plus dL/dsh [N,16] for a cfg built with sh coefficients."""
+    p = _params(params)
+    dsh = np.zeros((max(p.shape[0], 1), 16))
+    c.dsh = _dp(dsh)
+    try:
+        g, dI = grad(p, views, dLdS, c, culled)
+    finally:
+        c.dsh = ctypes.POINTER(ctypes.c_double)()
+    return g, dsh[:p.shape[0]]
 
 
 def step(params, views, targets, c=None, culled=True):

@@ -71,8 +71,45 @@ typedef struct {
     double eps;        /* dilation added to both 2D covariances (px^2) */
     double T_min;      /* ray stops once T < T_min (0: never) */
     int32_t norm_mode; /* 0: energy-normalised beta, 1: peak (c_i = 1) */
-    int32_t pad;
+    int32_t sh_degree; /* 0..3: degree of the view-dependent scattering */
+    const double *sh;  /* [N][16] SH coefficients of degrees 1..3 (NULL: none) */
+    double *dsh;       /* [N][16] out: dL/dsh (orc_grad only; NULL: not wanted) */
 } orc_cfg;
+
+/* View-dependent scattering (the phase function of Section II-B-3, "from the
+ * centre and the spherical harmonic coefficients").  With plane-wave
+ * geometry the direction is the same for every Gaussian of a view: the unit
+ * vector d from the scene toward the radar (the negative line of sight).
+ * P_i(view) = P_i + sum_{l=1..degree} sum_m sh_i[l^2 - 1 + l + m] Y_lm(d),
+ * with the real orthonormal spherical harmonics (no Condon-Shortley phase):
+ *   l=1: c1 (y, z, x),                           c1 = sqrt(3/(4 pi))
+ *   l=2: c2 xy, c2 yz, c20 (3z^2 - 1), c2 xz, c22 (x^2 - y^2)
+ *        c2 = sqrt(15/pi)/2, c20 = sqrt(5/pi)/4, c22 = sqrt(15/pi)/4
+ *   l=3: c33 y(3x^2 - y^2), c32 xyz, c31 y(5z^2 - 1), c30 z(5z^2 - 3),
+ *        c31 x(5z^2 - 1), c32/2 z(x^2 - y^2), c33 x(x^2 - 3y^2)
+ *        c33 = sqrt(35/(2 pi))/4, c32 = sqrt(105/pi)/2, c31 = sqrt(21/(2 pi))/4,
+ *        c30 = sqrt(7/pi)/4 */
+static void sh_basis(const double d[3], double Y[15]) {
+    const double pi = ORC_PI;
+    const double x = d[0], y = d[1], z = d[2];
+    const double c1 = sqrt(3.0 / (4.0 * pi));
+    const double c2 = sqrt(15.0 / pi) / 2.0, c20 = sqrt(5.0 / pi) / 4.0, c22 = sqrt(15.0 / pi) / 4.0;
+    const double c33 = sqrt(35.0 / (2.0 * pi)) / 4.0, c32 = sqrt(105.0 / pi) / 2.0;
+    const double c31 = sqrt(21.0 / (2.0 * pi)) / 4.0, c30 = sqrt(7.0 / pi) / 4.0;
+    Y[0] = c1 * y; Y[1] = c1 * z; Y[2] = c1 * x;
+    Y[3] = c2 * x * y; Y[4] = c2 * y * z; Y[5] = c20 * (3 * z * z - 1); Y[6] = c2 * x * z; Y[7] = c22 * (x * x - y * y);
+    Y[8] = c33 * y * (3 * x * x - y * y); Y[9] = c32 * x * y * z; Y[10] = c31 * y * (5 * z * z - 1);
+    Y[11] = c30 * z * (5 * z * z - 3); Y[12] = c31 * x * (5 * z * z - 1); Y[13] = 0.5 * c32 * z * (x * x - y * y);
+    Y[14] = c33 * x * (x * x - 3 * y * y);
+}
+
+static int sh_count(int degree) { return degree <= 0 ? 0 : (degree >= 3 ? 15 : (degree == 1 ? 3 : 8)); }
+
+/* SH basis of the direction toward the radar of a view, for tests. */
+int orc_sh_basis(const double *d, double *Y) {
+    sh_basis(d, Y);
+    return 0;
+}
 
 typedef struct {
     /* activations (C1) */
@@ -92,6 +129,7 @@ typedef struct {
     double C2[2][2][2];  /* its inverse */
     double det[2];
     double cnorm;        /* imaging-plane normaliser c_i */
+    double Ysh[15];      /* SH basis of this view's direction (zeros past the degree) */
     int bb[2][4];        /* inclusive pixel box x0, x1, y0, y1 (culled mode) */
 } orc_gauss;
 
@@ -147,7 +185,7 @@ static double mahal(const double C[2][2], double dx, double dy) {
 }
 
 /* Mapping and Projection Algorithm for one Gaussian and one view. */
-static void project(const double *p, const orc_view *v, const orc_cfg *cfg, orc_gauss *g) {
+static void project(const double *p, const orc_view *v, const orc_cfg *cfg, orc_gauss *g, const double *sh_row) {
     int a, b, k;
     /* activations */
     for (k = 0; k < 3; ++k) g->s[k] = exp(p[4 + k]);
@@ -156,6 +194,15 @@ static void project(const double *p, const orc_view *v, const orc_cfg *cfg, orc_
     g->o = 1.0 / (1.0 + exp(-p[3]));
     g->P = p[7];
     quat_to_rot(g->qhat, g->R);
+    memset(g->Ysh, 0, sizeof(g->Ysh));
+    if (sh_row && cfg->sh_degree > 0) {
+        double st = sin(v->theta), ct = cos(v->theta), sp = sin(v->phi), cp = cos(v->phi);
+        const double d[3] = {ct * cp, -ct * sp, st}; /* toward the radar */
+        int k, nk = sh_count(cfg->sh_degree);
+        sh_basis(d, g->Ysh);
+        for (k = nk; k < 15; ++k) g->Ysh[k] = 0.0;
+        for (k = 0; k < nk; ++k) g->P += sh_row[k] * g->Ysh[k];
+    }
     for (a = 0; a < 3; ++a)
         for (b = 0; b < 3; ++b) {
             double acc = 0.0;
@@ -390,7 +437,7 @@ static int view_forward(const double *params, int N, const orc_view *v, const or
                         int *order, double *A, double *I, double *S, double *Tfin) {
     int i;
 #pragma omp parallel for schedule(static)
-    for (i = 0; i < N; ++i) project(params + 12 * (size_t)i, v, cfg, &g[i]);
+    for (i = 0; i < N; ++i) project(params + 12 * (size_t)i, v, cfg, &g[i], cfg->sh ? cfg->sh + 16 * (size_t)i : NULL);
     depth_order(g, N, order);
     intensity_pass(g, N, order, v, cfg, culled, A, Tfin);
     for (i = 0; i < N; ++i) I[i] = g[i].P * A[i];
@@ -416,7 +463,7 @@ int orc_project(const double *params, int32_t N, const orc_view *v, const orc_cf
     int i;
     for (i = 0; i < N; ++i) {
         orc_gauss g;
-        project(params + 12 * (size_t)i, v, cfg, &g);
+        project(params + 12 * (size_t)i, v, cfg, &g, cfg->sh ? cfg->sh + 16 * (size_t)i : NULL);
         double *o = out + 16 * (size_t)i;
         o[0] = g.u[0][0]; o[1] = g.u[0][1];
         o[2] = g.S2[0][0][0]; o[3] = g.S2[0][0][1]; o[4] = g.S2[0][1][1];
@@ -456,7 +503,7 @@ int orc_depth_order(const double *params, int32_t N, const orc_view *v, const or
     orc_gauss *g = (orc_gauss *)malloc(sizeof(orc_gauss) * (size_t)(N > 0 ? N : 1));
     int *o = (int *)malloc(sizeof(int) * (size_t)(N > 0 ? N : 1));
     int i;
-    for (i = 0; i < N; ++i) project(params + 12 * (size_t)i, v, cfg, &g[i]);
+    for (i = 0; i < N; ++i) project(params + 12 * (size_t)i, v, cfg, &g[i], cfg->sh ? cfg->sh + 16 * (size_t)i : NULL);
     depth_order(g, N, o);
     for (i = 0; i < N; ++i) order[i] = o[i];
     free(g); free(o);
@@ -671,6 +718,10 @@ static int view_adjoint(int N, const orc_view *v, const orc_cfg *cfg, int culled
         gr[3] += ad->o * q->o * (1.0 - q->o);
         for (k = 0; k < 3; ++k) gr[4 + k] += ds[k] * q->s[k];
         gr[7] += ad->gI * A[i];
+        if (cfg->dsh) {
+            int kk;
+            for (kk = 0; kk < 15; ++kk) cfg->dsh[16 * (size_t)i + kk] += ad->gI * A[i] * q->Ysh[kk];
+        }
         for (k = 0; k < 4; ++k) gr[8 + k] += dq[k];
         if (dLdI_out) dLdI_out[i] = ad->gI;
     }
@@ -697,6 +748,7 @@ int orc_grad(const double *params, int32_t N, const orc_view *views, int32_t V, 
     size_t pix = 0;
     int v;
     memset(grads, 0, sizeof(double) * 12 * (size_t)N);
+    if (cfg->dsh) memset(cfg->dsh, 0, sizeof(double) * 16 * (size_t)N);
     for (v = 0; v < V; ++v) {
         view_backward(params, N, &views[v], cfg, culled, dLdS + pix, grads, dLdI ? dLdI + (size_t)v * N : NULL);
         pix += (size_t)views[v].NA * views[v].NR;
@@ -734,6 +786,7 @@ double orc_step(const double *params, int32_t N, const orc_view *views, int32_t 
     double *dLdS = (double *)malloc(sizeof(double) * (pix > 0 ? pix : 1));
     double loss = orc_l1(images, targets, (int64_t)pix, dLdS);
     memset(grads, 0, sizeof(double) * 12 * (size_t)N);
+    if (cfg->dsh) memset(cfg->dsh, 0, sizeof(double) * 16 * (size_t)N);
     for (v = 0; v < V; ++v) {
         view_adjoint(N, &views[v], cfg, culled, g[v], order[v], A[v], I[v], dLdS + poff[v], grads, NULL);
         free(g[v]); free(order[v]); free(A[v]); free(I[v]);

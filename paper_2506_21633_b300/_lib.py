@@ -22,7 +22,7 @@ EXPORTS = (
     "sdgr_bin_sort", "sdgr_render_fwd", "sdgr_render_bwd", "sdgr_adam_step", "sdgr_l1_loss",
     "sdgr_read_status", "sdgr_status_string", "sdgr_profile_enable", "sdgr_profile_read",
     "sdgr_count_pairs", "sdgr_launch_count", "sdgr_render_fwd_noalloc", "sdgr_adam_step_device",
-    "sdgr_copy_status_async",
+    "sdgr_copy_status_async", "sdgr_set_sh",
 )
 
 STAGES = ("preprocess", "depth_sort", "bin", "intensity_fwd", "splat_fwd", "splat_bwd", "intensity_bwd",
@@ -88,6 +88,7 @@ def lib():
         L.sdgr_adam_step_device.argtypes = [vp, vp, vp, vp, i64, P(ctypes.c_float), f32, f32, f32, vp, vp]
         L.sdgr_read_status.argtypes = [vp, P(ctypes.c_int64)]
         L.sdgr_copy_status_async.argtypes = [vp, vp, vp]
+        L.sdgr_set_sh.argtypes = [vp, vp, vp, i32]
         L.sdgr_profile_enable.argtypes = [vp, i32]
         L.sdgr_profile_read.argtypes = [vp, P(ctypes.c_double), P(ctypes.c_int64), i32]
         L.sdgr_status_string.argtypes = [ctypes.c_int]
@@ -205,6 +206,11 @@ def sdgr_adam_step_device(p, g, m, v, N, lr, b1, b2, eps, step_ptr, stream):
 def sdgr_l1_loss(images, targets, npix, dLdS, loss, stream):
     _check("sdgr_l1_loss", lib().sdgr_l1_loss(ctypes.c_void_p(images), ctypes.c_void_p(targets), int(npix),
                                               ctypes.c_void_p(dLdS), ctypes.c_void_p(loss), ctypes.c_void_p(stream)))
+
+
+def sdgr_set_sh(ws, sh_ptr, dsh_ptr, degree):
+    _check("sdgr_set_sh", lib().sdgr_set_sh(ws, ctypes.c_void_p(sh_ptr or None), ctypes.c_void_p(dsh_ptr or None),
+                                            int(degree)))
 
 
 def sdgr_copy_status_async(ws, host_ptr, stream):

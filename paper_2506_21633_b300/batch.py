@@ -19,6 +19,12 @@ from .render import Renderer, _stream_handle, l1_loss, views_npix
 DEFAULT_LR = (1.6e-4, 5e-3, 1e-3, 5e-2, 2.5e-3)  # means, log-scales, quaternions, opacity logit, P
 
 
+def sh_degree_at(iteration, every=2500, max_degree=3):
+    """SH degree schedule of the training set-up (Section III-B-3): one more
+    degree every `every` iterations, up to `max_degree`."""
+    return min(max_degree, max(0, int(iteration)) // int(every))
+
+
 class FusedStep:
     """State and call sequence of one optimisation step over a batch.
 

@@ -129,6 +129,9 @@ struct sdgr_ws {
     int prof_used = 0;
     double prof_ms[SDGR_NUM_STAGES] = {0};
     int64_t prof_n[SDGR_NUM_STAGES] = {0};
+    const float *sh = nullptr;  // sdgr_set_sh
+    float *dsh = nullptr;
+    int sh_degree = 0;
     std::vector<ViewDev> hviews;
     std::vector<SceneDev> hscenes;
     std::vector<int32_t> hscene_views;
@@ -286,6 +289,20 @@ sdgr_status sdgr_preprocess(sdgr_ws *ws, const float *params, const int64_t *sce
             d.cd[b] = in.center[b];
             d.c[b] = (float)in.center[b];
         }
+        // real SH of degrees 1..3 at the direction toward the radar (float64, rounded)
+        {
+            const double x = ct * cp, y = -ct * sp, z = st, pi = 3.14159265358979323846;
+            const double c1 = sqrt(3.0 / (4.0 * pi)), c2 = sqrt(15.0 / pi) / 2.0, c20 = sqrt(5.0 / pi) / 4.0;
+            const double c22 = sqrt(15.0 / pi) / 4.0, c33 = sqrt(35.0 / (2.0 * pi)) / 4.0;
+            const double c32 = sqrt(105.0 / pi) / 2.0, c31 = sqrt(21.0 / (2.0 * pi)) / 4.0, c30 = sqrt(7.0 / pi) / 4.0;
+            const double Y[15] = {c1 * y, c1 * z, c1 * x,
+                                  c2 * x * y, c2 * y * z, c20 * (3 * z * z - 1), c2 * x * z, c22 * (x * x - y * y),
+                                  c33 * y * (3 * x * x - y * y), c32 * x * y * z, c31 * y * (5 * z * z - 1),
+                                  c30 * z * (5 * z * z - 3), c31 * x * (5 * z * z - 1), 0.5 * c32 * z * (x * x - y * y),
+                                  c33 * x * (x * x - 3 * y * y)};
+            const int nk = ws->sh_degree <= 0 ? 0 : (ws->sh_degree == 1 ? 3 : (ws->sh_degree == 2 ? 8 : 15));
+            for (int k = 0; k < 16; ++k) d.Ysh[k] = k < nk ? (float)Y[k] : 0.f;
+        }
         d.inv_dA = (float)(1.0 / in.dA);
         d.inv_cy = (float)(1.0 / (in.dR * tan(in.theta)));
         d.inv_dR = (float)(1.0 / in.dR);
@@ -352,7 +369,10 @@ sdgr_status sdgr_preprocess(sdgr_ws *ws, const float *params, const int64_t *sce
     CK(cudaMemsetAsync(ws->base + L.status, 0, sizeof(StatusDev), s));
     const sdgr_cfg &c = ws->cfg;
     const int pk = prof_begin(ws, SDGR_STAGE_PREPROCESS, s);
-    CK(launch_preprocess(reinterpret_cast<const float4 *>(params), ws->at<ViewDev>(L.views), V, vg, c.cutoff_K,
+    const int sh_count = ws->sh ? (ws->sh_degree <= 0 ? 0 : (ws->sh_degree == 1 ? 3 : (ws->sh_degree == 2 ? 8 : 15))) : 0;
+    CK(launch_preprocess(reinterpret_cast<const float4 *>(params),
+                         sh_count > 0 ? reinterpret_cast<const float4 *>(ws->sh) : nullptr, sh_count,
+                         ws->at<ViewDev>(L.views), V, vg, c.cutoff_K,
                          c.dilation_eps, c.norm_mode, ws->at<CompRec>(L.comp), ws->at<ImgRec>(L.img),
                          ws->at<uint2>(L.rectC), ws->at<uint2>(L.rectI), ws->at<uint32_t>(L.cntC),
                          ws->at<uint32_t>(L.cntI), ws->at<uint32_t>(L.dk0), ws->at<uint32_t>(L.dv0), ws->sms, s));
@@ -449,6 +469,8 @@ sdgr_status sdgr_render_bwd(sdgr_ws *ws, const float *dL_dimages, float *grads, 
         CK(cudaMemsetAsync(accC, 0, (size_t)ws->VG * 2 * sizeof(float4), s));
     }
     if (ws->n_gauss > 0 && !accumulate) CK(cudaMemsetAsync(grads, 0, (size_t)ws->n_gauss * 12 * 4, s));
+    float *dsh = ws->sh ? ws->dsh : nullptr;
+    if (dsh && ws->n_gauss > 0 && !accumulate) CK(cudaMemsetAsync(dsh, 0, (size_t)ws->n_gauss * 16 * 4, s));
     int pk = prof_begin(ws, SDGR_STAGE_SPLAT_BWD, s);
     CK(launch_splat_bwd(ranges + ws->tiles, ws->inst_vals, ws->at<ImgRec>(L.img), dL_dimages, views, ws->V, ws->tiles,
                         cut, st, accI, s));
@@ -461,9 +483,19 @@ sdgr_status sdgr_render_bwd(sdgr_ws *ws, const float *dL_dimages, float *grads, 
     pk = prof_begin(ws, SDGR_STAGE_PARAM_BWD, s);
     CK(launch_param_bwd(reinterpret_cast<const float4 *>(ws->params), views, ws->at<SceneDev>(L.scenes),
                         ws->at<int32_t>(L.scene_views), ws->n_scenes, ws->n_gauss, ws->cfg.dilation_eps,
-                        ws->cfg.norm_mode, ws->at<float>(L.A), accI, accC, st, reinterpret_cast<float4 *>(grads),
-                        ws->sms, s));
+                        ws->cfg.norm_mode, ws->at<float>(L.A), ws->at<CompRec>(L.comp), accI, accC, st,
+                        reinterpret_cast<float4 *>(grads),
+                        reinterpret_cast<float4 *>(dsh), ws->sms, s));
     prof_end(ws, pk, s);
+    return SDGR_OK;
+}
+
+sdgr_status sdgr_set_sh(sdgr_ws *ws, const float *sh, float *dsh, int32_t degree) {
+    if (!ws || degree < 0 || degree > 3) return SDGR_ERR_INVALID;
+    if (((uintptr_t)sh | (uintptr_t)dsh) % 16 != 0) return SDGR_ERR_INVALID;
+    ws->sh = sh;
+    ws->dsh = dsh;
+    ws->sh_degree = sh ? degree : 0;
     return SDGR_OK;
 }
 

@@ -31,8 +31,9 @@ __device__ __forceinline__ void neg_cgc(float a, float b, float c, float p, floa
 __global__ void __launch_bounds__(256)
 k_param_bwd(const float4 *__restrict__ params, const ViewDev *__restrict__ views, const SceneDev *__restrict__ scenes,
             const int32_t *__restrict__ scene_views, int n_scenes, int64_t n_gauss, float eps, int norm_mode,
-            const float *__restrict__ A, const float4 *__restrict__ accI, const float4 *__restrict__ accC,
-            const StatusDev *st, float4 *__restrict__ grads) {
+            const float *__restrict__ A, const CompRec *__restrict__ comp, const float4 *__restrict__ accI,
+            const float4 *__restrict__ accC, const StatusDev *st, float4 *__restrict__ grads,
+            float4 *__restrict__ dsh) {
     if (st->code != SDGR_OK) return;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n_gauss; g += stride) {
@@ -52,6 +53,9 @@ k_param_bwd(const float4 *__restrict__ params, const ViewDev *__restrict__ views
         float dS[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};  // dL/dSigma
         float dmu[3] = {0.f, 0.f, 0.f};
         float go = 0.f, gP = 0.f;
+        float gsh[15];
+#pragma unroll
+        for (int k = 0; k < 15; ++k) gsh[k] = 0.f;
         for (int kv = 0; kv < sc.vcount; ++kv) {
             const ViewDev &vd = views[scene_views[sc.vstart + kv]];
             const int64_t vg = vd.vg_off + (g - vd.g_off);
@@ -80,7 +84,7 @@ k_param_bwd(const float4 *__restrict__ params, const ViewDev *__restrict__ views
             const float4 m0 = accI[2 * vg], m1 = accI[2 * vg + 1];
             const float4 n0 = accC[2 * vg], n1 = accC[2 * vg + 1];
             const float Av = A[vg];
-            const float Ival = p1.w * Av;
+            const float Ival = comp[vg].P * Av;  // P of this view (includes the SH term)
             // imaging plane: moments of dL/dS exp(-delta/2)
             const float dLdI = cn * m0.x;
             const float cI = Ival * cn;
@@ -100,7 +104,12 @@ k_param_bwd(const float4 *__restrict__ params, const ViewDev *__restrict__ views
             float dC00, dC01, dC11;
             neg_cgc(Ca, Cb, Cc, -0.5f * o * n0.w, -0.5f * o * n1.x, -0.5f * o * n1.y, dC00, dC01, dC11);
             go += n0.x;
-            gP += dLdI * Av;
+            const float dLdP = dLdI * Av;  // dL/dP of this view (P depends on the view through SH)
+            gP += dLdP;
+            if (dsh) {
+#pragma unroll
+                for (int k = 0; k < 15; ++k) gsh[k] = fmaf(dLdP, vd.Ysh[k], gsh[k]);
+            }
             // Sigma' = J Sigma_r J^T + eps I  ->  dL/dSigma_r (symmetric)
             float Gr[3][3];
             Gr[0][0] = iA * iA * (dC00 + dI00);
@@ -144,18 +153,29 @@ k_param_bwd(const float4 *__restrict__ params, const ViewDev *__restrict__ views
         grads[3 * g] = a0;
         grads[3 * g + 1] = a1;
         grads[3 * g + 2] = a2;
+        if (dsh) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                float4 d4 = dsh[4 * g + q];
+                d4.x += gsh[4 * q];
+                d4.y += gsh[4 * q + 1];
+                d4.z += gsh[4 * q + 2];
+                if (4 * q + 3 < 15) d4.w += gsh[4 * q + 3];
+                dsh[4 * g + q] = d4;
+            }
+        }
     }
 }
 
 cudaError_t launch_param_bwd(const float4 *params, const ViewDev *views, const SceneDev *scenes,
                              const int32_t *scene_views, int n_scenes, int64_t n_gauss, float eps, int norm_mode,
-                             const float *A, const float4 *accI, const float4 *accC, const StatusDev *st,
-                             float4 *grads, int sms, cudaStream_t s) {
+                             const float *A, const CompRec *comp, const float4 *accI, const float4 *accC,
+                             const StatusDev *st, float4 *grads, float4 *dsh, int sms, cudaStream_t s) {
     if (n_gauss <= 0) return cudaSuccess;
     int64_t blocks = (n_gauss + 255) / 256;
     if (blocks > (int64_t)sms * 8) blocks = (int64_t)sms * 8;
     k_param_bwd<<<(unsigned)blocks, 256, 0, s>>>(params, views, scenes, scene_views, n_scenes, n_gauss, eps, norm_mode,
-                                                  A, accI, accC, st, grads);
+                                                  A, comp, accI, accC, st, grads, dsh);
     note_launch();
     return cudaGetLastError();
 }

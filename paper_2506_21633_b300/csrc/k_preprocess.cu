@@ -70,7 +70,8 @@ __device__ __forceinline__ uint32_t tile_rect(float ux, float uy, float sxx, flo
 }
 
 __global__ void __launch_bounds__(256)
-k_preprocess(const float4 *__restrict__ params, const ViewDev *__restrict__ views, int V, int64_t VG, float K,
+k_preprocess(const float4 *__restrict__ params, const float4 *__restrict__ sh, int sh_count,
+             const ViewDev *__restrict__ views, int V, int64_t VG, float K,
              float eps, int norm_mode, CompRec *__restrict__ comp, ImgRec *__restrict__ img, uint2 *__restrict__ rectC,
              uint2 *__restrict__ rectI, uint32_t *__restrict__ cntC, uint32_t *__restrict__ cntI,
              uint32_t *__restrict__ dkey, uint32_t *__restrict__ dval) {
@@ -142,7 +143,21 @@ k_preprocess(const float4 *__restrict__ params, const ViewDev *__restrict__ view
         cr.qa = -0.5f * LOG2E * (cyy * idC);
         cr.qb = -LOG2E * (-cxy * idC);
         cr.qc = -0.5f * LOG2E * (cxx * idC);
-        cr.o = o; cr.P = p1.w; cr.ry = ellipse_ry(cyy, K);
+        // view-dependent scattering: P + sum_k sh_k Y_k(direction of this view)
+        float P = p1.w;
+        if (sh) {
+            const float4 *row = sh + 4 * g;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                if (4 * q >= sh_count) break;
+                const float4 c4 = __ldg(row + q);
+                P = fmaf(c4.x, vd.Ysh[4 * q], P);
+                P = fmaf(c4.y, vd.Ysh[4 * q + 1], P);
+                P = fmaf(c4.z, vd.Ysh[4 * q + 2], P);
+                P = fmaf(c4.w, vd.Ysh[4 * q + 3], P);
+            }
+        }
+        cr.o = o; cr.P = P; cr.ry = ellipse_ry(cyy, K);
         ImgRec ir;
         ir.ux = uCx; ir.uy = uIy;
         ir.qa = -0.5f * LOG2E * (iyy * idI);
@@ -166,14 +181,15 @@ k_preprocess(const float4 *__restrict__ params, const ViewDev *__restrict__ view
     }
 }
 
-cudaError_t launch_preprocess(const float4 *params, const ViewDev *views, int V, int64_t VG, float K, float eps,
-                              int norm_mode, CompRec *comp, ImgRec *img, uint2 *rectC, uint2 *rectI, uint32_t *cntC,
+cudaError_t launch_preprocess(const float4 *params, const float4 *sh, int sh_count, const ViewDev *views, int V,
+                              int64_t VG, float K, float eps, int norm_mode, CompRec *comp, ImgRec *img, uint2 *rectC, uint2 *rectI, uint32_t *cntC,
                               uint32_t *cntI, uint32_t *dkey, uint32_t *dval, int sms, cudaStream_t s) {
     if (VG <= 0) return cudaSuccess;
     int64_t blocks = (VG + 255) / 256;
     int64_t cap = (int64_t)sms * 8;
     if (blocks > cap) blocks = cap;
-    k_preprocess<<<(unsigned)blocks, 256, 0, s>>>(params, views, V, VG, K, eps, norm_mode, comp, img, rectC, rectI,
+    k_preprocess<<<(unsigned)blocks, 256, 0, s>>>(params, sh, sh_count, views, V, VG, K, eps, norm_mode, comp, img,
+                                                   rectC, rectI,
                                                    cntC, cntI, dkey, dval);
     note_launch();
     return cudaGetLastError();

@@ -40,8 +40,9 @@ struct alignas(16) ViewDev {
     int32_t sblk_off;   // first depth-sort block of this view
     int32_t sblk_n;     // depth-sort blocks of this view
     int32_t pad;
+    float Ysh[16];      // real SH (degrees 1..3) of the direction toward the radar; 0 past the degree
 };
-static_assert(sizeof(ViewDev) == 192, "ViewDev layout");
+static_assert(sizeof(ViewDev) == 256, "ViewDev layout");
 
 struct alignas(16) SceneDev {
     int64_t g_off;      // first Gaussian
@@ -142,8 +143,8 @@ void note_launch();
 
 cudaError_t launch_upload(const void *host_src, size_t bytes, void *dev_dst, cudaStream_t s);
 
-cudaError_t launch_preprocess(const float4 *params, const ViewDev *views, int V, int64_t VG, float K, float eps,
-                              int norm_mode, CompRec *comp, ImgRec *img, uint2 *rectC, uint2 *rectI, uint32_t *cntC,
+cudaError_t launch_preprocess(const float4 *params, const float4 *sh, int sh_count, const ViewDev *views, int V,
+                              int64_t VG, float K, float eps, int norm_mode, CompRec *comp, ImgRec *img, uint2 *rectC, uint2 *rectI, uint32_t *cntC,
                               uint32_t *cntI, uint32_t *dkey, uint32_t *dval, int sms, cudaStream_t s);
 
 // exclusive scans (scratch: see scan_scratch_elems)
@@ -189,8 +190,8 @@ cudaError_t launch_intensity_out(const CompRec *comp, const float *A, int64_t VG
 // parameter adjoint, optimiser, loss
 cudaError_t launch_param_bwd(const float4 *params, const ViewDev *views, const SceneDev *scenes,
                              const int32_t *scene_views, int n_scenes, int64_t n_gauss, float eps, int norm_mode,
-                             const float *A, const float4 *accI, const float4 *accC, const StatusDev *st,
-                             float4 *grads, int sms, cudaStream_t s);
+                             const float *A, const CompRec *comp, const float4 *accI, const float4 *accC,
+                             const StatusDev *st, float4 *grads, float4 *dsh, int sms, cudaStream_t s);
 cudaError_t launch_adam(float4 *p, const float4 *g, float4 *m, float4 *v, int64_t n4, const float *lr, float b1,
                         float b2, float eps, int step, int sms, cudaStream_t s);
 cudaError_t launch_adam_dev(float4 *p, const float4 *g, float4 *m, float4 *v, int64_t n4, const float *lr, float b1,

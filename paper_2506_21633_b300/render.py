@@ -76,6 +76,9 @@ class Renderer:
         self.buf = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
         self.ws = L.sdgr_ws_create(self.buf.data_ptr(), nbytes, self.cfg, caps)
         self.caps = caps
+        pend = getattr(self, "_sh_state", None)
+        if pend is not None:  # the SH binding belongs to the workspace: carry it over
+            L.sdgr_set_sh(self.ws, *pend)
 
     def workspace_bytes(self):
         return 0 if self.buf is None else self.buf.numel()
@@ -132,6 +135,15 @@ class Renderer:
         assert dL_dimages.is_contiguous() and dL_dimages.dtype == torch.float32
         L.sdgr_render_bwd(self.ws, dL_dimages.data_ptr(), grads.data_ptr(), accumulate, _stream_handle(stream))
         return grads
+
+    def set_sh(self, sh=None, dsh=None, degree=0):
+        """View-dependent scattering: sh, dsh cuda float32 [N, 16] (or None);
+        applies to the following prepare()/backward() calls."""
+        self._sh = (sh, dsh)  # keep the tensors alive while the workspace points at them
+        self._sh_state = (sh.data_ptr() if sh is not None else None, dsh.data_ptr() if dsh is not None else None,
+                          degree)
+        if self.ws is not None:
+            L.sdgr_set_sh(self.ws, *self._sh_state)
 
     def count_pairs(self, stream=None):
         """In-cutoff (pixel, Gaussian) pairs (computation plane, imaging plane)

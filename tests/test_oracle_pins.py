@@ -492,3 +492,64 @@ def test_step_matches_render_l1_grad(orc):
     for a, b in zip(imgs, ref_imgs):
         assert np.array_equal(a, b)
     assert np.array_equal(g, ref_g)
+
+
+# ---------------------------------------------------------------------------
+# view-dependent scattering (spherical harmonics of the direction to the radar)
+# ---------------------------------------------------------------------------
+def test_sh_basis_orthonormal(orc):
+    """Gauss-Legendre x uniform-azimuth quadrature (exact for these
+    polynomials) of Y_a Y_b over the sphere is the identity."""
+    nz, nphi = 12, 24
+    z, wz = np.polynomial.legendre.leggauss(nz)
+    G = np.zeros((15, 15))
+    for zi, wi in zip(z, wz):
+        r = math.sqrt(1 - zi * zi)
+        for k in range(nphi):
+            ph = 2 * math.pi * k / nphi
+            Y = orc.sh_basis([r * math.cos(ph), r * math.sin(ph), zi])
+            G += wi * (2 * math.pi / nphi) * np.outer(Y, Y)
+    assert np.abs(G - np.eye(15)).max() < 1e-12
+
+
+def test_sh_degree_zero_and_direction(orc):
+    params = sc.vehicle_box_scene(30, seed=41, extent=(1.0, 1.0, 1.0), log_s_mean=math.log(0.12), center=(0, 0, 0))
+    v = sc.make_view(35.0, 40.0, 0.05, 0.05, 40, 40)
+    sh = np.random.default_rng(1).normal(size=(30, 16))
+    base, A0, _ = orc.render(params, [v], orc.cfg())
+    same, A1, _ = orc.render(params, [v], orc.cfg(sh=sh, sh_degree=0))
+    assert np.array_equal(base[0], same[0])
+    # a pure l=1, m=0 coefficient (c1 z) changes P by c1 * sin(theta): the
+    # direction toward the radar has vertical component sin(theta)
+    sh1 = np.zeros((30, 16))
+    sh1[:, 1] = 1.0
+    d = np.array([math.cos(v["theta"]) * math.cos(v["phi"]), -math.cos(v["theta"]) * math.sin(v["phi"]),
+                  math.sin(v["theta"])])
+    p2 = params.copy()
+    p2[:, 7] += math.sqrt(3 / (4 * math.pi)) * d[2]
+    a, _, _ = orc.render(params, [v], orc.cfg(sh=sh1, sh_degree=1))
+    b, _, _ = orc.render(p2, [v], orc.cfg())
+    assert np.abs(a[0] - b[0]).max() <= 1e-13 * np.abs(b[0]).max()
+
+
+def test_sh_gradients_fd(orc):
+    params = sc.vehicle_box_scene(5, seed=43, extent=(1.0, 0.8, 0.6), log_s_mean=math.log(0.15), center=(0, 0, 0))
+    views = [sc.make_view(25.0, 40.0, 0.06, 0.07, 24, 20), sc.make_view(160.0, 55.0, 0.07, 0.06, 20, 24)]
+    sh = np.random.default_rng(2).normal(scale=0.2, size=(5, 16))
+    G = [np.random.default_rng(3).normal(size=(v["NR"], v["NA"])) for v in views]
+    c = orc.cfg(K=0.0, sh=sh, sh_degree=3)
+    _, dsh = orc.grad_sh(params, views, G, c)
+    def L(shv):
+        imgs, _, _ = orc.render(params, views, orc.cfg(K=0.0, sh=shv, sh_degree=3))
+        return sum(float((g * im).sum()) for g, im in zip(G, imgs))
+    scale = np.abs(dsh).max()
+    assert scale > 0
+    for i in range(5):
+        for k in (0, 1, 4, 7, 11, 14):
+            h = 1e-6
+            a, b = sh.copy(), sh.copy()
+            a[i, k] += h
+            b[i, k] -= h
+            fd = (L(a) - L(b)) / (2 * h)
+            assert abs(fd - dsh[i, k]) <= 1e-6 * scale
+    assert np.all(dsh[:, 15] == 0)

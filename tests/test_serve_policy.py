@@ -72,3 +72,8 @@ def test_cancelled_requests_are_dropped():
     reqs[1].future.cancel()
     s._pending.extend(reqs)
     assert [r.rid for r in s._form_batch()] == [0, 2]
+
+
+def test_sh_degree_schedule():
+    from paper_2506_21633_b300.batch import sh_degree_at
+    assert [sh_degree_at(i) for i in (0, 2499, 2500, 4999, 5000, 7500, 30000)] == [0, 0, 1, 1, 2, 3, 3]
