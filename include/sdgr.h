@@ -197,6 +197,56 @@ sdgr_status sdgr_render_bwd(sdgr_ws *ws, const float *dL_dimages, float *grads, 
  *   misaligned pointers). */
 sdgr_status sdgr_set_sh(sdgr_ws *ws, const float *sh, float *dsh, int32_t degree);
 
+/* Densification and pruning (the "Densification and Pruning Operation" of
+ * Section II-B and the thresholds of Section III-D).  Gradient statistics:
+ * while bound, every sdgr_render_bwd adds, for each Gaussian and each view
+ * in which it received any image-plane weight, the norm of its image-plane
+ * positional gradient |dL/du_I| (pixel units) to accum[i] and 1 to
+ * count[i] (device float32 [max_gaussians]; the caller zeroes them at the
+ * start of an accumulation window).  NULL pointers unbind. */
+sdgr_status sdgr_set_densify_stats(sdgr_ws *ws, float *accum, float *count);
+
+/* Densification rules (all comparisons in float32):
+ * grad_threshold  densify Gaussians with count > 0 and accum/count > it
+ *                 (default 0.003)
+ * dense_scale     densified Gaussians whose largest scale is <= it are
+ *                 cloned (the copy moved by its largest scale along
+ *                 -dL/dmu), larger ones are split in two (children half
+ *                 their largest scale from the centre along that axis,
+ *                 child 0 on the -dL/dmu side, log-scales - ln split_factor)
+ * max_scale       prune if the largest scale exceeds it (0.3 x the
+ *                 illuminated extent)
+ * min_opacity     prune if sigmoid(opacity logit) < it
+ * min_P           prune if P < it (backscattering too small)
+ * split_factor    scale divisor of split children (1.6) */
+typedef struct {
+    float grad_threshold;
+    float dense_scale;
+    float max_scale;
+    float min_opacity;
+    float min_P;
+    float split_factor;
+} sdgr_densify_cfg;
+
+/* Bytes of device scratch sdgr_densify needs for N Gaussians (host only). */
+size_t sdgr_densify_scratch_bytes(int64_t N);
+
+/* Applies the rules to N Gaussians.  In: params, grads (dL/dparams of the
+ * last step; its mean part sets the displacement direction), accum, count
+ * (device, as above), m, v (Adam moments, device [N][12]), sh (device
+ * [N][16] or NULL).  Out: out_params, out_m, out_v (device [out_capacity][12])
+ * and out_sh (device [out_capacity][16], iff sh): Gaussian i's survivors
+ * appear in order -- kept (its moments carried over), kept + clone, or the
+ * two split children -- new Gaussians with zero moments.  scratch: device,
+ * sdgr_densify_scratch_bytes(N) bytes.  *new_N (host) receives the output
+ * count.  Synchronous: waits for `stream` to read the count.
+ * Errors: SDGR_ERR_INVALID; SDGR_ERR_CAPACITY if the output would exceed
+ * out_capacity (*new_N then holds the required count, nothing is written). */
+sdgr_status sdgr_densify(const float *params, const float *grads, const float *accum, const float *count,
+                         const float *m, const float *v, const float *sh, int64_t N, const sdgr_densify_cfg *cfg,
+                         float *out_params, float *out_m, float *out_v, float *out_sh, int64_t out_capacity,
+                         void *scratch, int64_t *new_N, void *stream);
+
 /* Step a13: one Adam step (Kingma & Ba; bias-corrected, eps added to the
  * square root of the corrected second moment, torch.optim.Adam semantics,
  * no weight decay) over N Gaussians.  params, grads, m, v: device

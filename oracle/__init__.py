@@ -42,6 +42,7 @@ class OrcCfg(ctypes.Structure):
         ("K", ctypes.c_double), ("eps", ctypes.c_double), ("T_min", ctypes.c_double),
         ("norm_mode", ctypes.c_int32), ("sh_degree", ctypes.c_int32),
         ("sh", ctypes.POINTER(ctypes.c_double)), ("dsh", ctypes.POINTER(ctypes.c_double)),
+        ("duI", ctypes.POINTER(ctypes.c_double)),
     ]
 
 
@@ -178,6 +179,20 @@ def grad_sh(params, views, dLdS, c, culled=False):
     finally:
         c.dsh = ctypes.POINTER(ctypes.c_double)()
     return g, dsh[:p.shape[0]]
+
+
+def grad_uI(params, views, dLdS, c=None, culled=False):
+    """As grad(), plus dL/du_I (image-plane pixel coordinates) per view and
+    Gaussian, [V, N, 2]."""
+    c = c or cfg()
+    p = _params(params)
+    duI = np.zeros((max(len(views), 1), max(p.shape[0], 1), 2))
+    c.duI = _dp(duI)
+    try:
+        g, dI = grad(p, views, dLdS, c, culled)
+    finally:
+        c.duI = ctypes.POINTER(ctypes.c_double)()
+    return g, dI, duI[:len(views), :p.shape[0]]
 
 
 def step(params, views, targets, c=None, culled=True):

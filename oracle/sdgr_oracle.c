@@ -74,6 +74,7 @@ typedef struct {
     int32_t sh_degree; /* 0..3: degree of the view-dependent scattering */
     const double *sh;  /* [N][16] SH coefficients of degrees 1..3 (NULL: none) */
     double *dsh;       /* [N][16] out: dL/dsh (orc_grad only; NULL: not wanted) */
+    double *duI;       /* [V][N][2] out: dL/du_I per view (orc_grad only; NULL: not wanted) */
 } orc_cfg;
 
 /* View-dependent scattering (the phase function of Section II-B-3, "from the
@@ -547,7 +548,7 @@ typedef struct {
  * ray sums A, intensities I); adds the view's gradient into grads. */
 static int view_adjoint(int N, const orc_view *v, const orc_cfg *cfg, int culled, const orc_gauss *g,
                         const int *order, const double *A, const double *I, const double *dLdS, double *grads,
-                        double *dLdI_out) {
+                        double *dLdI_out, double *duI_out) {
     double K2 = cutoff2(cfg);
     orc_adj *adj = (orc_adj *)calloc((size_t)(N > 0 ? N : 1), sizeof(orc_adj));
     int i;
@@ -724,19 +725,20 @@ static int view_adjoint(int N, const orc_view *v, const orc_cfg *cfg, int culled
         }
         for (k = 0; k < 4; ++k) gr[8 + k] += dq[k];
         if (dLdI_out) dLdI_out[i] = ad->gI;
+        if (duI_out) { duI_out[2 * (size_t)i] = ad->uI[0]; duI_out[2 * (size_t)i + 1] = ad->uI[1]; }
     }
     free(chat); free(adj);
     return 0;
 }
 
 static int view_backward(const double *params, int N, const orc_view *v, const orc_cfg *cfg, int culled,
-                         const double *dLdS, double *grads, double *dLdI_out) {
+                         const double *dLdS, double *grads, double *dLdI_out, double *duI_out) {
     orc_gauss *g = (orc_gauss *)malloc(sizeof(orc_gauss) * (size_t)(N > 0 ? N : 1));
     int *order = (int *)malloc(sizeof(int) * (size_t)(N > 0 ? N : 1));
     double *A = (double *)malloc(sizeof(double) * (size_t)(N > 0 ? N : 1));
     double *I = (double *)malloc(sizeof(double) * (size_t)(N > 0 ? N : 1));
     view_forward(params, N, v, cfg, culled, g, order, A, I, NULL, NULL);
-    view_adjoint(N, v, cfg, culled, g, order, A, I, dLdS, grads, dLdI_out);
+    view_adjoint(N, v, cfg, culled, g, order, A, I, dLdS, grads, dLdI_out, duI_out);
     free(g); free(order); free(A); free(I);
     return 0;
 }
@@ -750,7 +752,8 @@ int orc_grad(const double *params, int32_t N, const orc_view *views, int32_t V, 
     memset(grads, 0, sizeof(double) * 12 * (size_t)N);
     if (cfg->dsh) memset(cfg->dsh, 0, sizeof(double) * 16 * (size_t)N);
     for (v = 0; v < V; ++v) {
-        view_backward(params, N, &views[v], cfg, culled, dLdS + pix, grads, dLdI ? dLdI + (size_t)v * N : NULL);
+        view_backward(params, N, &views[v], cfg, culled, dLdS + pix, grads, dLdI ? dLdI + (size_t)v * N : NULL,
+                      cfg->duI ? cfg->duI + (size_t)v * N * 2 : NULL);
         pix += (size_t)views[v].NA * views[v].NR;
     }
     return 0;
@@ -788,7 +791,7 @@ double orc_step(const double *params, int32_t N, const orc_view *views, int32_t 
     memset(grads, 0, sizeof(double) * 12 * (size_t)N);
     if (cfg->dsh) memset(cfg->dsh, 0, sizeof(double) * 16 * (size_t)N);
     for (v = 0; v < V; ++v) {
-        view_adjoint(N, &views[v], cfg, culled, g[v], order[v], A[v], I[v], dLdS + poff[v], grads, NULL);
+        view_adjoint(N, &views[v], cfg, culled, g[v], order[v], A[v], I[v], dLdS + poff[v], grads, NULL, NULL);
         free(g[v]); free(order[v]); free(A[v]); free(I[v]);
     }
     free(g); free(order); free(A); free(I); free(poff); free(dLdS);

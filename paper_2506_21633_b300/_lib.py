@@ -22,7 +22,8 @@ EXPORTS = (
     "sdgr_bin_sort", "sdgr_render_fwd", "sdgr_render_bwd", "sdgr_adam_step", "sdgr_l1_loss",
     "sdgr_read_status", "sdgr_status_string", "sdgr_profile_enable", "sdgr_profile_read",
     "sdgr_count_pairs", "sdgr_launch_count", "sdgr_render_fwd_noalloc", "sdgr_adam_step_device",
-    "sdgr_copy_status_async", "sdgr_set_sh",
+    "sdgr_copy_status_async", "sdgr_set_sh", "sdgr_set_densify_stats", "sdgr_densify_scratch_bytes",
+    "sdgr_densify",
 )
 
 STAGES = ("preprocess", "depth_sort", "bin", "intensity_fwd", "splat_fwd", "splat_bwd", "intensity_bwd",
@@ -53,6 +54,12 @@ class SdgrCaps(ctypes.Structure):
         ("max_pixels", ctypes.c_int64), ("max_tiles", ctypes.c_int64),
         ("max_instances", ctypes.c_int64),
     ]
+
+
+class SdgrDensifyCfg(ctypes.Structure):
+    _fields_ = [("grad_threshold", ctypes.c_float), ("dense_scale", ctypes.c_float),
+                ("max_scale", ctypes.c_float), ("min_opacity", ctypes.c_float),
+                ("min_P", ctypes.c_float), ("split_factor", ctypes.c_float)]
 
 
 class SdgrError(RuntimeError):
@@ -89,6 +96,10 @@ def lib():
         L.sdgr_read_status.argtypes = [vp, P(ctypes.c_int64)]
         L.sdgr_copy_status_async.argtypes = [vp, vp, vp]
         L.sdgr_set_sh.argtypes = [vp, vp, vp, i32]
+        L.sdgr_set_densify_stats.argtypes = [vp, vp, vp]
+        L.sdgr_densify_scratch_bytes.argtypes = [i64]
+        L.sdgr_densify.argtypes = [vp, vp, vp, vp, vp, vp, vp, i64, P(SdgrDensifyCfg), vp, vp, vp, vp, i64, vp,
+                                   P(ctypes.c_int64), vp]
         L.sdgr_profile_enable.argtypes = [vp, i32]
         L.sdgr_profile_read.argtypes = [vp, P(ctypes.c_double), P(ctypes.c_int64), i32]
         L.sdgr_status_string.argtypes = [ctypes.c_int]
@@ -97,6 +108,7 @@ def lib():
             if name != "sdgr_status_string":
                 getattr(L, name).restype = ctypes.c_int
         L.sdgr_launch_count.restype = ctypes.c_int64
+        L.sdgr_densify_scratch_bytes.restype = ctypes.c_size_t
         _lib = L
     return _lib
 
@@ -206,6 +218,26 @@ def sdgr_adam_step_device(p, g, m, v, N, lr, b1, b2, eps, step_ptr, stream):
 def sdgr_l1_loss(images, targets, npix, dLdS, loss, stream):
     _check("sdgr_l1_loss", lib().sdgr_l1_loss(ctypes.c_void_p(images), ctypes.c_void_p(targets), int(npix),
                                               ctypes.c_void_p(dLdS), ctypes.c_void_p(loss), ctypes.c_void_p(stream)))
+
+
+def sdgr_set_densify_stats(ws, accum_ptr, count_ptr):
+    _check("sdgr_set_densify_stats", lib().sdgr_set_densify_stats(ws, ctypes.c_void_p(accum_ptr or None),
+                                                                  ctypes.c_void_p(count_ptr or None)))
+
+
+def sdgr_densify_scratch_bytes(N):
+    return int(lib().sdgr_densify_scratch_bytes(int(N)))
+
+
+def sdgr_densify(params, grads, accum, count, m, v, sh, N, cfg, out_p, out_m, out_v, out_sh, cap, scratch, stream):
+    """Returns (status code, new_N); pointers as integers (sh/out_sh may be None)."""
+    n = ctypes.c_int64()
+    code = lib().sdgr_densify(*[ctypes.c_void_p(x) for x in (params, grads, accum, count, m, v, sh)], int(N),
+                              ctypes.byref(cfg), *[ctypes.c_void_p(x) for x in (out_p, out_m, out_v, out_sh)],
+                              int(cap), ctypes.c_void_p(scratch), ctypes.byref(n), ctypes.c_void_p(stream))
+    if code not in (SDGR_OK, SDGR_ERR_CAPACITY):
+        raise SdgrError("sdgr_densify", code)
+    return code, n.value
 
 
 def sdgr_set_sh(ws, sh_ptr, dsh_ptr, degree):

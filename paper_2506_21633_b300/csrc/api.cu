@@ -132,6 +132,7 @@ struct sdgr_ws {
     const float *sh = nullptr;  // sdgr_set_sh
     float *dsh = nullptr;
     int sh_degree = 0;
+    float *dens_accum = nullptr, *dens_count = nullptr;  // sdgr_set_densify_stats
     std::vector<ViewDev> hviews;
     std::vector<SceneDev> hscenes;
     std::vector<int32_t> hscene_views;
@@ -485,8 +486,15 @@ sdgr_status sdgr_render_bwd(sdgr_ws *ws, const float *dL_dimages, float *grads, 
                         ws->at<int32_t>(L.scene_views), ws->n_scenes, ws->n_gauss, ws->cfg.dilation_eps,
                         ws->cfg.norm_mode, ws->at<float>(L.A), ws->at<CompRec>(L.comp), accI, accC, st,
                         reinterpret_cast<float4 *>(grads),
-                        reinterpret_cast<float4 *>(dsh), ws->sms, s));
+                        reinterpret_cast<float4 *>(dsh), ws->dens_accum, ws->dens_count, ws->sms, s));
     prof_end(ws, pk, s);
+    return SDGR_OK;
+}
+
+sdgr_status sdgr_set_densify_stats(sdgr_ws *ws, float *accum, float *count) {
+    if (!ws || ((accum == nullptr) != (count == nullptr))) return SDGR_ERR_INVALID;
+    ws->dens_accum = accum;
+    ws->dens_count = count;
     return SDGR_OK;
 }
 

@@ -33,7 +33,7 @@ k_param_bwd(const float4 *__restrict__ params, const ViewDev *__restrict__ views
             const int32_t *__restrict__ scene_views, int n_scenes, int64_t n_gauss, float eps, int norm_mode,
             const float *__restrict__ A, const CompRec *__restrict__ comp, const float4 *__restrict__ accI,
             const float4 *__restrict__ accC, const StatusDev *st, float4 *__restrict__ grads,
-            float4 *__restrict__ dsh) {
+            float4 *__restrict__ dsh, float *__restrict__ dens_accum, float *__restrict__ dens_count) {
     if (st->code != SDGR_OK) return;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n_gauss; g += stride) {
@@ -53,6 +53,7 @@ k_param_bwd(const float4 *__restrict__ params, const ViewDev *__restrict__ views
         float dS[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};  // dL/dSigma
         float dmu[3] = {0.f, 0.f, 0.f};
         float go = 0.f, gP = 0.f;
+        float dacc = 0.f, dcnt = 0.f;  // densification statistics of this call
         float gsh[15];
 #pragma unroll
         for (int k = 0; k < 15; ++k) gsh[k] = 0.f;
@@ -103,6 +104,10 @@ k_param_bwd(const float4 *__restrict__ params, const ViewDev *__restrict__ views
             const float guCy = o * (Cb * n0.y + Cc * n0.z);
             float dC00, dC01, dC11;
             neg_cgc(Ca, Cb, Cc, -0.5f * o * n0.w, -0.5f * o * n1.x, -0.5f * o * n1.y, dC00, dC01, dC11);
+            if (m0.x != 0.f || m0.y != 0.f || m0.z != 0.f) {  // the Gaussian received image-plane weight
+                dacc += sqrtf(guIx * guIx + guIy * guIy);
+                dcnt += 1.f;
+            }
             go += n0.x;
             const float dLdP = dLdI * Av;  // dL/dP of this view (P depends on the view through SH)
             gP += dLdP;
@@ -153,6 +158,10 @@ k_param_bwd(const float4 *__restrict__ params, const ViewDev *__restrict__ views
         grads[3 * g] = a0;
         grads[3 * g + 1] = a1;
         grads[3 * g + 2] = a2;
+        if (dens_accum) {
+            dens_accum[g] += dacc;
+            dens_count[g] += dcnt;
+        }
         if (dsh) {
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
@@ -170,12 +179,13 @@ k_param_bwd(const float4 *__restrict__ params, const ViewDev *__restrict__ views
 cudaError_t launch_param_bwd(const float4 *params, const ViewDev *views, const SceneDev *scenes,
                              const int32_t *scene_views, int n_scenes, int64_t n_gauss, float eps, int norm_mode,
                              const float *A, const CompRec *comp, const float4 *accI, const float4 *accC,
-                             const StatusDev *st, float4 *grads, float4 *dsh, int sms, cudaStream_t s) {
+                             const StatusDev *st, float4 *grads, float4 *dsh, float *dens_accum,
+                             float *dens_count, int sms, cudaStream_t s) {
     if (n_gauss <= 0) return cudaSuccess;
     int64_t blocks = (n_gauss + 255) / 256;
     if (blocks > (int64_t)sms * 8) blocks = (int64_t)sms * 8;
     k_param_bwd<<<(unsigned)blocks, 256, 0, s>>>(params, views, scenes, scene_views, n_scenes, n_gauss, eps, norm_mode,
-                                                  A, comp, accI, accC, st, grads, dsh);
+                                                  A, comp, accI, accC, st, grads, dsh, dens_accum, dens_count);
     note_launch();
     return cudaGetLastError();
 }

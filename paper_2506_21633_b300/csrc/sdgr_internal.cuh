@@ -191,7 +191,8 @@ cudaError_t launch_intensity_out(const CompRec *comp, const float *A, int64_t VG
 cudaError_t launch_param_bwd(const float4 *params, const ViewDev *views, const SceneDev *scenes,
                              const int32_t *scene_views, int n_scenes, int64_t n_gauss, float eps, int norm_mode,
                              const float *A, const CompRec *comp, const float4 *accI, const float4 *accC,
-                             const StatusDev *st, float4 *grads, float4 *dsh, int sms, cudaStream_t s);
+                             const StatusDev *st, float4 *grads, float4 *dsh, float *dens_accum,
+                             float *dens_count, int sms, cudaStream_t s);
 cudaError_t launch_adam(float4 *p, const float4 *g, float4 *m, float4 *v, int64_t n4, const float *lr, float b1,
                         float b2, float eps, int step, int sms, cudaStream_t s);
 cudaError_t launch_adam_dev(float4 *p, const float4 *g, float4 *m, float4 *v, int64_t n4, const float *lr, float b1,

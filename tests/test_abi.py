@@ -13,7 +13,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 def _declared():
     src = open(os.path.join(ROOT, "include", "sdgr.h")).read()
-    return sorted(set(re.findall(r"^(?:sdgr_status|const char \*|int64_t)\s*(sdgr_\w+)\s*\(", src, re.M)))
+    return sorted(set(re.findall(r"^(?:sdgr_status|const char \*|int64_t|size_t)\s*(sdgr_\w+)\s*\(", src, re.M)))
 
 
 @pytest.fixture(scope="module")

@@ -553,3 +553,41 @@ def test_sh_gradients_fd(orc):
             fd = (L(a) - L(b)) / (2 * h)
             assert abs(fd - dsh[i, k]) <= 1e-6 * scale
     assert np.all(dsh[:, 15] == 0)
+
+
+# ---------------------------------------------------------------------------
+# densification and pruning rules
+# ---------------------------------------------------------------------------
+def test_densify_rules():
+    from oracle.densify import densify
+    f = np.float32
+    P = np.zeros((7, 12), f)
+    P[:, 8] = 1.0                       # identity rotations
+    P[:, 3] = 2.0                       # opacity ~0.88
+    P[:, 7] = 0.5
+    P[:, 4:7] = math.log(0.01)
+    P[:, 0] = np.arange(7)              # distinct means
+    P[0, 3] = math.log(0.001 / 0.999)   # opacity 0.001 < 0.005: pruned
+    P[1, 7] = 1e-5                      # P below 1e-3: pruned
+    P[2, 4] = math.log(2.0)             # larger than max_scale 1.0: pruned
+    P[4, 4] = math.log(0.02)            # small, above threshold: cloned
+    P[5, 4:7] = [math.log(0.2), math.log(0.05), math.log(0.05)]   # large: split along x
+    grads = np.zeros((7, 12), f)
+    grads[4, 0:3] = [1.0, 0.0, 0.0]
+    grads[5, 0:3] = [-1.0, 0.0, 0.0]    # -dL/dmu points along +x
+    accum = np.array([1, 1, 1, 0.001, 1, 1, 5.0], f)
+    count = np.array([1, 1, 1, 1, 1, 1, 0], f)   # G6: no views, never densified
+    m = np.full((7, 12), 0.25, f)
+    v = np.full((7, 12), 0.5, f)
+    out, om, ov, _, act = densify(P, grads, accum, count, m, v)
+    assert act == ["prune", "prune", "prune", "keep", "clone", "split", "keep"]
+    assert out.shape == (6, 12)
+    # kept Gaussians keep their moments, new ones start from zero
+    assert np.all(om[0] == 0.25) and np.all(ov[0] == 0.5)
+    # clone: original, then the copy one largest scale along -dL/dmu
+    assert np.allclose(out[1], P[4]) and np.allclose(out[2, 0:3], P[4, 0:3] + [-0.02, 0, 0])
+    assert np.all(om[2] == 0) and np.all(ov[2] == 0)
+    # split: children at +-0.1 along the largest axis, child 0 on the -dL/dmu side, scales / 1.6
+    assert np.allclose(out[3, 0:3], P[5, 0:3] + [0.1, 0, 0]) and np.allclose(out[4, 0:3], P[5, 0:3] - [0.1, 0, 0])
+    assert np.allclose(np.exp(out[3, 4:7]), np.exp(P[5, 4:7]) / 1.6, rtol=1e-6)
+    assert np.allclose(out[5], P[6])
