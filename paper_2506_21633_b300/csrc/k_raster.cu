@@ -3,19 +3,29 @@
 // Section II-A-2, eq. I_i) and the layover splat on the imaging plane
 // (Section II-A-3, eq. S_{n,m}), and their adjoints (Section II-B-1/2).
 //
-// One CTA per 16x16 tile, one thread per pixel (ray).  The tile's instance
-// list is staged through shared memory in batches of 256 Gaussian records.
+// One CTA per 16x16 tile, one thread per pixel (ray); warp w covers the 8x4
+// pixel block with columns 8 (w & 1) .. +7 and rows 4 (w >> 1) .. +3.  The
+// tile's instance list is staged through shared memory in batches of 256.
+//
+// Culling: when a batch is staged, each Gaussian gets the set of the tile's
+// eight pixel blocks that its K-ellipse reaches (found from the ellipse's
+// exact horizontal extent over each band of four rows).  A warp walks only
+// the Gaussians whose set holds its block: per 32 staged Gaussians one ballot
+// gives the warp its hit list, which it visits in list order (front to back
+// for the intensity pass, back to front for its adjoint).
+//
+// Exponent: in a tile, a pixel's exponent of Gaussian i is a quadratic in the
+// pixel's tile-local coordinates (X, Y); the six coefficients are formed when
+// the batch is staged, so a pair costs five FMAs on per-thread constants.
 //
 // Sums over the tile's pixels per Gaussian (the ray sums A_i of the intensity
-// pass and the six moments of the adjoints) use a two-phase transpose
-// instead of warp-shuffle reductions: in phase 1 every thread (pixel) walks a
-// sub-batch of 32 Gaussians in list order and writes each pair's weight into
-// a 32 x 256 shared-memory table; in phase 2 eight threads per Gaussian sum
-// that Gaussian's row of the table (two columns each, only over the rows its
-// K-ellipse can reach), and three shuffles combine the eight partial sums.
-// The table's row stride (264 floats) makes both the phase-1 stores and the
-// phase-2 loads free of bank conflicts.  A warp (two pixel rows) skips a
-// Gaussian whose K-ellipse misses both of its rows.
+// pass and the six moments of the adjoints) use a two-phase transpose instead
+// of warp-shuffle reductions: in phase 1 every pixel writes its weight for
+// each of its hit Gaussians into a 32 x 256 shared-memory table; in phase 2
+// eight threads per Gaussian read the table's entries of that Gaussian's hit
+// blocks (one float4 per thread per block: four rows of one column) and
+// three shuffles combine the eight partial sums.  Entries of blocks that a
+// Gaussian does not reach are never written and never read.
 #include "sdgr_internal.cuh"
 
 namespace sdgr {
@@ -30,6 +40,8 @@ struct TileCtx {
     int px, py;  // this thread's pixel
     bool inside;
     int64_t pix;
+    int toff;    // this pixel's entry in a weight-table row
+    uint32_t valid;  // pixel blocks with at least one pixel inside the image
 };
 
 __device__ __forceinline__ TileCtx tile_ctx(const ViewDev *views, int V, int tile) {
@@ -39,14 +51,57 @@ __device__ __forceinline__ TileCtx tile_ctx(const ViewDev *views, int V, int til
     const int lt = tile - vd.tile_off;
     c.x0 = (lt % vd.tiles_x) * TILE;
     c.y0 = (lt / vd.tiles_x) * TILE;
-    // warp w covers the 8x4 pixel block (columns 8 (w & 1) .. +7, rows
-    // 4 (w >> 1) .. +3); lane l sits at column l & 7, row l >> 3 of it
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
     c.px = c.x0 + 8 * (w & 1) + (l & 7);
     c.py = c.y0 + 4 * (w >> 1) + (l >> 3);
     c.inside = c.px < vd.NA && c.py < vd.NR;
     c.pix = vd.pix_off + (int64_t)c.py * vd.NA + c.px;
+    // table layout inside a block: column-major, so that the four rows of
+    // one column are one float4
+    c.toff = 32 * w + 4 * (l & 7) + (l >> 3);
+    c.valid = 0;
+#pragma unroll
+    for (int b = 0; b < 8; ++b)
+        if (c.x0 + 8 * (b & 1) < vd.NA && c.y0 + 4 * (b >> 1) < vd.NR) c.valid |= 1u << b;
     return c;
+}
+
+// Tile-local pixel coordinates of the thread and their products.
+struct LaneXY {
+    float X, Y, X2, XY, Y2;
+};
+
+__device__ __forceinline__ LaneXY lane_xy() {
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    LaneXY L;
+    L.X = (float)(8 * (w & 1) + (l & 7));
+    L.Y = (float)(4 * (w >> 1) + (l >> 3));
+    L.X2 = L.X * L.X;
+    L.XY = L.X * L.Y;
+    L.Y2 = L.Y * L.Y;
+    return L;
+}
+
+// Exponent coefficients in tile-local coordinates.  With the centre (u, v)
+// relative to the tile origin and the pre-scaled conic (qa, qb, qc), the
+// exponent qa dx^2 + qb dx dy + qc dy^2 at dx = X - u, dy = Y - v equals
+// qa X^2 + qb XY + qc Y^2 + l1 X + l2 Y + c0.  Explicit round-to-nearest
+// intrinsics: every kernel that evaluates a pair must get the same bits (the
+// adjoint rebuilds the transmittance from the forward's factors).
+__device__ __forceinline__ void poly_coeffs(float u, float v, float qa, float qb, float qc, float4 &P, float2 &Q) {
+    const float l1 = -__fmaf_rn(2.f * qa, u, __fmul_rn(qb, v));
+    const float l2 = -__fmaf_rn(2.f * qc, v, __fmul_rn(qb, u));
+    const float c0 = __fmaf_rn(__fmaf_rn(qa, u, __fmul_rn(qb, v)), u, __fmul_rn(__fmul_rn(qc, v), v));
+    P = make_float4(qa, qb, qc, l1);
+    Q = make_float2(l2, c0);
+}
+
+__device__ __forceinline__ float poly_q(const float4 &P, float l2, float c0, const LaneXY &L) {
+    float q = __fmaf_rn(l2, L.Y, c0);
+    q = __fmaf_rn(P.w, L.X, q);
+    q = __fmaf_rn(P.z, L.Y2, q);
+    q = __fmaf_rn(P.y, L.XY, q);
+    return __fmaf_rn(P.x, L.X2, q);
 }
 
 // Tile-local rows [x, y] that the K-ellipse of a Gaussian centred at row uy
@@ -55,83 +110,63 @@ __device__ __forceinline__ int2 tile_rows(float uy, float ry, int y0) {
     float lo = ceilf(uy - ry) - (float)y0, hi = floorf(uy + ry) - (float)y0;
     lo = fminf(fmaxf(lo, 0.f), 16.f);
     hi = fminf(fmaxf(hi, -1.f), 15.f);
-    if (!(lo <= 16.f)) lo = 0.f;  // NaN centre: keep every row, the pair test decides
+    if (!(lo <= 16.f)) lo = 0.f;  // NaN centre: keep every row, the mask test decides
     if (!(hi >= -1.f)) hi = 15.f;
     return make_int2((int)lo, (int)hi);
 }
 
-// Tile-local columns the K-ellipse can reach, from its conic: with the
-// pre-scaled conic (qa, qb, qc) and cut = -K^2 log2(e) / 2, the bounding-box
-// half-width is K sqrt(Sigma_xx) = sqrt(4 cut qc / (4 qa qc - qb^2)).
-__device__ __forceinline__ int2 tile_cols(float ux, float qa, float qb, float qc, float cut, int x0) {
-    const float rx = sqrtf(4.f * cut * qc / (4.f * qa * qc - qb * qb)) * 1.0001f + 1e-3f;
-    return tile_rows(ux, rx, x0);
-}
-
-// Bit w set when the K-ellipse's box reaches the pixel block of warp w.
-__device__ __forceinline__ uint32_t warp_mask(int2 rows, int2 cols) {
+// Pixel blocks of the tile that the K-ellipse reaches.  (u, v): centre
+// relative to the tile origin; q = qa dx^2 + qb dx dy + qc dy^2 (negative
+// definite); rows: the tile rows of the ellipse's bounding box; cutm: the
+// exponent cutoff widened by 1% so that the test stays conservative under
+// rounding.  For a fixed dy the in-cutoff dx form the interval
+// kx dy +- hw(dy), kx = -qb / (2 qa), hw(dy)^2 = (cutm - qs dy^2) / qa,
+// qs = qc - qb^2 / (4 qa).  The right end is concave in dy and peaks at the
+// ellipse's right-most point dy_R = ky dx_R (ky = -qb / (2 qc), dx_R the
+// bounding-box half-width), so over a band of rows it peaks at dy_R clamped
+// into the band; the left end mirrors this at -dy_R.  A block is kept when
+// the band's extent overlaps its eight columns.  NaN records get no block.
+__device__ __forceinline__ uint32_t block_mask(float u, float v, float qa, float qb, float qc, float cutm, int2 rows) {
+    const float kx = -0.5f * __fdividef(qb, qa);
+    const float ky = -0.5f * __fdividef(qb, qc);
+    const float qs = fmaf(0.5f * qb, kx, qc);
+    const float qt = fmaf(0.5f * qb, ky, qa);
+    const float dyR = ky * sqrtf(fmaxf(0.f, __fdividef(cutm, qt)));
+    const float iqa = __fdividef(1.f, qa);
     uint32_t m = 0;
 #pragma unroll
-    for (int w = 0; w < 8; ++w) {
-        const int r0 = 4 * (w >> 1), c0 = 8 * (w & 1);
-        if (rows.y >= r0 && rows.x <= r0 + 3 && cols.y >= c0 && cols.x <= c0 + 7) m |= 1u << w;
+    for (int rb = 0; rb < 4; ++rb) {
+        if (rows.x > 4 * rb + 3 || rows.y < 4 * rb) continue;
+        const float ya = (float)(4 * rb) - v, yb = ya + 3.f;
+        const float tR = fminf(fmaxf(dyR, ya), yb), tL = fminf(fmaxf(-dyR, ya), yb);
+        const float hR = sqrtf(fmaxf(0.f, (cutm - qs * tR * tR) * iqa));
+        const float hL = sqrtf(fmaxf(0.f, (cutm - qs * tL * tL) * iqa));
+        const float xmax = fmaf(kx, tR, hR), xmin = fmaf(kx, tL, -hL);
+        const float xa = -u, xb = 8.f - u;
+        if (xmax >= xa && xmin <= xa + 7.f) m |= 1u << (2 * rb);
+        if (xmax >= xb && xmin <= xb + 7.f) m |= 2u << (2 * rb);
     }
     return m;
 }
 
-__device__ __forceinline__ bool warp_hit(uint32_t mask, int warp) { return (mask >> warp) & 1u; }
-
-// Offset in the weight-table row of tile-local row r, column c (c < 8); the
-// pixel in column c + 8 sits 32 entries further.
-__device__ __forceinline__ int table_idx(int r, int c) { return 64 * (r >> 2) + 8 * (r & 3) + c; }
-
-// Phase 2, one sum: every lane of the group of eight returns the sum of
-// Gaussian (threadIdx.x / 8)'s table row over the rows [rows.x, rows.y].
-// The four groups of a warp loop over the union of their row ranges (rows
-// outside a group's range hold zeros), so every lane reads the same row at
-// the same time: no divergence, no bank conflicts.
-__device__ __forceinline__ int2 warp_union(int2 rows) {
-    return make_int2(__reduce_min_sync(0xffffffffu, rows.x), __reduce_max_sync(0xffffffffu, rows.y));
+// Per-column moments of one block: weights w of rows dy, dy + 1, dy + 2,
+// dy + 3 at column offset dx; adds sum w, w dx, w dy, w dx^2, w dx dy, w dy^2.
+__device__ __forceinline__ void block_moments(const float4 &w, float dx, float dy, float m[6]) {
+    const float sw = (w.x + w.y) + (w.z + w.w);
+    const float s1 = fmaf(3.f, w.w, fmaf(2.f, w.z, w.y));  // sum w_i i
+    const float s2 = fmaf(9.f, w.w, fmaf(4.f, w.z, w.y));  // sum w_i i^2
+    const float py = fmaf(dy, sw, s1);                      // sum w_i (dy + i)
+    const float pyy = fmaf(dy, py + s1, s2);                // sum w_i (dy + i)^2
+    const float px = sw * dx;
+    m[0] += sw;
+    m[1] += px;
+    m[2] += py;
+    m[3] = fmaf(px, dx, m[3]);
+    m[4] = fmaf(py, dx, m[4]);
+    m[5] += pyy;
 }
 
-__device__ __forceinline__ float table_sum(const float *W, int2 rows) {
-    rows = warp_union(rows);
-    const int j = threadIdx.x >> 3, c = threadIdx.x & 7;
-    const float *w = W + j * WSTRIDE + c;  // thread index of pixel (row r, column c) = table_idx(r, c)
-    float s = 0.f;
-    for (int r = rows.x; r <= rows.y; ++r) {
-        const int i = table_idx(r, 0);
-        s += w[i] + w[i + 32];
-    }
-    s += __shfl_xor_sync(0xffffffffu, s, 1);
-    s += __shfl_xor_sync(0xffffffffu, s, 2);
-    s += __shfl_xor_sync(0xffffffffu, s, 4);
-    return s;
-}
-
-// Phase 2, six moments of the weights w over the pixels: sum w, w dx, w dy,
-// w dx^2, w dx dy, w dy^2 with (dx, dy) = pixel - centre.  dx0 = offset of
-// the thread's first column (x0 + c - ux), dy0 = y0 - uy.
-__device__ __forceinline__ void table_moments(const float *W, int2 rows, float dx0, float dy0, float m[6]) {
-    rows = warp_union(rows);
-    const int j = threadIdx.x >> 3, c = threadIdx.x & 7;
-    const float *w = W + j * WSTRIDE + c;
-    const float dx1 = dx0 + 8.f;
-    float m0 = 0.f, mx = 0.f, my = 0.f, mxx = 0.f, mxy = 0.f, myy = 0.f;
-    for (int r = rows.x; r <= rows.y; ++r) {
-        const float dy = dy0 + (float)r;
-        const int i = table_idx(r, 0);
-        const float w0 = w[i], w1 = w[i + 32];
-        const float a0 = w0 * dx0, a1 = w1 * dx1;
-        const float ws = w0 + w1, as = a0 + a1;
-        m0 += ws;
-        mx += as;
-        my = fmaf(ws, dy, my);
-        mxx = fmaf(a0, dx0, fmaf(a1, dx1, mxx));
-        mxy = fmaf(as, dy, mxy);
-        myy = fmaf(ws * dy, dy, myy);
-    }
-    m[0] = m0; m[1] = mx; m[2] = my; m[3] = mxx; m[4] = mxy; m[5] = myy;
+__device__ __forceinline__ void reduce8(float m[6]) {
 #pragma unroll
     for (int q = 0; q < 6; ++q) {
         m[q] += __shfl_xor_sync(0xffffffffu, m[q], 1);
@@ -148,78 +183,114 @@ __device__ __forceinline__ void add_moments(float4 *acc, uint32_t vg, const floa
     }
 }
 
+// Hit list of this warp among the staged Gaussians [k0, k0 + n) (n <= 32).
+__device__ __forceinline__ uint32_t warp_hits(const uint32_t *sM, int k0, int n) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const bool h = lane < n && ((sM[k0 + (lane < n ? lane : 0)] >> warp) & 1u);
+    return __ballot_sync(0xffffffffu, h);
+}
+
+__device__ __forceinline__ float cut_margin(float cut) { return cut * 1.01f; }
+
+// Stage one computation-plane record: exponent coefficients, block set and
+// the Gaussian's (view, Gaussian) slot.
+__device__ __forceinline__ void stage_comp(const CompRec *__restrict__ comp, uint32_t vg, const TileCtx &c, float cutm,
+                                           float4 &P, float2 &Q, uint32_t &mask, float2 &uv, float2 &oP) {
+    const float4 *cp = reinterpret_cast<const float4 *>(comp + vg);
+    const float4 c0 = cp[0], c1 = cp[1];  // (ux, uy, qa, qb), (qc, o, P, ry)
+    oP = make_float2(c1.y, c1.z);
+    const float u = __fsub_rn(c0.x, (float)c.x0), v = __fsub_rn(c0.y, (float)c.y0);
+    poly_coeffs(u, v, c0.z, c0.w, c1.x, P, Q);
+    mask = block_mask(u, v, c0.z, c0.w, c1.x, cutm, tile_rows(c0.y, c1.w, c.y0)) & c.valid;
+    uv = make_float2(u, v);
+}
+
 // ---------------------------------------------------------------------------
 // a7: intensity pass.  Per ray (cell centre): T = 1; for each Gaussian in
 // depth order: alpha = o exp(-delta/2) within the cutoff; the Gaussian
 // receives alpha T; T *= 1 - alpha.  The ray stops once T < Tfloor.  For the
-// adjoint each ray records the index just past its last in-cutoff Gaussian
-// and the transmittance in front of that Gaussian.
+// adjoint each ray records where it stopped: last = index + 1 of the Gaussian
+// at which T fell below the floor and Tstop = the transmittance in front of
+// it; or last = 0 and Tstop = the transmittance behind the whole list.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256)
 k_intensity_fwd(const uint2 *__restrict__ ranges, const uint32_t *__restrict__ vals, const CompRec *__restrict__ comp,
                 const ViewDev *__restrict__ views, int V, float cut, float Tfloor, const StatusDev *st,
                 float *__restrict__ A, float *__restrict__ Tstop, int32_t *__restrict__ last) {
     if (st->code != SDGR_OK) return;
-    __shared__ float4 sA[BATCH];
-    __shared__ float2 sB[BATCH];
-    __shared__ int2 sR[BATCH];
+    __shared__ float4 sP[BATCH];  // (qa, qb, qc, l1)
+    __shared__ float4 sQ[BATCH];  // (l2, c0, o, -)
     __shared__ uint32_t sM[BATCH];
     __shared__ uint32_t sid[BATCH];
-    __shared__ float W[SUB * WSTRIDE];
-    const int t = threadIdx.x, warp = t >> 5;
+    __shared__ __align__(16) float W[SUB * WSTRIDE];
+    const int t = threadIdx.x;
     const TileCtx c = tile_ctx(views, V, blockIdx.x);
+    const LaneXY L = lane_xy();
     const uint2 r = ranges[blockIdx.x];
-    const float fx = (float)c.px, fy = (float)c.py;
-    float T = 1.f, Tprev = 1.f;
+    const float cutm = cut_margin(cut);
+    float T = 1.f, Tst = 0.f;
     int32_t lastj = 0;
     bool done = !c.inside;
     for (uint32_t base = r.x; base < r.y; base += BATCH) {
         if (__syncthreads_count(done) == (int)blockDim.x) break;
-        const uint32_t jload = base + t;
-        if (jload < r.y) {
-            const uint32_t vg = vals[jload];
-            const float4 *cp = reinterpret_cast<const float4 *>(comp + vg);
-            const float4 c0 = cp[0], c1 = cp[1];
-            sA[t] = c0;
-            sB[t] = make_float2(c1.x, c1.y);
-            const int2 rows = tile_rows(c0.y, c1.w, c.y0);
-            sR[t] = rows;
-            sM[t] = warp_mask(rows, tile_cols(c0.x, c0.z, c0.w, c1.x, cut, c.x0));
+        if (base + t < r.y) {
+            const uint32_t vg = vals[base + t];
+            float4 P;
+            float2 Q, uv, oP;
+            uint32_t m;
+            stage_comp(comp, vg, c, cutm, P, Q, m, uv, oP);
+            sP[t] = P;
+            sQ[t] = make_float4(Q.x, Q.y, oP.x, 0.f);
+            sM[t] = m;
             sid[t] = vg;
         }
         __syncthreads();
         const int nb = min(BATCH, (int)(r.y - base));
         for (int sub = 0; sub < nb; sub += SUB) {
             const int ns = min(SUB, nb - sub);
-#pragma unroll 4
-            for (int jj = 0; jj < ns; ++jj) {
-                const int k = sub + jj;
+            uint32_t hm = warp_hits(sM, sub, ns);
+            while (hm) {
+                const int jj = __ffs(hm) - 1;
+                hm &= hm - 1;
+                const float4 P = sP[sub + jj];
+                const float4 Q = sQ[sub + jj];
+                const float q = poly_q(P, Q.x, Q.y, L);
                 float contrib = 0.f;
-                if (warp_hit(sM[k], warp) && !done) {
-                    const float4 a = sA[k];
-                    const float2 b = sB[k];
-                    const float dx = __fsub_rn(fx, a.x), dy = __fsub_rn(fy, a.y);
-                    const float q = gauss_q(a.z, a.w, b.x, dx, dy);
-                    if (q >= cut) {
-                        const float alpha = __fmul_rn(b.y, ex2_approx(q));
-                        contrib = __fmul_rn(alpha, T);
-                        Tprev = T;
-                        lastj = (int32_t)(base + k + 1);
-                        T = __fmul_rn(T, __fsub_rn(1.f, alpha));
-                        if (T < Tfloor) done = true;
+                if (q >= cut && !done) {
+                    const float alpha = __fmul_rn(Q.z, ex2_approx(q));
+                    contrib = __fmul_rn(alpha, T);
+                    const float Tn = __fmaf_rn(-alpha, T, T);  // T (1 - alpha), one rounding
+                    if (Tn < Tfloor) {
+                        done = true;
+                        Tst = T;
+                        lastj = (int32_t)(base + sub + jj + 1);
                     }
+                    T = Tn;
                 }
-                W[jj * WSTRIDE + t] = contrib;
+                W[jj * WSTRIDE + c.toff] = contrib;
             }
             __syncthreads();
-            const int j = t >> 3;
-            const float s = table_sum(W, j < ns ? sR[sub + j] : make_int2(16, -1));
-            if ((t & 7) == 0 && j < ns && s != 0.f) atomicAdd(&A[sid[sub + j]], s);
+            const int j = t >> 3, cc = t & 7;
+            uint32_t mb = j < ns ? sM[sub + j] : 0u;
+            const float *wr = W + j * WSTRIDE + 4 * cc;
+            float s = 0.f;
+            while (__any_sync(0xffffffffu, mb)) {
+                if (mb) {
+                    const int b = __ffs(mb) - 1;
+                    mb &= mb - 1;
+                    const float4 w4 = *reinterpret_cast<const float4 *>(wr + 32 * b);
+                    s += (w4.x + w4.y) + (w4.z + w4.w);
+                }
+            }
+            s += __shfl_xor_sync(0xffffffffu, s, 1);
+            s += __shfl_xor_sync(0xffffffffu, s, 2);
+            s += __shfl_xor_sync(0xffffffffu, s, 4);
+            if (cc == 0 && j < ns && s != 0.f) atomicAdd(&A[sid[sub + j]], s);
             __syncthreads();
         }
     }
     if (c.inside) {
-        Tstop[c.pix] = Tprev;
+        Tstop[c.pix] = lastj ? Tst : T;
         last[c.pix] = lastj;
     }
 }
@@ -233,42 +304,62 @@ cudaError_t launch_intensity_fwd(const uint2 *ranges, const uint32_t *vals, cons
     return cudaGetLastError();
 }
 
+// Stage one imaging-plane record.
+__device__ __forceinline__ void stage_img(const ImgRec *__restrict__ img, uint32_t vg, const TileCtx &c, float cutm,
+                                          float4 &G, float2 &uv, float &cn, uint32_t &mask) {
+    const float4 *ip = reinterpret_cast<const float4 *>(img + vg);
+    const float4 i0 = ip[0], i1 = ip[1];  // (ux, uy, qa, qb), (qc, cn, ry, -)
+    const float u = __fsub_rn(i0.x, (float)c.x0), v = __fsub_rn(i0.y, (float)c.y0);
+    G = make_float4(i0.z, i0.w, i1.x, 0.f);
+    uv = make_float2(u, v);
+    cn = i1.y;
+    mask = block_mask(u, v, i0.z, i0.w, i1.x, cutm, tile_rows(i0.y, i1.z, c.y0)) & c.valid;
+}
+
 // ---------------------------------------------------------------------------
 // a8: imaging splat.  S[pixel] = sum_i c_i exp(-delta_I/2) I_i, I_i = P_i A_i.
-// Each pixel gathers; no reduction is needed.
+// Each pixel gathers over its warp's hit list; no reduction is needed.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256)
 k_splat_fwd(const uint2 *__restrict__ rangesI, const uint32_t *__restrict__ vals, const ImgRec *__restrict__ img,
             const CompRec *__restrict__ comp, const float *__restrict__ A, const ViewDev *__restrict__ views, int V,
             float cut, const StatusDev *st, float *__restrict__ images) {
-    __shared__ float4 sA[BATCH];
-    __shared__ float2 sB[BATCH];
+    __shared__ float4 sP[BATCH];  // (qa, qb, qc, l1)
+    __shared__ float4 sQ[BATCH];  // (l2, c0, c I, -)
     __shared__ uint32_t sM[BATCH];
-    const int t = threadIdx.x, warp = t >> 5;
+    const int t = threadIdx.x;
     const TileCtx c = tile_ctx(views, V, blockIdx.x);
+    const LaneXY L = lane_xy();
     const bool ok = st->code == SDGR_OK;
     const uint2 r = ok ? rangesI[blockIdx.x] : make_uint2(0u, 0u);
-    const float fx = (float)c.px, fy = (float)c.py;
+    const float cutm = cut_margin(cut);
     float acc = 0.f;
     for (uint32_t base = r.x; base < r.y; base += BATCH) {
         __syncthreads();
-        const uint32_t j = base + t;
-        if (j < r.y) {
-            const uint32_t vg = vals[j];
-            const float4 *ip = reinterpret_cast<const float4 *>(img + vg);
-            const float4 i0 = ip[0], i1 = ip[1];
-            sA[t] = i0;
-            sB[t] = make_float2(i1.x, i1.y * comp[vg].P * A[vg]);
-            sM[t] = warp_mask(tile_rows(i0.y, i1.z, c.y0), tile_cols(i0.x, i0.z, i0.w, i1.x, cut, c.x0));
+        if (base + t < r.y) {
+            const uint32_t vg = vals[base + t];
+            float4 G, P;
+            float2 uv, Q;
+            float cn;
+            uint32_t m;
+            stage_img(img, vg, c, cutm, G, uv, cn, m);
+            poly_coeffs(uv.x, uv.y, G.x, G.y, G.z, P, Q);
+            sP[t] = P;
+            sQ[t] = make_float4(Q.x, Q.y, cn * comp[vg].P * A[vg], 0.f);
+            sM[t] = m;
         }
         __syncthreads();
         const int nb = min(BATCH, (int)(r.y - base));
-        for (int k = 0; k < nb; ++k) {
-            if (!warp_hit(sM[k], warp)) continue;
-            const float4 a = sA[k];
-            const float2 b = sB[k];
-            const float q = gauss_q(a.z, a.w, b.x, fx - a.x, fy - a.y);
-            if (q >= cut) acc = fmaf(b.y, ex2_approx(q), acc);
+        for (int k0 = 0; k0 < nb; k0 += 32) {
+            uint32_t hm = warp_hits(sM, k0, min(32, nb - k0));
+            while (hm) {
+                const int k = k0 + __ffs(hm) - 1;
+                hm &= hm - 1;
+                const float4 P = sP[k];
+                const float4 Q = sQ[k];
+                const float q = poly_q(P, Q.x, Q.y, L);
+                if (q >= cut) acc = fmaf(Q.z, ex2_approx(q), acc);
+            }
         }
     }
     if (c.inside) images[c.pix] = acc;
@@ -288,83 +379,79 @@ cudaError_t launch_splat_fwd(const uint2 *rangesI, const uint32_t *vals, const I
 // w = dL/dS * exp(-delta_I/2); the parameter adjoint turns them into
 // dL/dI = c M0, dL/du_I, dL/dconic_I and dL/dc.  No pixel depends on
 // another here, so the kernel is Gaussian-parallel: eight threads per
-// Gaussian, each taking two columns (c, c + 8) of the rows its K-ellipse can
-// reach; along a column the exponent is a quadratic in dy evaluated with two
-// FMAs; dL/dS comes from shared memory; three shuffles combine the eight
-// partial moments.
+// Gaussian walk its hit blocks, each thread one column (four rows) per block,
+// with dL/dS read from shared memory as one float4; three shuffles combine
+// the eight partial moments.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256)
 k_splat_bwd(const uint2 *__restrict__ rangesI, const uint32_t *__restrict__ vals, const ImgRec *__restrict__ img,
             const float *__restrict__ dLdS, const ViewDev *__restrict__ views, int V, float cut, const StatusDev *st,
             float4 *__restrict__ accI) {
     if (st->code != SDGR_OK) return;
-    __shared__ float4 sA[BATCH];
-    __shared__ float sC[BATCH];
-    __shared__ int4 sRC[BATCH];  // tile-local rows (x, y) and columns (z, w) the ellipse can reach
+    __shared__ float4 sG[BATCH];  // (qa, qb, qc, -)
+    __shared__ float2 sU[BATCH];  // tile-local centre
+    __shared__ uint32_t sM[BATCH];
     __shared__ uint32_t sid[BATCH];
-    __shared__ float sg[TILE_PIX];  // dL/dS of the tile's pixels, by thread index
+    __shared__ __align__(16) float sg[TILE_PIX];  // dL/dS of the tile's pixels, in table layout
     const int t = threadIdx.x;
     const TileCtx c = tile_ctx(views, V, blockIdx.x);
     const uint2 r = rangesI[blockIdx.x];
     const float g = c.inside ? dLdS[c.pix] : 0.f;
-    sg[t] = g;
+    sg[c.toff] = g;
     if (__syncthreads_count(g != 0.f) == 0) return;
-    const int col = t & 7;
-    const float colx = (float)(c.x0 + col);
+    const float cutm = cut_margin(cut);
+    const int cc = t & 7;
     for (uint32_t base = r.x; base < r.y; base += BATCH) {
         __syncthreads();
-        const uint32_t jload = base + t;
-        if (jload < r.y) {
-            const uint32_t vg = vals[jload];
-            const float4 *ip = reinterpret_cast<const float4 *>(img + vg);
-            const float4 i0 = ip[0], i1 = ip[1];
-            sA[t] = i0;
-            sC[t] = i1.x;
-            const int2 rows = tile_rows(i0.y, i1.z, c.y0);
-            const int2 cols = tile_cols(i0.x, i0.z, i0.w, i1.x, cut, c.x0);
-            sRC[t] = make_int4(rows.x, rows.y, cols.x, cols.y);
+        if (base + t < r.y) {
+            const uint32_t vg = vals[base + t];
+            float4 G;
+            float2 uv;
+            float cn;
+            uint32_t m;
+            stage_img(img, vg, c, cutm, G, uv, cn, m);
+            sG[t] = G;
+            sU[t] = uv;
+            sM[t] = m;
             sid[t] = vg;
         }
         __syncthreads();
         const int nb = min(BATCH, (int)(r.y - base));
         for (int j0 = 0; j0 < nb; j0 += 32) {
             const int k = j0 + (t >> 3);
-            float m0 = 0.f, mx = 0.f, my = 0.f, mxx = 0.f, mxy = 0.f, myy = 0.f;
-            if (k < nb) {
-                const float4 a = sA[k];
-                const float qc = sC[k];
-                const int4 rc = sRC[k];
-                const float dxa = colx - a.x, dxb = dxa + 8.f;
-                // exponent along a column: qa dx^2 + (qb dx) dy + qc dy^2
-                const float Aa = a.z * dxa * dxa, Ba = a.w * dxa;
-                const float Ab = a.z * dxb * dxb, Bb = a.w * dxb;
-                const bool va = col >= rc.z && col <= rc.w, vb = col + 8 >= rc.z && col + 8 <= rc.w;
-                const float dy0 = (float)c.y0 - a.y;
-                for (int rr = rc.x; rr <= rc.y; ++rr) {
-                    const float dy = dy0 + (float)rr;
-                    const int i = table_idx(rr, col);
-                    const float qa_ = fmaf(dy, fmaf(qc, dy, Ba), Aa);
-                    const float qb_ = fmaf(dy, fmaf(qc, dy, Bb), Ab);
-                    const float wa = (va && qa_ >= cut) ? sg[i] * ex2_approx(qa_) : 0.f;
-                    const float wb = (vb && qb_ >= cut) ? sg[i + 32] * ex2_approx(qb_) : 0.f;
-                    const float xa = wa * dxa, xb = wb * dxb;
-                    const float ws = wa + wb, xs = xa + xb;
-                    m0 += ws;
-                    mx += xs;
-                    my = fmaf(ws, dy, my);
-                    mxx = fmaf(xa, dxa, fmaf(xb, dxb, mxx));
-                    mxy = fmaf(xs, dy, mxy);
-                    myy = fmaf(ws * dy, dy, myy);
+            const int ks = k < nb ? k : j0;
+            uint32_t mb = k < nb ? sM[k] : 0u;
+            const float4 G = sG[ks];
+            const float2 uv = sU[ks];
+            const float dx0 = (float)cc - uv.x, dy00 = -uv.y;
+            float m[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            while (__any_sync(0xffffffffu, mb)) {
+                if (mb) {
+                    const int b = __ffs(mb) - 1;
+                    mb &= mb - 1;
+                    const float dx = dx0 + (float)(8 * (b & 1));
+                    const float dy0 = dy00 + (float)(4 * (b >> 1));
+                    const float4 g4 = *reinterpret_cast<const float4 *>(sg + 32 * b + 4 * cc);
+                    // exponent along the column: qa dx^2 + (qb dx) dy + qc dy^2
+                    const float Aq = G.x * dx * dx, Bq = G.y * dx;
+                    float4 w;
+                    float dy = dy0, q;
+                    q = fmaf(fmaf(G.z, dy, Bq), dy, Aq);
+                    w.x = q >= cut ? g4.x * ex2_approx(q) : 0.f;
+                    dy += 1.f;
+                    q = fmaf(fmaf(G.z, dy, Bq), dy, Aq);
+                    w.y = q >= cut ? g4.y * ex2_approx(q) : 0.f;
+                    dy += 1.f;
+                    q = fmaf(fmaf(G.z, dy, Bq), dy, Aq);
+                    w.z = q >= cut ? g4.z * ex2_approx(q) : 0.f;
+                    dy += 1.f;
+                    q = fmaf(fmaf(G.z, dy, Bq), dy, Aq);
+                    w.w = q >= cut ? g4.w * ex2_approx(q) : 0.f;
+                    block_moments(w, dx, dy0, m);
                 }
             }
-            float m[6] = {m0, mx, my, mxx, mxy, myy};
-#pragma unroll
-            for (int q = 0; q < 6; ++q) {
-                m[q] += __shfl_xor_sync(0xffffffffu, m[q], 1);
-                m[q] += __shfl_xor_sync(0xffffffffu, m[q], 2);
-                m[q] += __shfl_xor_sync(0xffffffffu, m[q], 4);
-            }
-            if (col == 0 && k < nb) add_moments(accI, sid[k], m);
+            reduce8(m);
+            if (cc == 0 && k < nb) add_moments(accI, sid[k], m);
         }
     }
 }
@@ -382,11 +469,13 @@ cudaError_t launch_splat_bwd(const uint2 *rangesI, const uint32_t *vals, const I
 // a11: adjoint of the intensity pass.  With chat_i = dL/dI_i P_i the ray's
 // share of L is sum_i chat_i alpha_i T_i, so dL/dalpha_i = T_i (chat_i - B_i),
 // B_i = sum_{j>i} chat_j alpha_j prod_{i<k<j}(1 - alpha_k).  Each ray walks
-// its list back to front from the last in-cutoff Gaussian the forward pass
-// recorded: B by the suffix recursion B <- chat alpha + (1 - alpha) B, T by
-// undoing the forward products (T_i = T_{i+1} / (1 - alpha_i), with the same
-// float bits of alpha and the same skipped pairs as the forward; every
-// factor is > 0 because T_{i+1} >= Tfloor).  Per (view, Gaussian) the
+// its hit list back to front: B by the suffix recursion
+// B <- B + alpha (chat - B), T by undoing the forward products
+// (T_i = T_{i+1} / (1 - alpha_i), with the same float bits of alpha and the
+// same skipped pairs as the forward).  A ray that stopped starts at its
+// stopping Gaussian with the recorded T in front of it; any other starts at
+// the list end with the transmittance behind the list.  Every divisor is
+// > 0: each T the forward kept is >= Tfloor.  Per (view, Gaussian) the
 // moments of w = dL/dalpha exp(-delta_C/2).
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256)
@@ -395,77 +484,90 @@ k_intensity_bwd(const uint2 *__restrict__ ranges, const uint32_t *__restrict__ v
                 const int32_t *__restrict__ last, const ViewDev *__restrict__ views, int V, float cut,
                 const StatusDev *st, float4 *__restrict__ accC) {
     if (st->code != SDGR_OK) return;
-    __shared__ float4 sA[BATCH];
-    __shared__ float4 sB[BATCH];
-    __shared__ int2 sR[BATCH];
+    __shared__ float4 sP[BATCH];  // (qa, qb, qc, l1)
+    __shared__ float4 sQ[BATCH];  // (l2, c0, o, chat)
+    __shared__ float2 sU[BATCH];  // tile-local centre
     __shared__ uint32_t sM[BATCH];
     __shared__ uint32_t sid[BATCH];
-    __shared__ float W[SUB * WSTRIDE];
+    __shared__ __align__(16) float W[SUB * WSTRIDE];
     __shared__ int smax;
-    const int t = threadIdx.x, warp = t >> 5;
+    const int t = threadIdx.x;
     const TileCtx c = tile_ctx(views, V, blockIdx.x);
+    const LaneXY L = lane_xy();
     const uint2 r = ranges[blockIdx.x];
-    const float fx = (float)c.px, fy = (float)c.py;
-    const int32_t mylast = c.inside ? last[c.pix] : 0;
+    const int32_t rec = c.inside ? last[c.pix] : 0;
+    // exclusive end of this ray's list; rays outside the image take none
+    const int32_t mylast = !c.inside ? (int32_t)r.x : (rec > 0 ? rec : (int32_t)r.y);
     float T = c.inside ? Tstop[c.pix] : 0.f;
-    if (t == 0) smax = 0;
+    bool first = rec > 0;
+    if (t == 0) smax = (int)r.x;
     __syncthreads();
-    if (mylast > 0) atomicMax(&smax, mylast);
+    if (mylast > (int32_t)r.x) atomicMax(&smax, mylast);
     __syncthreads();
     const int hi0 = smax;
-    const float colx = (float)(c.x0 + (t & 7));
+    const float cutm = cut_margin(cut);
     float B = 0.f;
-    bool first = true;
     for (int hi = hi0; hi > (int)r.x; hi -= BATCH) {
         const int lo = max((int)r.x, hi - BATCH);
         const int nb = hi - lo;
         __syncthreads();
         if (t < nb) {
             const uint32_t vg = vals[lo + t];
-            const float4 *cp = reinterpret_cast<const float4 *>(comp + vg);
-            const float4 c0 = cp[0], c1 = cp[1];
+            float4 P;
+            float2 Q, uv, oP;
+            uint32_t m;
+            stage_comp(comp, vg, c, cutm, P, Q, m, uv, oP);
             const float dLdI = accI[2 * (size_t)vg].x * img[vg].cn;
-            sA[t] = c0;
-            sB[t] = make_float4(c1.x, c1.y, dLdI * c1.z, 0.f);
-            const int2 rows = tile_rows(c0.y, c1.w, c.y0);
-            sR[t] = rows;
-            sM[t] = warp_mask(rows, tile_cols(c0.x, c0.z, c0.w, c1.x, cut, c.x0));
+            sP[t] = P;
+            sQ[t] = make_float4(Q.x, Q.y, oP.x, dLdI * oP.y);
+            sU[t] = uv;
+            sM[t] = m;
             sid[t] = vg;
         }
         __syncthreads();
+        const int lim = mylast - lo;  // this ray takes staged Gaussians k < lim
         for (int send = nb; send > 0; send -= SUB) {
             const int sub = max(0, send - SUB);
             const int ns = send - sub;
-#pragma unroll 4
-            for (int jj = ns - 1; jj >= 0; --jj) {
+            uint32_t hm = warp_hits(sM, sub, ns);
+            while (hm) {
+                const int jj = 31 - __clz(hm);
+                hm ^= 1u << jj;
                 const int k = sub + jj;
+                const float4 P = sP[k];
+                const float4 Q = sQ[k];
+                const float q = poly_q(P, Q.x, Q.y, L);
                 float w = 0.f;
-                if (warp_hit(sM[k], warp) && lo + k < mylast) {
-                    const float4 a = sA[k];
-                    const float4 b = sB[k];
-                    const float dx = __fsub_rn(fx, a.x), dy = __fsub_rn(fy, a.y);
-                    const float q = gauss_q(a.z, a.w, b.x, dx, dy);
-                    if (q >= cut) {
-                        const float e = ex2_approx(q);
-                        const float alpha = __fmul_rn(b.y, e);
-                        // relative error of a few ulp per step; the forward's rounding
-                        // of 1 - alpha is undone exactly because both sides share it
-                        if (!first) T = __fdividef(T, __fsub_rn(1.f, alpha));
-                        first = false;
-                        const float chat = b.z;
-                        const float ga = T * (chat - B);
-                        B = fmaf(chat, alpha, (1.f - alpha) * B);
-                        w = ga * e;
-                    }
+                if (q >= cut && k < lim) {
+                    const float e = ex2_approx(q);
+                    const float alpha = __fmul_rn(Q.z, e);
+                    // relative error of a few ulp per step; the factor 1 - alpha
+                    // is the forward's (same alpha bits, exact subtraction)
+                    if (!first) T = __fdividef(T, __fsub_rn(1.f, alpha));
+                    first = false;
+                    const float d = Q.w - B;
+                    B = fmaf(alpha, d, B);
+                    w = T * d * e;
                 }
-                W[jj * WSTRIDE + t] = w;
+                W[jj * WSTRIDE + c.toff] = w;
             }
             __syncthreads();
-            const int j = t >> 3;
-            float m[6];
-            const float4 a = sA[sub + (j < ns ? j : 0)];
-            table_moments(W, j < ns ? sR[sub + j] : make_int2(16, -1), colx - a.x, (float)c.y0 - a.y, m);
-            if ((t & 7) == 0 && j < ns) add_moments(accC, sid[sub + j], m);
+            const int j = t >> 3, cc = t & 7;
+            uint32_t mb = j < ns ? sM[sub + j] : 0u;
+            const float2 uv = sU[sub + (j < ns ? j : 0)];
+            const float dx0 = (float)cc - uv.x, dy00 = -uv.y;
+            const float *wr = W + j * WSTRIDE + 4 * cc;
+            float m[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            while (__any_sync(0xffffffffu, mb)) {
+                if (mb) {
+                    const int b = __ffs(mb) - 1;
+                    mb &= mb - 1;
+                    const float4 w4 = *reinterpret_cast<const float4 *>(wr + 32 * b);
+                    block_moments(w4, dx0 + (float)(8 * (b & 1)), dy00 + (float)(4 * (b >> 1)), m);
+                }
+            }
+            reduce8(m);
+            if (cc == 0 && j < ns) add_moments(accC, sid[sub + j], m);
             __syncthreads();
         }
     }
