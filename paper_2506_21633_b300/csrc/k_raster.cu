@@ -126,12 +126,24 @@ __device__ __forceinline__ int2 tile_rows(float uy, float ry, int y0) {
 // bounding-box half-width), so over a band of rows it peaks at dy_R clamped
 // into the band; the left end mirrors this at -dy_R.  A block is kept when
 // the band's extent overlaps its eight columns.  NaN records get no block.
+__device__ __forceinline__ float sqrt_approx(float x) {
+    float y;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ float rcp_approx(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 __device__ __forceinline__ uint32_t block_mask(float u, float v, float qa, float qb, float qc, float cutm, int2 rows) {
     const float kx = -0.5f * __fdividef(qb, qa);
     const float ky = -0.5f * __fdividef(qb, qc);
     const float qs = fmaf(0.5f * qb, kx, qc);
     const float qt = fmaf(0.5f * qb, ky, qa);
-    const float dyR = ky * sqrtf(fmaxf(0.f, __fdividef(cutm, qt)));
+    const float dyR = ky * sqrt_approx(fmaxf(0.f, __fdividef(cutm, qt)));
     const float iqa = __fdividef(1.f, qa);
     uint32_t m = 0;
 #pragma unroll
@@ -139,8 +151,8 @@ __device__ __forceinline__ uint32_t block_mask(float u, float v, float qa, float
         if (rows.x > 4 * rb + 3 || rows.y < 4 * rb) continue;
         const float ya = (float)(4 * rb) - v, yb = ya + 3.f;
         const float tR = fminf(fmaxf(dyR, ya), yb), tL = fminf(fmaxf(-dyR, ya), yb);
-        const float hR = sqrtf(fmaxf(0.f, (cutm - qs * tR * tR) * iqa));
-        const float hL = sqrtf(fmaxf(0.f, (cutm - qs * tL * tL) * iqa));
+        const float hR = sqrt_approx(fmaxf(0.f, (cutm - qs * tR * tR) * iqa));
+        const float hL = sqrt_approx(fmaxf(0.f, (cutm - qs * tL * tL) * iqa));
         const float xmax = fmaf(kx, tR, hR), xmin = fmaf(kx, tL, -hL);
         const float xa = -u, xb = 8.f - u;
         if (xmax >= xa && xmin <= xa + 7.f) m |= 1u << (2 * rb);
@@ -192,6 +204,23 @@ __device__ __forceinline__ uint32_t warp_hits(const uint32_t *sM, int k0, int n)
 
 __device__ __forceinline__ float cut_margin(float cut) { return cut * 1.01f; }
 
+// Phase-2 order of the staged Gaussians [k0, k0 + n) (n <= 32): ascending
+// block count, so that the four Gaussians that one warp sums side by side
+// have about the same number of blocks.  Called by a whole warp; writes
+// perm[0..31] (slots past n hold Gaussians with no block).
+__device__ __forceinline__ void order_by_blocks(const uint32_t *sM, int k0, int n, uint8_t *perm) {
+    const int lane = threadIdx.x & 31;
+    const int pc = lane < n ? __popc(sM[k0 + (lane < n ? lane : 0)]) : 0;
+    const uint32_t lt = (1u << lane) - 1u;
+    int rank = 0;
+#pragma unroll
+    for (int p = 0; p <= 8; ++p) {
+        const uint32_t b = __ballot_sync(0xffffffffu, pc == p);
+        rank += p < pc ? __popc(b) : (p == pc ? __popc(b & lt) : 0);
+    }
+    perm[rank] = (uint8_t)lane;
+}
+
 // Stage one computation-plane record: exponent coefficients, block set and
 // the Gaussian's (view, Gaussian) slot.
 __device__ __forceinline__ void stage_comp(const CompRec *__restrict__ comp, uint32_t vg, const TileCtx &c, float cutm,
@@ -209,9 +238,10 @@ __device__ __forceinline__ void stage_comp(const CompRec *__restrict__ comp, uin
 // a7: intensity pass.  Per ray (cell centre): T = 1; for each Gaussian in
 // depth order: alpha = o exp(-delta/2) within the cutoff; the Gaussian
 // receives alpha T; T *= 1 - alpha.  The ray stops once T < Tfloor.  For the
-// adjoint each ray records where it stopped: last = index + 1 of the Gaussian
-// at which T fell below the floor and Tstop = the transmittance in front of
-// it; or last = 0 and Tstop = the transmittance behind the whole list.
+// adjoint each ray records the index just past its last in-cutoff Gaussian
+// and the transmittance in front of that Gaussian.  The pair update is
+// branch-free: a pair outside the cutoff (or on a stopped ray) gets weight 0,
+// which leaves T unchanged.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256)
 k_intensity_fwd(const uint2 *__restrict__ ranges, const uint32_t *__restrict__ vals, const CompRec *__restrict__ comp,
@@ -222,17 +252,17 @@ k_intensity_fwd(const uint2 *__restrict__ ranges, const uint32_t *__restrict__ v
     __shared__ float4 sQ[BATCH];  // (l2, c0, o, -)
     __shared__ uint32_t sM[BATCH];
     __shared__ uint32_t sid[BATCH];
+    __shared__ uint8_t sperm[BATCH];
     __shared__ __align__(16) float W[SUB * WSTRIDE];
-    const int t = threadIdx.x;
+    const int t = threadIdx.x, warp = t >> 5;
     const TileCtx c = tile_ctx(views, V, blockIdx.x);
     const LaneXY L = lane_xy();
     const uint2 r = ranges[blockIdx.x];
     const float cutm = cut_margin(cut);
-    float T = 1.f, Tst = 0.f;
+    float T = c.inside ? 1.f : 0.f, Tprev = 1.f;  // a ray outside the image takes no pair
     int32_t lastj = 0;
-    bool done = !c.inside;
     for (uint32_t base = r.x; base < r.y; base += BATCH) {
-        if (__syncthreads_count(done) == (int)blockDim.x) break;
+        if (__syncthreads_count(T < Tfloor) == (int)blockDim.x) break;
         if (base + t < r.y) {
             const uint32_t vg = vals[base + t];
             float4 P;
@@ -246,31 +276,27 @@ k_intensity_fwd(const uint2 *__restrict__ ranges, const uint32_t *__restrict__ v
         }
         __syncthreads();
         const int nb = min(BATCH, (int)(r.y - base));
+        if (warp * SUB < nb) order_by_blocks(sM, warp * SUB, min(SUB, nb - warp * SUB), sperm + warp * SUB);
         for (int sub = 0; sub < nb; sub += SUB) {
             const int ns = min(SUB, nb - sub);
             uint32_t hm = warp_hits(sM, sub, ns);
+            const int32_t kb = (int32_t)(base + sub + 1);
             while (hm) {
                 const int jj = __ffs(hm) - 1;
                 hm &= hm - 1;
                 const float4 P = sP[sub + jj];
                 const float4 Q = sQ[sub + jj];
                 const float q = poly_q(P, Q.x, Q.y, L);
-                float contrib = 0.f;
-                if (q >= cut && !done) {
-                    const float alpha = __fmul_rn(Q.z, ex2_approx(q));
-                    contrib = __fmul_rn(alpha, T);
-                    const float Tn = __fmaf_rn(-alpha, T, T);  // T (1 - alpha), one rounding
-                    if (Tn < Tfloor) {
-                        done = true;
-                        Tst = T;
-                        lastj = (int32_t)(base + sub + jj + 1);
-                    }
-                    T = Tn;
-                }
-                W[jj * WSTRIDE + c.toff] = contrib;
+                const bool in = (q >= cut) & (T >= Tfloor);
+                const float e = in ? ex2_approx(q) : 0.f;
+                const float alpha = __fmul_rn(Q.z, e);
+                W[jj * WSTRIDE + c.toff] = __fmul_rn(alpha, T);
+                Tprev = in ? T : Tprev;
+                lastj = in ? kb + jj : lastj;
+                T = __fmul_rn(T, __fsub_rn(1.f, alpha));
             }
             __syncthreads();
-            const int j = t >> 3, cc = t & 7;
+            const int j = sperm[sub + (t >> 3)], cc = t & 7;
             uint32_t mb = j < ns ? sM[sub + j] : 0u;
             const float *wr = W + j * WSTRIDE + 4 * cc;
             float s = 0.f;
@@ -290,7 +316,7 @@ k_intensity_fwd(const uint2 *__restrict__ ranges, const uint32_t *__restrict__ v
         }
     }
     if (c.inside) {
-        Tstop[c.pix] = lastj ? Tst : T;
+        Tstop[c.pix] = Tprev;
         last[c.pix] = lastj;
     }
 }
@@ -392,8 +418,9 @@ k_splat_bwd(const uint2 *__restrict__ rangesI, const uint32_t *__restrict__ vals
     __shared__ float2 sU[BATCH];  // tile-local centre
     __shared__ uint32_t sM[BATCH];
     __shared__ uint32_t sid[BATCH];
+    __shared__ uint8_t sperm[BATCH];
     __shared__ __align__(16) float sg[TILE_PIX];  // dL/dS of the tile's pixels, in table layout
-    const int t = threadIdx.x;
+    const int t = threadIdx.x, warp = t >> 5;
     const TileCtx c = tile_ctx(views, V, blockIdx.x);
     const uint2 r = rangesI[blockIdx.x];
     const float g = c.inside ? dLdS[c.pix] : 0.f;
@@ -417,8 +444,10 @@ k_splat_bwd(const uint2 *__restrict__ rangesI, const uint32_t *__restrict__ vals
         }
         __syncthreads();
         const int nb = min(BATCH, (int)(r.y - base));
+        if (warp * 32 < nb) order_by_blocks(sM, warp * 32, min(32, nb - warp * 32), sperm + warp * 32);
+        __syncthreads();
         for (int j0 = 0; j0 < nb; j0 += 32) {
-            const int k = j0 + (t >> 3);
+            const int k = j0 + sperm[j0 + (t >> 3)];
             const int ks = k < nb ? k : j0;
             uint32_t mb = k < nb ? sM[k] : 0u;
             const float4 G = sG[ks];
@@ -469,14 +498,13 @@ cudaError_t launch_splat_bwd(const uint2 *rangesI, const uint32_t *vals, const I
 // a11: adjoint of the intensity pass.  With chat_i = dL/dI_i P_i the ray's
 // share of L is sum_i chat_i alpha_i T_i, so dL/dalpha_i = T_i (chat_i - B_i),
 // B_i = sum_{j>i} chat_j alpha_j prod_{i<k<j}(1 - alpha_k).  Each ray walks
-// its hit list back to front: B by the suffix recursion
-// B <- B + alpha (chat - B), T by undoing the forward products
-// (T_i = T_{i+1} / (1 - alpha_i), with the same float bits of alpha and the
-// same skipped pairs as the forward).  A ray that stopped starts at its
-// stopping Gaussian with the recorded T in front of it; any other starts at
-// the list end with the transmittance behind the list.  Every divisor is
-// > 0: each T the forward kept is >= Tfloor.  Per (view, Gaussian) the
-// moments of w = dL/dalpha exp(-delta_C/2).
+// its hit list back to front from the last in-cutoff Gaussian the forward
+// pass recorded: B by the suffix recursion B <- B + alpha (chat - B), T by
+// undoing the forward products (T_i = T_{i+1} / (1 - alpha_i), with the same
+// float bits of alpha and the same skipped pairs as the forward; every
+// factor is > 0 because T_{i+1} >= Tfloor).  The pair update is branch-free
+// (weight 0 outside the cutoff leaves B and T unchanged).  Per
+// (view, Gaussian) the moments of w = dL/dalpha exp(-delta_C/2).
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256)
 k_intensity_bwd(const uint2 *__restrict__ ranges, const uint32_t *__restrict__ vals, const CompRec *__restrict__ comp,
@@ -489,20 +517,19 @@ k_intensity_bwd(const uint2 *__restrict__ ranges, const uint32_t *__restrict__ v
     __shared__ float2 sU[BATCH];  // tile-local centre
     __shared__ uint32_t sM[BATCH];
     __shared__ uint32_t sid[BATCH];
+    __shared__ uint8_t sperm[BATCH];
     __shared__ __align__(16) float W[SUB * WSTRIDE];
     __shared__ int smax;
-    const int t = threadIdx.x;
+    const int t = threadIdx.x, warp = t >> 5;
     const TileCtx c = tile_ctx(views, V, blockIdx.x);
     const LaneXY L = lane_xy();
     const uint2 r = ranges[blockIdx.x];
-    const int32_t rec = c.inside ? last[c.pix] : 0;
-    // exclusive end of this ray's list; rays outside the image take none
-    const int32_t mylast = !c.inside ? (int32_t)r.x : (rec > 0 ? rec : (int32_t)r.y);
+    const int32_t mylast = c.inside ? last[c.pix] : 0;
     float T = c.inside ? Tstop[c.pix] : 0.f;
-    bool first = rec > 0;
-    if (t == 0) smax = (int)r.x;
+    bool first = true;
+    if (t == 0) smax = 0;
     __syncthreads();
-    if (mylast > (int32_t)r.x) atomicMax(&smax, mylast);
+    if (mylast > 0) atomicMax(&smax, mylast);
     __syncthreads();
     const int hi0 = smax;
     const float cutm = cut_margin(cut);
@@ -525,9 +552,14 @@ k_intensity_bwd(const uint2 *__restrict__ ranges, const uint32_t *__restrict__ v
             sid[t] = vg;
         }
         __syncthreads();
+        // slices of 32 from the top of the batch: slice s = [nb - 32 (s + 1), nb - 32 s)
+        if (warp * SUB < nb) {
+            const int send = nb - warp * SUB, sub = max(0, send - SUB);
+            order_by_blocks(sM, sub, send - sub, sperm + warp * SUB);
+        }
         const int lim = mylast - lo;  // this ray takes staged Gaussians k < lim
-        for (int send = nb; send > 0; send -= SUB) {
-            const int sub = max(0, send - SUB);
+        for (int sl = 0; sl * SUB < nb; ++sl) {
+            const int send = nb - sl * SUB, sub = max(0, send - SUB);
             const int ns = send - sub;
             uint32_t hm = warp_hits(sM, sub, ns);
             while (hm) {
@@ -537,22 +569,20 @@ k_intensity_bwd(const uint2 *__restrict__ ranges, const uint32_t *__restrict__ v
                 const float4 P = sP[k];
                 const float4 Q = sQ[k];
                 const float q = poly_q(P, Q.x, Q.y, L);
-                float w = 0.f;
-                if (q >= cut && k < lim) {
-                    const float e = ex2_approx(q);
-                    const float alpha = __fmul_rn(Q.z, e);
-                    // relative error of a few ulp per step; the factor 1 - alpha
-                    // is the forward's (same alpha bits, exact subtraction)
-                    if (!first) T = __fdividef(T, __fsub_rn(1.f, alpha));
-                    first = false;
-                    const float d = Q.w - B;
-                    B = fmaf(alpha, d, B);
-                    w = T * d * e;
-                }
-                W[jj * WSTRIDE + c.toff] = w;
+                const bool in = (q >= cut) & (k < lim);
+                const float e = in ? ex2_approx(q) : 0.f;
+                const float alpha = __fmul_rn(Q.z, e);
+                // relative error of a few ulp per step; the factor 1 - alpha is
+                // the forward's (same alpha bits, same rounding)
+                const float Td = T * rcp_approx(__fsub_rn(1.f, alpha));
+                T = (in & !first) ? Td : T;
+                first = first & !in;
+                const float d = Q.w - B;
+                B = fmaf(alpha, d, B);
+                W[jj * WSTRIDE + c.toff] = T * d * e;
             }
             __syncthreads();
-            const int j = t >> 3, cc = t & 7;
+            const int j = sperm[sl * SUB + (t >> 3)], cc = t & 7;
             uint32_t mb = j < ns ? sM[sub + j] : 0u;
             const float2 uv = sU[sub + (j < ns ? j : 0)];
             const float dx0 = (float)cc - uv.x, dy00 = -uv.y;
