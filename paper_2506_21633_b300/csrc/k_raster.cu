@@ -261,10 +261,11 @@ k_intensity_fwd(const uint2 *__restrict__ ranges, const uint32_t *__restrict__ v
     const float cutm = cut_margin(cut);
     float T = c.inside ? 1.f : 0.f, Tprev = 1.f;  // a ray outside the image takes no pair
     int32_t lastj = 0;
+    uint32_t vnext = r.x + t < r.y ? vals[r.x + t] : 0u;  // next batch's list entry, loaded one batch ahead
     for (uint32_t base = r.x; base < r.y; base += BATCH) {
         if (__syncthreads_count(T < Tfloor) == (int)blockDim.x) break;
         if (base + t < r.y) {
-            const uint32_t vg = vals[base + t];
+            const uint32_t vg = vnext;
             float4 P;
             float2 Q, uv, oP;
             uint32_t m;
@@ -274,6 +275,7 @@ k_intensity_fwd(const uint2 *__restrict__ ranges, const uint32_t *__restrict__ v
             sM[t] = m;
             sid[t] = vg;
         }
+        if (base + BATCH + t < r.y) vnext = vals[base + BATCH + t];
         __syncthreads();
         const int nb = min(BATCH, (int)(r.y - base));
         if (warp * SUB < nb) order_by_blocks(sM, warp * SUB, min(SUB, nb - warp * SUB), sperm + warp * SUB);
@@ -360,10 +362,11 @@ k_splat_fwd(const uint2 *__restrict__ rangesI, const uint32_t *__restrict__ vals
     const uint2 r = ok ? rangesI[blockIdx.x] : make_uint2(0u, 0u);
     const float cutm = cut_margin(cut);
     float acc = 0.f;
+    uint32_t vnext = r.x + t < r.y ? vals[r.x + t] : 0u;
     for (uint32_t base = r.x; base < r.y; base += BATCH) {
         __syncthreads();
         if (base + t < r.y) {
-            const uint32_t vg = vals[base + t];
+            const uint32_t vg = vnext;
             float4 G, P;
             float2 uv, Q;
             float cn;
@@ -374,6 +377,7 @@ k_splat_fwd(const uint2 *__restrict__ rangesI, const uint32_t *__restrict__ vals
             sQ[t] = make_float4(Q.x, Q.y, cn * comp[vg].P * A[vg], 0.f);
             sM[t] = m;
         }
+        if (base + BATCH + t < r.y) vnext = vals[base + BATCH + t];
         __syncthreads();
         const int nb = min(BATCH, (int)(r.y - base));
         for (int k0 = 0; k0 < nb; k0 += 32) {
@@ -381,10 +385,15 @@ k_splat_fwd(const uint2 *__restrict__ rangesI, const uint32_t *__restrict__ vals
             while (hm) {
                 const int k = k0 + __ffs(hm) - 1;
                 hm &= hm - 1;
-                const float4 P = sP[k];
-                const float4 Q = sQ[k];
-                const float q = poly_q(P, Q.x, Q.y, L);
-                if (q >= cut) acc = fmaf(Q.z, ex2_approx(q), acc);
+                const bool two = hm != 0u;
+                const int k1 = two ? k0 + __ffs(hm) - 1 : k;
+                hm &= hm - 1;
+                const float4 P0 = sP[k], Q0 = sQ[k];
+                const float4 P1 = sP[k1], Q1 = sQ[k1];
+                const float q0 = poly_q(P0, Q0.x, Q0.y, L);
+                const float q1 = poly_q(P1, Q1.x, Q1.y, L);
+                if (q0 >= cut) acc = fmaf(Q0.z, ex2_approx(q0), acc);
+                if (two & (q1 >= cut)) acc = fmaf(Q1.z, ex2_approx(q1), acc);
             }
         }
     }
@@ -428,10 +437,11 @@ k_splat_bwd(const uint2 *__restrict__ rangesI, const uint32_t *__restrict__ vals
     if (__syncthreads_count(g != 0.f) == 0) return;
     const float cutm = cut_margin(cut);
     const int cc = t & 7;
+    uint32_t vnext = r.x + t < r.y ? vals[r.x + t] : 0u;
     for (uint32_t base = r.x; base < r.y; base += BATCH) {
         __syncthreads();
         if (base + t < r.y) {
-            const uint32_t vg = vals[base + t];
+            const uint32_t vg = vnext;
             float4 G;
             float2 uv;
             float cn;
@@ -442,6 +452,7 @@ k_splat_bwd(const uint2 *__restrict__ rangesI, const uint32_t *__restrict__ vals
             sM[t] = m;
             sid[t] = vg;
         }
+        if (base + BATCH + t < r.y) vnext = vals[base + BATCH + t];
         __syncthreads();
         const int nb = min(BATCH, (int)(r.y - base));
         if (warp * 32 < nb) order_by_blocks(sM, warp * 32, min(32, nb - warp * 32), sperm + warp * 32);
@@ -534,12 +545,14 @@ k_intensity_bwd(const uint2 *__restrict__ ranges, const uint32_t *__restrict__ v
     const int hi0 = smax;
     const float cutm = cut_margin(cut);
     float B = 0.f;
+    uint32_t vnext = 0u;  // next batch's list entry, loaded one batch ahead
+    if (hi0 > (int)r.x && t < hi0 - max((int)r.x, hi0 - BATCH)) vnext = vals[max((int)r.x, hi0 - BATCH) + t];
     for (int hi = hi0; hi > (int)r.x; hi -= BATCH) {
         const int lo = max((int)r.x, hi - BATCH);
         const int nb = hi - lo;
         __syncthreads();
         if (t < nb) {
-            const uint32_t vg = vals[lo + t];
+            const uint32_t vg = vnext;
             float4 P;
             float2 Q, uv, oP;
             uint32_t m;
@@ -550,6 +563,10 @@ k_intensity_bwd(const uint2 *__restrict__ ranges, const uint32_t *__restrict__ v
             sU[t] = uv;
             sM[t] = m;
             sid[t] = vg;
+        }
+        {
+            const int nlo = max((int)r.x, lo - BATCH);
+            if (lo > (int)r.x && t < lo - nlo) vnext = vals[nlo + t];
         }
         __syncthreads();
         // slices of 32 from the top of the batch: slice s = [nb - 32 (s + 1), nb - 32 s)
@@ -563,23 +580,40 @@ k_intensity_bwd(const uint2 *__restrict__ ranges, const uint32_t *__restrict__ v
             const int ns = send - sub;
             uint32_t hm = warp_hits(sM, sub, ns);
             while (hm) {
-                const int jj = 31 - __clz(hm);
-                hm ^= 1u << jj;
-                const int k = sub + jj;
-                const float4 P = sP[k];
-                const float4 Q = sQ[k];
-                const float q = poly_q(P, Q.x, Q.y, L);
-                const bool in = (q >= cut) & (k < lim);
-                const float e = in ? ex2_approx(q) : 0.f;
-                const float alpha = __fmul_rn(Q.z, e);
-                // relative error of a few ulp per step; the factor 1 - alpha is
-                // the forward's (same alpha bits, same rounding)
-                const float Td = T * rcp_approx(__fsub_rn(1.f, alpha));
-                T = (in & !first) ? Td : T;
-                first = first & !in;
-                const float d = Q.w - B;
-                B = fmaf(alpha, d, B);
-                W[jj * WSTRIDE + c.toff] = T * d * e;
+                // two hits per iteration, back to front (the second may be absent)
+                const int j0 = 31 - __clz(hm);
+                hm ^= 1u << j0;
+                const bool two = hm != 0u;
+                const int j1 = two ? 31 - __clz(hm) : j0;
+                if (two) hm ^= 1u << j1;
+                const float4 P0 = sP[sub + j0], Q0 = sQ[sub + j0];
+                const float4 P1 = sP[sub + j1], Q1 = sQ[sub + j1];
+                const float q0 = poly_q(P0, Q0.x, Q0.y, L);
+                const float q1 = poly_q(P1, Q1.x, Q1.y, L);
+                {
+                    const bool in = (q0 >= cut) & (sub + j0 < lim);
+                    const float e = in ? ex2_approx(q0) : 0.f;
+                    const float alpha = __fmul_rn(Q0.z, e);
+                    // relative error of a few ulp per step; the factor 1 - alpha is
+                    // the forward's (same alpha bits, same rounding)
+                    const float Td = T * rcp_approx(__fsub_rn(1.f, alpha));
+                    T = (in & !first) ? Td : T;
+                    first = first & !in;
+                    const float d = Q0.w - B;
+                    B = fmaf(alpha, d, B);
+                    W[j0 * WSTRIDE + c.toff] = T * d * e;
+                }
+                {
+                    const bool in = two & (q1 >= cut) & (sub + j1 < lim);
+                    const float e = in ? ex2_approx(q1) : 0.f;
+                    const float alpha = __fmul_rn(Q1.z, e);
+                    const float Td = T * rcp_approx(__fsub_rn(1.f, alpha));
+                    T = (in & !first) ? Td : T;
+                    first = first & !in;
+                    const float d = Q1.w - B;
+                    B = fmaf(alpha, d, B);
+                    if (two) W[j1 * WSTRIDE + c.toff] = T * d * e;
+                }
             }
             __syncthreads();
             const int j = sperm[sl * SUB + (t >> 3)], cc = t & 7;
