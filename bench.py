@@ -62,6 +62,8 @@ def parse():
     ap.add_argument("--workload", choices=["config3", "medium", "small", "config4", "serve"], default="config3",
                     help="medium: the config-3 scene with 8 views (profiling); small: a reduced scene for "
                          "quick checks (neither is a bench line)")
+    ap.add_argument("--schedule", choices=["auto", "tiles", "ordered", "persistent"], default="auto",
+                    help="raster launch policy; auto times each before the timed region and keeps the fastest")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -279,6 +281,22 @@ def run_sdgr(args):
         code, required = r.status()
         assert code == _lib.SDGR_OK, "device status %d" % code
     pairs = r.count_pairs()
+    schedule_ms = None
+    if args.schedule == "auto":  # untimed: two steps per schedule, keep the fastest
+        schedule_ms = {}
+        for name in ("tiles", "ordered", "persistent"):
+            r.set_schedule(name)
+            step()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(2):
+                step()
+            e1.record(stream)
+            e1.synchronize()
+            schedule_ms[name] = round(e0.elapsed_time(e1) / 2, 3)
+        r.set_schedule(min(schedule_ms, key=schedule_ms.get))
+    else:
+        r.set_schedule(args.schedule)
     r.profile(True)
     r.profile_read(reset=True)
 
@@ -402,7 +420,8 @@ def run_sdgr(args):
                    "image": [views[0]["NR"], views[0]["NA"]], "parallelism": "replicas" if world > 1 else "single",
                    "l2": "inputs larger than L2 (workspace %.1f GB per step)" % (r.workspace_bytes() / 1e9),
                    "pairs_per_step": {"computation_plane": pairs[0], "imaging_plane": pairs[1]},
-                   "instances_per_step": int(r.n_inst)},
+                   "instances_per_step": int(r.n_inst), "schedule": r.schedule,
+                   "schedule_ms_per_step": schedule_ms},
         "gaussian_pixel_evals_per_s": round((pairs[0] + pairs[1]) * world * args.steps / (ms_max / 1e3), 1),
         "plain": plain, "e2e": e2e, "roofline": roof, "gpu_launches": int(launches), "clocks": clocks,
     }
@@ -493,6 +512,13 @@ def run_uneven(args):
     p = torch.from_numpy(start.astype(np.float32)).to(dev).contiguous()
     fs = FusedStep(p, views, targets, offs)
     fs.capture()
+    schedule_ms = None
+    if args.schedule == "auto":
+        _, schedule_ms = fs.autotune(steps=2)
+    elif args.schedule != fs.r.schedule:
+        fs.r.set_schedule(args.schedule)
+        fs.graph = None
+        fs.capture()
     for _ in range(max(args.warmup, 1)):
         fs.step()
     fs.check()
@@ -500,7 +526,6 @@ def run_uneven(args):
     stream = torch.cuda.current_stream(dev)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize(dev)
-    l0 = _lib.sdgr_launch_count()
     ev0.record(stream)
     for _ in range(args.steps):
         fs.step()
@@ -529,9 +554,11 @@ def run_uneven(args):
                                    % (len(scenes), min(s.shape[0] for s in scenes), max(s.shape[0] for s in scenes),
                                       offs[-1], sizes, V),
                        "pairs_per_step": {"computation_plane": pairs[0], "imaging_plane": pairs[1]},
-                       "instances_per_step": int(fs.r.n_inst)},
+                       "instances_per_step": int(fs.r.n_inst), "schedule": fs.r.schedule,
+                       "schedule_ms_per_step": {k: round(v, 3) for k, v in schedule_ms.items()} if schedule_ms else None},
             "plain": {"value": round(V / t_plain, 3), "unit": UNIT, "s_per_step": round(t_plain, 3)},
-            "gpu_launches_per_step": int((_lib.sdgr_launch_count() - l0) / max(args.steps, 1))}
+            "gpu_launches": int(fs.graph_launches) * args.steps,
+            "gpu_launches_how": "kernel launches captured in the step's graph x steps"}
 
 
 def run_serving(args):

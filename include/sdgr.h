@@ -197,6 +197,24 @@ sdgr_status sdgr_render_bwd(sdgr_ws *ws, const float *dL_dimages, float *grads, 
  *   misaligned pointers). */
 sdgr_status sdgr_set_sh(sdgr_ws *ws, const float *sh, float *dsh, int32_t degree);
 
+/* Raster schedule (no counterpart in the paper: a launch policy of this
+ * library; results do not depend on it beyond float32 atomic order).
+ * Every sdgr_bin_sort also builds, per plane, a work list of the tiles whose
+ * instance list is non-empty, longest list first (bucketed by the bit length
+ * of the list size).  mode:
+ *   0: one CTA per tile of the plane, in tile order (every tile launched);
+ *   SDGR_SCHED_ORDERED: one CTA per work-list item (empty tiles cost no
+ *     work; the images are zeroed before the splat);
+ *   SDGR_SCHED_ORDERED | SDGR_SCHED_PERSISTENT: SMs x (CTAs per SM) resident
+ *     CTAs pull work-list items from a device counter until the list is
+ *     exhausted (no waits between CTAs).
+ * Read by the following sdgr_render_fwd / sdgr_render_bwd calls.  Default:
+ * SDGR_SCHED_ORDERED | SDGR_SCHED_PERSISTENT.  Errors: SDGR_ERR_INVALID (NULL ws, unknown bits,
+ * PERSISTENT without ORDERED). */
+#define SDGR_SCHED_ORDERED 1
+#define SDGR_SCHED_PERSISTENT 2
+sdgr_status sdgr_set_schedule(sdgr_ws *ws, int32_t mode);
+
 /* Densification and pruning (the "Densification and Pruning Operation" of
  * Section II-B and the thresholds of Section III-D).  Gradient statistics:
  * while bound, every sdgr_render_bwd adds, for each Gaussian and each view

@@ -23,8 +23,12 @@ EXPORTS = (
     "sdgr_read_status", "sdgr_status_string", "sdgr_profile_enable", "sdgr_profile_read",
     "sdgr_count_pairs", "sdgr_launch_count", "sdgr_render_fwd_noalloc", "sdgr_adam_step_device",
     "sdgr_copy_status_async", "sdgr_set_sh", "sdgr_set_densify_stats", "sdgr_densify_scratch_bytes",
-    "sdgr_densify",
+    "sdgr_densify", "sdgr_set_schedule",
 )
+
+SCHED_ORDERED = 1
+SCHED_PERSISTENT = 2
+SCHEDULES = {"tiles": 0, "ordered": SCHED_ORDERED, "persistent": SCHED_ORDERED | SCHED_PERSISTENT}
 
 STAGES = ("preprocess", "depth_sort", "bin", "intensity_fwd", "splat_fwd", "splat_bwd", "intensity_bwd",
           "param_bwd")
@@ -97,6 +101,7 @@ def lib():
         L.sdgr_copy_status_async.argtypes = [vp, vp, vp]
         L.sdgr_set_sh.argtypes = [vp, vp, vp, i32]
         L.sdgr_set_densify_stats.argtypes = [vp, vp, vp]
+        L.sdgr_set_schedule.argtypes = [vp, i32]
         L.sdgr_densify_scratch_bytes.argtypes = [i64]
         L.sdgr_densify.argtypes = [vp, vp, vp, vp, vp, vp, vp, i64, P(SdgrDensifyCfg), vp, vp, vp, vp, i64, vp,
                                    P(ctypes.c_int64), vp]
@@ -223,6 +228,10 @@ def sdgr_l1_loss(images, targets, npix, dLdS, loss, stream):
 def sdgr_set_densify_stats(ws, accum_ptr, count_ptr):
     _check("sdgr_set_densify_stats", lib().sdgr_set_densify_stats(ws, ctypes.c_void_p(accum_ptr or None),
                                                                   ctypes.c_void_p(count_ptr or None)))
+
+
+def sdgr_set_schedule(ws, mode):
+    _check("sdgr_set_schedule", lib().sdgr_set_schedule(ws, int(mode)))
 
 
 def sdgr_densify_scratch_bytes(N):

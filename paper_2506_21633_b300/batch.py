@@ -88,10 +88,50 @@ class FusedStep:
             t.copy_(s0)
         torch.cuda.synchronize(self.p.device)
         g = torch.cuda.CUDAGraph()
+        l0 = L.sdgr_launch_count()
         with torch.cuda.graph(g):
             self.enqueue()
+        self.graph_launches = L.sdgr_launch_count() - l0  # kernel launches captured = launches per replay
         self.graph = g
         return self
+
+    def autotune(self, schedules=("tiles", "ordered", "persistent"), steps=3):
+        """Time `steps` steps under each raster schedule (re-capturing the
+        graph if one is captured) and keep the fastest.  The optimiser state is
+        restored afterwards, so tuning does not advance the optimisation.
+        Returns (best, {schedule: ms per step})."""
+        state = (self.p, self.m, self.v, self.step_dev)
+        saved = [t.clone() for t in state]
+        captured = self.graph is not None
+        stream = torch.cuda.current_stream(self.p.device)
+        times = {}
+        for name in schedules:
+            self.r.set_schedule(name)
+            if captured:
+                self.graph = None
+                self.capture()
+            self.step()  # warm-up
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(steps):
+                self.step()
+            e1.record(stream)
+            e1.synchronize()
+            if not self.check():
+                raise RuntimeError("instance capacity exceeded while tuning")
+            times[name] = e0.elapsed_time(e1) / steps
+            for t, s0 in zip(state, saved):
+                t.copy_(s0)
+        best = min(times, key=times.get)
+        self.r.set_schedule(best)
+        if captured:
+            self.graph = None
+            self.capture()
+        for t, s0 in zip(state, saved):
+            t.copy_(s0)
+        torch.cuda.synchronize(self.p.device)
+        self.schedule_ms = times
+        return best, times
 
     def step(self):
         if self.graph is not None:

@@ -28,7 +28,7 @@ struct Layout {
     size_t dk0, dv0, dk1, dv1;
     size_t scnt, soff, scan64;
     size_t ik0, iv0, ik1, iv1;
-    size_t hist, scan32, ranges, segs;
+    size_t hist, scan32, ranges, segs, order, work;
     size_t A, Tstop, last, accI, accC;
     size_t total;
 };
@@ -82,6 +82,8 @@ Layout make_layout(const sdgr_caps *c) {
     L.scan32 = take(scan_scratch_elems(hn) * 4);
     L.ranges = take(2 * NT * sizeof(uint2));
     L.segs = take((2 * V + 2) * sizeof(SegDev));
+    L.order = take(2 * NT * 4);
+    L.work = take(sizeof(TileWorkDev));
     L.A = take(VG * 4);
     L.Tstop = take(NP * 4);
     L.last = take(NP * 4);
@@ -133,6 +135,7 @@ struct sdgr_ws {
     float *dsh = nullptr;
     int sh_degree = 0;
     float *dens_accum = nullptr, *dens_count = nullptr;  // sdgr_set_densify_stats
+    int sched = SDGR_SCHED_ORDERED | SDGR_SCHED_PERSISTENT;  // sdgr_set_schedule
     std::vector<ViewDev> hviews;
     std::vector<SceneDev> hscenes;
     std::vector<int32_t> hscene_views;
@@ -416,12 +419,32 @@ sdgr_status sdgr_bin_sort(sdgr_ws *ws, void *stream) {
     uint2 *ranges = ws->at<uint2>(L.ranges);
     CK(cudaMemsetAsync(ranges, 0, (size_t)2 * ws->tiles * sizeof(uint2), s));
     CK(launch_ranges(ws->inst_keys, st, ws->caps.max_instances, ranges, ws->sms, s));
+    CK(launch_tile_order(ranges, ws->tiles, ws->at<TileWorkDev>(L.work), ws->at<int32_t>(L.order), ws->sms, s));
     prof_end(ws, pk1, s);
     ws->stage = 2;
     return SDGR_OK;
 }
 
 static float exp2_cut(float K) { return -0.5f * LOG2E * K * K; }
+
+// Schedule of raster kernel `kernel` (0 intensity, 1 splat, 2 splat adjoint,
+// 3 intensity adjoint) under the workspace's schedule mode; a persistent
+// launch gets its item counter zeroed first.
+static cudaError_t raster_sched(sdgr_ws *ws, int kernel, cudaStream_t s, TileSched &sc) {
+    const int plane = (kernel == 1 || kernel == 2) ? 1 : 0;
+    sc.order = nullptr;
+    sc.work = ws->at<TileWorkDev>(ws->L.work);
+    sc.plane = plane;
+    sc.slot = kernel;
+    sc.persistent_grid = 0;
+    if (!(ws->sched & SDGR_SCHED_ORDERED)) return cudaSuccess;
+    sc.order = ws->at<int32_t>(ws->L.order) + (size_t)plane * ws->tiles;
+    if (ws->sched & SDGR_SCHED_PERSISTENT) {
+        sc.persistent_grid = ws->sms * raster_blocks_per_sm(kernel);
+        return cudaMemsetAsync(&sc.work->next[kernel], 0, sizeof(int32_t), s);
+    }
+    return cudaSuccess;
+}
 
 static float t_floor(float T_min) {
     const float f = 7.888609052210118e-31f;  // 2^-100
@@ -440,13 +463,18 @@ sdgr_status sdgr_render_fwd(sdgr_ws *ws, float *images, float *intensity, void *
     const float cut = exp2_cut(ws->cfg.cutoff_K);
     float *A = ws->at<float>(L.A);
     if (ws->VG > 0) CK(cudaMemsetAsync(A, 0, (size_t)ws->VG * 4, s));
+    // a work list skips tiles with empty lists: their pixels stay 0
+    if ((ws->sched & SDGR_SCHED_ORDERED) && ws->npix > 0) CK(cudaMemsetAsync(images, 0, (size_t)ws->npix * 4, s));
+    TileSched sc;
+    CK(raster_sched(ws, 0, s, sc));
     int pk = prof_begin(ws, SDGR_STAGE_INTENSITY_FWD, s);
     CK(launch_intensity_fwd(ranges, ws->inst_vals, ws->at<CompRec>(L.comp), views, ws->V, ws->tiles, cut,
-                            t_floor(ws->cfg.T_min), st, A, ws->at<float>(L.Tstop), ws->at<int32_t>(L.last), s));
+                            t_floor(ws->cfg.T_min), st, A, ws->at<float>(L.Tstop), ws->at<int32_t>(L.last), sc, s));
     prof_end(ws, pk, s);
+    CK(raster_sched(ws, 1, s, sc));
     pk = prof_begin(ws, SDGR_STAGE_SPLAT_FWD, s);
     CK(launch_splat_fwd(ranges + ws->tiles, ws->inst_vals, ws->at<ImgRec>(L.img), ws->at<CompRec>(L.comp), A, views,
-                        ws->V, ws->tiles, cut, st, images, s));
+                        ws->V, ws->tiles, cut, st, images, sc, s));
     prof_end(ws, pk, s);
     if (intensity) CK(launch_intensity_out(ws->at<CompRec>(L.comp), A, ws->VG, intensity, ws->sms, s));
     ws->stage = 3;
@@ -472,14 +500,17 @@ sdgr_status sdgr_render_bwd(sdgr_ws *ws, const float *dL_dimages, float *grads, 
     if (ws->n_gauss > 0 && !accumulate) CK(cudaMemsetAsync(grads, 0, (size_t)ws->n_gauss * 12 * 4, s));
     float *dsh = ws->sh ? ws->dsh : nullptr;
     if (dsh && ws->n_gauss > 0 && !accumulate) CK(cudaMemsetAsync(dsh, 0, (size_t)ws->n_gauss * 16 * 4, s));
+    TileSched sc;
+    CK(raster_sched(ws, 2, s, sc));
     int pk = prof_begin(ws, SDGR_STAGE_SPLAT_BWD, s);
     CK(launch_splat_bwd(ranges + ws->tiles, ws->inst_vals, ws->at<ImgRec>(L.img), dL_dimages, views, ws->V, ws->tiles,
-                        cut, st, accI, s));
+                        cut, st, accI, sc, s));
     prof_end(ws, pk, s);
+    CK(raster_sched(ws, 3, s, sc));
     pk = prof_begin(ws, SDGR_STAGE_INTENSITY_BWD, s);
     CK(launch_intensity_bwd(ranges, ws->inst_vals, ws->at<CompRec>(L.comp), ws->at<ImgRec>(L.img), accI,
                             ws->at<float>(L.Tstop), ws->at<int32_t>(L.last), views, ws->V, ws->tiles, cut, st, accC,
-                            s));
+                            sc, s));
     prof_end(ws, pk, s);
     pk = prof_begin(ws, SDGR_STAGE_PARAM_BWD, s);
     CK(launch_param_bwd(reinterpret_cast<const float4 *>(ws->params), views, ws->at<SceneDev>(L.scenes),
@@ -488,6 +519,14 @@ sdgr_status sdgr_render_bwd(sdgr_ws *ws, const float *dL_dimages, float *grads, 
                         reinterpret_cast<float4 *>(grads),
                         reinterpret_cast<float4 *>(dsh), ws->dens_accum, ws->dens_count, ws->sms, s));
     prof_end(ws, pk, s);
+    return SDGR_OK;
+}
+
+sdgr_status sdgr_set_schedule(sdgr_ws *ws, int32_t mode) {
+    if (!ws || (mode & ~(SDGR_SCHED_ORDERED | SDGR_SCHED_PERSISTENT)) ||
+        ((mode & SDGR_SCHED_PERSISTENT) && !(mode & SDGR_SCHED_ORDERED)))
+        return SDGR_ERR_INVALID;
+    ws->sched = mode;
     return SDGR_OK;
 }
 

@@ -221,6 +221,29 @@ __device__ __forceinline__ void order_by_blocks(const uint32_t *sM, int k0, int 
     perm[rank] = (uint8_t)lane;
 }
 
+// Runs body(tile) for the tiles this CTA owns under the launch's schedule.
+template <typename F>
+__device__ __forceinline__ void for_tiles(const TileSched &sc, F &&body) {
+    if (!sc.order) {
+        body((int)blockIdx.x);
+        return;
+    }
+    const int n = sc.work->count[sc.plane];
+    if (sc.persistent_grid == 0) {
+        if ((int)blockIdx.x < n) body(sc.order[blockIdx.x]);
+        return;
+    }
+    __shared__ int s_item;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(&sc.work->next[sc.slot], 1);
+        __syncthreads();
+        const int item = s_item;
+        __syncthreads();  // every thread has read s_item before it is overwritten
+        if (item >= n) break;
+        body(sc.order[item]);
+    }
+}
+
 // Stage one computation-plane record: exponent coefficients, block set and
 // the Gaussian's (view, Gaussian) slot.
 __device__ __forceinline__ void stage_comp(const CompRec *__restrict__ comp, uint32_t vg, const TileCtx &c, float cutm,
@@ -243,11 +266,10 @@ __device__ __forceinline__ void stage_comp(const CompRec *__restrict__ comp, uin
 // branch-free: a pair outside the cutoff (or on a stopped ray) gets weight 0,
 // which leaves T unchanged.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256)
-k_intensity_fwd(const uint2 *__restrict__ ranges, const uint32_t *__restrict__ vals, const CompRec *__restrict__ comp,
-                const ViewDev *__restrict__ views, int V, float cut, float Tfloor, const StatusDev *st,
-                float *__restrict__ A, float *__restrict__ Tstop, int32_t *__restrict__ last) {
-    if (st->code != SDGR_OK) return;
+__device__ __forceinline__ void
+intensity_fwd_tile(const int tile, const uint2 *__restrict__ ranges, const uint32_t *__restrict__ vals,
+                   const CompRec *__restrict__ comp, const ViewDev *__restrict__ views, int V, float cut, float Tfloor,
+                   float *__restrict__ A, float *__restrict__ Tstop, int32_t *__restrict__ last) {
     __shared__ float4 sP[BATCH];  // (qa, qb, qc, l1)
     __shared__ float4 sQ[BATCH];  // (l2, c0, o, -)
     __shared__ uint32_t sM[BATCH];
@@ -255,9 +277,9 @@ k_intensity_fwd(const uint2 *__restrict__ ranges, const uint32_t *__restrict__ v
     __shared__ uint8_t sperm[BATCH];
     __shared__ __align__(16) float W[SUB * WSTRIDE];
     const int t = threadIdx.x, warp = t >> 5;
-    const TileCtx c = tile_ctx(views, V, blockIdx.x);
+    const TileCtx c = tile_ctx(views, V, tile);
     const LaneXY L = lane_xy();
-    const uint2 r = ranges[blockIdx.x];
+    const uint2 r = ranges[tile];
     const float cutm = cut_margin(cut);
     float T = c.inside ? 1.f : 0.f, Tprev = 1.f;  // a ray outside the image takes no pair
     int32_t lastj = 0;
@@ -323,11 +345,25 @@ k_intensity_fwd(const uint2 *__restrict__ ranges, const uint32_t *__restrict__ v
     }
 }
 
+__global__ void __launch_bounds__(256)
+k_intensity_fwd(const uint2 *__restrict__ ranges, const uint32_t *__restrict__ vals, const CompRec *__restrict__ comp,
+                const ViewDev *__restrict__ views, int V, float cut, float Tfloor, const StatusDev *st,
+                float *__restrict__ A, float *__restrict__ Tstop, int32_t *__restrict__ last, const TileSched sc) {
+    if (st->code != SDGR_OK) return;
+    for_tiles(sc, [&](int tile) { intensity_fwd_tile(tile, ranges, vals, comp, views, V, cut, Tfloor, A, Tstop, last); });
+}
+
+// Grid of a raster launch: one CTA per tile (or work item), or the persistent grid.
+static unsigned raster_grid(int tiles, const TileSched &sc) {
+    return sc.order && sc.persistent_grid > 0 ? (unsigned)sc.persistent_grid : (unsigned)tiles;
+}
+
 cudaError_t launch_intensity_fwd(const uint2 *ranges, const uint32_t *vals, const CompRec *comp, const ViewDev *views,
                                  int V, int tiles, float cut, float Tfloor, const StatusDev *st, float *A,
-                                 float *Tstop, int32_t *last, cudaStream_t s) {
+                                 float *Tstop, int32_t *last, const TileSched &sched, cudaStream_t s) {
     if (tiles <= 0) return cudaSuccess;
-    k_intensity_fwd<<<tiles, TILE_PIX, 0, s>>>(ranges, vals, comp, views, V, cut, Tfloor, st, A, Tstop, last);
+    k_intensity_fwd<<<raster_grid(tiles, sched), TILE_PIX, 0, s>>>(ranges, vals, comp, views, V, cut, Tfloor, st, A,
+                                                                   Tstop, last, sched);
     note_launch();
     return cudaGetLastError();
 }
@@ -348,18 +384,17 @@ __device__ __forceinline__ void stage_img(const ImgRec *__restrict__ img, uint32
 // a8: imaging splat.  S[pixel] = sum_i c_i exp(-delta_I/2) I_i, I_i = P_i A_i.
 // Each pixel gathers over its warp's hit list; no reduction is needed.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256)
-k_splat_fwd(const uint2 *__restrict__ rangesI, const uint32_t *__restrict__ vals, const ImgRec *__restrict__ img,
-            const CompRec *__restrict__ comp, const float *__restrict__ A, const ViewDev *__restrict__ views, int V,
-            float cut, const StatusDev *st, float *__restrict__ images) {
+__device__ __forceinline__ void
+splat_fwd_tile(const int tile, const uint2 *__restrict__ rangesI, const uint32_t *__restrict__ vals,
+               const ImgRec *__restrict__ img, const CompRec *__restrict__ comp, const float *__restrict__ A,
+               const ViewDev *__restrict__ views, int V, float cut, bool ok, float *__restrict__ images) {
     __shared__ float4 sP[BATCH];  // (qa, qb, qc, l1)
     __shared__ float4 sQ[BATCH];  // (l2, c0, c I, -)
     __shared__ uint32_t sM[BATCH];
     const int t = threadIdx.x;
-    const TileCtx c = tile_ctx(views, V, blockIdx.x);
+    const TileCtx c = tile_ctx(views, V, tile);
     const LaneXY L = lane_xy();
-    const bool ok = st->code == SDGR_OK;
-    const uint2 r = ok ? rangesI[blockIdx.x] : make_uint2(0u, 0u);
+    const uint2 r = ok ? rangesI[tile] : make_uint2(0u, 0u);
     const float cutm = cut_margin(cut);
     float acc = 0.f;
     uint32_t vnext = r.x + t < r.y ? vals[r.x + t] : 0u;
@@ -400,11 +435,23 @@ k_splat_fwd(const uint2 *__restrict__ rangesI, const uint32_t *__restrict__ vals
     if (c.inside) images[c.pix] = acc;
 }
 
+// Every pixel is written: with a work list (non-empty tiles only) the caller
+// zeroes the images first.
+__global__ void __launch_bounds__(256)
+k_splat_fwd(const uint2 *__restrict__ rangesI, const uint32_t *__restrict__ vals, const ImgRec *__restrict__ img,
+            const CompRec *__restrict__ comp, const float *__restrict__ A, const ViewDev *__restrict__ views, int V,
+            float cut, const StatusDev *st, float *__restrict__ images, const TileSched sc) {
+    const bool ok = st->code == SDGR_OK;
+    if (!ok && sc.order) return;
+    for_tiles(sc, [&](int tile) { splat_fwd_tile(tile, rangesI, vals, img, comp, A, views, V, cut, ok, images); });
+}
+
 cudaError_t launch_splat_fwd(const uint2 *rangesI, const uint32_t *vals, const ImgRec *img, const CompRec *comp,
                              const float *A, const ViewDev *views, int V, int tiles, float cut, const StatusDev *st,
-                             float *images, cudaStream_t s) {
+                             float *images, const TileSched &sched, cudaStream_t s) {
     if (tiles <= 0) return cudaSuccess;
-    k_splat_fwd<<<tiles, TILE_PIX, 0, s>>>(rangesI, vals, img, comp, A, views, V, cut, st, images);
+    k_splat_fwd<<<raster_grid(tiles, sched), TILE_PIX, 0, s>>>(rangesI, vals, img, comp, A, views, V, cut, st, images,
+                                                               sched);
     note_launch();
     return cudaGetLastError();
 }
@@ -418,11 +465,10 @@ cudaError_t launch_splat_fwd(const uint2 *rangesI, const uint32_t *vals, const I
 // with dL/dS read from shared memory as one float4; three shuffles combine
 // the eight partial moments.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256)
-k_splat_bwd(const uint2 *__restrict__ rangesI, const uint32_t *__restrict__ vals, const ImgRec *__restrict__ img,
-            const float *__restrict__ dLdS, const ViewDev *__restrict__ views, int V, float cut, const StatusDev *st,
-            float4 *__restrict__ accI) {
-    if (st->code != SDGR_OK) return;
+__device__ __forceinline__ void
+splat_bwd_tile(const int tile, const uint2 *__restrict__ rangesI, const uint32_t *__restrict__ vals,
+               const ImgRec *__restrict__ img, const float *__restrict__ dLdS, const ViewDev *__restrict__ views, int V,
+               float cut, float4 *__restrict__ accI) {
     __shared__ float4 sG[BATCH];  // (qa, qb, qc, -)
     __shared__ float2 sU[BATCH];  // tile-local centre
     __shared__ uint32_t sM[BATCH];
@@ -430,8 +476,8 @@ k_splat_bwd(const uint2 *__restrict__ rangesI, const uint32_t *__restrict__ vals
     __shared__ uint8_t sperm[BATCH];
     __shared__ __align__(16) float sg[TILE_PIX];  // dL/dS of the tile's pixels, in table layout
     const int t = threadIdx.x, warp = t >> 5;
-    const TileCtx c = tile_ctx(views, V, blockIdx.x);
-    const uint2 r = rangesI[blockIdx.x];
+    const TileCtx c = tile_ctx(views, V, tile);
+    const uint2 r = rangesI[tile];
     const float g = c.inside ? dLdS[c.pix] : 0.f;
     sg[c.toff] = g;
     if (__syncthreads_count(g != 0.f) == 0) return;
@@ -496,11 +542,20 @@ k_splat_bwd(const uint2 *__restrict__ rangesI, const uint32_t *__restrict__ vals
     }
 }
 
+__global__ void __launch_bounds__(256)
+k_splat_bwd(const uint2 *__restrict__ rangesI, const uint32_t *__restrict__ vals, const ImgRec *__restrict__ img,
+            const float *__restrict__ dLdS, const ViewDev *__restrict__ views, int V, float cut, const StatusDev *st,
+            float4 *__restrict__ accI, const TileSched sc) {
+    if (st->code != SDGR_OK) return;
+    for_tiles(sc, [&](int tile) { splat_bwd_tile(tile, rangesI, vals, img, dLdS, views, V, cut, accI); });
+}
+
 cudaError_t launch_splat_bwd(const uint2 *rangesI, const uint32_t *vals, const ImgRec *img, const float *dLdS,
                              const ViewDev *views, int V, int tiles, float cut, const StatusDev *st, float4 *accI,
-                             cudaStream_t s) {
+                             const TileSched &sched, cudaStream_t s) {
     if (tiles <= 0) return cudaSuccess;
-    k_splat_bwd<<<tiles, TILE_PIX, 0, s>>>(rangesI, vals, img, dLdS, views, V, cut, st, accI);
+    k_splat_bwd<<<raster_grid(tiles, sched), TILE_PIX, 0, s>>>(rangesI, vals, img, dLdS, views, V, cut, st, accI,
+                                                               sched);
     note_launch();
     return cudaGetLastError();
 }
@@ -517,12 +572,11 @@ cudaError_t launch_splat_bwd(const uint2 *rangesI, const uint32_t *vals, const I
 // (weight 0 outside the cutoff leaves B and T unchanged).  Per
 // (view, Gaussian) the moments of w = dL/dalpha exp(-delta_C/2).
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256)
-k_intensity_bwd(const uint2 *__restrict__ ranges, const uint32_t *__restrict__ vals, const CompRec *__restrict__ comp,
-                const ImgRec *__restrict__ img, const float4 *__restrict__ accI, const float *__restrict__ Tstop,
-                const int32_t *__restrict__ last, const ViewDev *__restrict__ views, int V, float cut,
-                const StatusDev *st, float4 *__restrict__ accC) {
-    if (st->code != SDGR_OK) return;
+__device__ __forceinline__ void
+intensity_bwd_tile(const int tile, const uint2 *__restrict__ ranges, const uint32_t *__restrict__ vals,
+                   const CompRec *__restrict__ comp, const ImgRec *__restrict__ img, const float4 *__restrict__ accI,
+                   const float *__restrict__ Tstop, const int32_t *__restrict__ last,
+                   const ViewDev *__restrict__ views, int V, float cut, float4 *__restrict__ accC) {
     __shared__ float4 sP[BATCH];  // (qa, qb, qc, l1)
     __shared__ float4 sQ[BATCH];  // (l2, c0, o, chat)
     __shared__ float2 sU[BATCH];  // tile-local centre
@@ -532,9 +586,9 @@ k_intensity_bwd(const uint2 *__restrict__ ranges, const uint32_t *__restrict__ v
     __shared__ __align__(16) float W[SUB * WSTRIDE];
     __shared__ int smax;
     const int t = threadIdx.x, warp = t >> 5;
-    const TileCtx c = tile_ctx(views, V, blockIdx.x);
+    const TileCtx c = tile_ctx(views, V, tile);
     const LaneXY L = lane_xy();
-    const uint2 r = ranges[blockIdx.x];
+    const uint2 r = ranges[tile];
     const int32_t mylast = c.inside ? last[c.pix] : 0;
     float T = c.inside ? Tstop[c.pix] : 0.f;
     bool first = true;
@@ -637,13 +691,46 @@ k_intensity_bwd(const uint2 *__restrict__ ranges, const uint32_t *__restrict__ v
     }
 }
 
+__global__ void __launch_bounds__(256)
+k_intensity_bwd(const uint2 *__restrict__ ranges, const uint32_t *__restrict__ vals, const CompRec *__restrict__ comp,
+                const ImgRec *__restrict__ img, const float4 *__restrict__ accI, const float *__restrict__ Tstop,
+                const int32_t *__restrict__ last, const ViewDev *__restrict__ views, int V, float cut,
+                const StatusDev *st, float4 *__restrict__ accC, const TileSched sc) {
+    if (st->code != SDGR_OK) return;
+    for_tiles(sc, [&](int tile) {
+        intensity_bwd_tile(tile, ranges, vals, comp, img, accI, Tstop, last, views, V, cut, accC);
+    });
+}
+
 cudaError_t launch_intensity_bwd(const uint2 *ranges, const uint32_t *vals, const CompRec *comp, const ImgRec *img,
                                  const float4 *accI, const float *Tstop, const int32_t *last, const ViewDev *views,
-                                 int V, int tiles, float cut, const StatusDev *st, float4 *accC, cudaStream_t s) {
+                                 int V, int tiles, float cut, const StatusDev *st, float4 *accC,
+                                 const TileSched &sched, cudaStream_t s) {
     if (tiles <= 0) return cudaSuccess;
-    k_intensity_bwd<<<tiles, TILE_PIX, 0, s>>>(ranges, vals, comp, img, accI, Tstop, last, views, V, cut, st, accC);
+    k_intensity_bwd<<<raster_grid(tiles, sched), TILE_PIX, 0, s>>>(ranges, vals, comp, img, accI, Tstop, last, views,
+                                                                   V, cut, st, accC, sched);
     note_launch();
     return cudaGetLastError();
+}
+
+int raster_blocks_per_sm(int kernel) {
+    static int cache[4] = {0, 0, 0, 0};
+    if (kernel < 0 || kernel > 3) return 1;
+    if (cache[kernel] > 0) return cache[kernel];
+    int n = 0;
+    cudaError_t e = cudaErrorInvalidValue;
+    switch (kernel) {
+        case 0: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_intensity_fwd, TILE_PIX, 0); break;
+        case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_splat_fwd, TILE_PIX, 0); break;
+        case 2: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_splat_bwd, TILE_PIX, 0); break;
+        default: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_intensity_bwd, TILE_PIX, 0); break;
+    }
+    if (e != cudaSuccess || n < 1) {
+        (void)cudaGetLastError();
+        n = 1;
+    }
+    cache[kernel] = n;
+    return n;
 }
 
 // Diagnostic: in-cutoff (pixel, Gaussian) pairs of every tile of one plane.

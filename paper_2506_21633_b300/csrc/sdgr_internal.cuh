@@ -62,6 +62,29 @@ struct alignas(16) StatusDev {
     unsigned long long pairs[2];  // sdgr_count_pairs: in-cutoff pairs per plane
 };
 
+// Work list of the raster kernels, rebuilt by every bin/sort: per plane the
+// tiles with a non-empty instance list, longest list first (longest-
+// processing-time order, by the bit length of the list size).
+struct alignas(16) TileWorkDev {
+    int32_t count[2];     // non-empty tiles per plane
+    int32_t next[4];      // item counters of the persistent launches (K3, K4, K5, K6)
+    int32_t pad[2];
+    int32_t hist[2][32];  // tiles per bucket (bucket = bit length of the list size - 1)
+    int32_t off[2][32];   // next free slot per bucket
+};
+
+// How a raster launch maps CTAs to tiles.  order == nullptr: CTA i takes tile
+// i of the plane.  Otherwise CTAs take items of the plane's work list: one CTA
+// per item (persistent_grid == 0) or persistent_grid CTAs that pull items
+// from next[slot] until the list is exhausted.
+struct TileSched {
+    const int32_t *order;   // work list of this plane (tile indices, plane-local)
+    TileWorkDev *work;
+    int plane;              // 0 computation, 1 imaging
+    int slot;               // item counter used by this launch
+    int persistent_grid;    // > 0: persistent launch with this many CTAs
+};
+
 // One segment of a segmented radix sort: items [start, start + len), digits
 // taken from (key - key_base); blk_start = first block of the segment.
 struct alignas(16) SegDev {
@@ -167,22 +190,26 @@ cudaError_t launch_check_capacity(const unsigned long long *scnt, const unsigned
 cudaError_t launch_emit(const uint32_t *sorted_vg, const unsigned long long *soff, const uint2 *rectC,
                         const uint2 *rectI, const ViewDev *views, int V, int64_t VG, int total_tiles,
                         const StatusDev *st, uint32_t *keys, uint32_t *vals, int sms, cudaStream_t s);
+cudaError_t launch_tile_order(const uint2 *ranges, int tiles, TileWorkDev *work, int32_t *order, int sms,
+                              cudaStream_t s);
 cudaError_t launch_ranges(const uint32_t *keys, const StatusDev *st, int64_t cap, uint2 *ranges, int sms,
                           cudaStream_t s);
 
 // raster passes
 cudaError_t launch_intensity_fwd(const uint2 *ranges, const uint32_t *vals, const CompRec *comp, const ViewDev *views,
                                  int V, int tiles, float cut, float Tfloor, const StatusDev *st, float *A,
-                                 float *Tstop, int32_t *last, cudaStream_t s);
+                                 float *Tstop, int32_t *last, const TileSched &sched, cudaStream_t s);
 cudaError_t launch_splat_fwd(const uint2 *rangesI, const uint32_t *vals, const ImgRec *img, const CompRec *comp,
                              const float *A, const ViewDev *views, int V, int tiles, float cut, const StatusDev *st,
-                             float *images, cudaStream_t s);
+                             float *images, const TileSched &sched, cudaStream_t s);
 cudaError_t launch_splat_bwd(const uint2 *rangesI, const uint32_t *vals, const ImgRec *img, const float *dLdS,
                              const ViewDev *views, int V, int tiles, float cut, const StatusDev *st, float4 *accI,
-                             cudaStream_t s);
+                             const TileSched &sched, cudaStream_t s);
 cudaError_t launch_intensity_bwd(const uint2 *ranges, const uint32_t *vals, const CompRec *comp, const ImgRec *img,
                                  const float4 *accI, const float *Tstop, const int32_t *last, const ViewDev *views,
-                                 int V, int tiles, float cut, const StatusDev *st, float4 *accC, cudaStream_t s);
+                                 int V, int tiles, float cut, const StatusDev *st, float4 *accC, const TileSched &sched, cudaStream_t s);
+// CTAs per SM of a raster kernel at 256 threads (occupancy query, cached).
+int raster_blocks_per_sm(int kernel);
 cudaError_t launch_count_pairs(const uint2 *ranges, const uint32_t *vals, const CompRec *comp, const ImgRec *img,
                                const ViewDev *views, int V, int tiles, float cut, StatusDev *st, cudaStream_t s);
 cudaError_t launch_intensity_out(const CompRec *comp, const float *A, int64_t VG, float *I, int sms, cudaStream_t s);

@@ -51,6 +51,7 @@ class Renderer:
         self.scene_offsets = None
         self.params = None
         self.n_inst = None
+        self.schedule = "persistent"
 
     def __del__(self):
         try:
@@ -79,6 +80,10 @@ class Renderer:
         pend = getattr(self, "_sh_state", None)
         if pend is not None:  # the SH binding belongs to the workspace: carry it over
             L.sdgr_set_sh(self.ws, *pend)
+        dens = getattr(self, "_dens_state", None)
+        if dens is not None:
+            L.sdgr_set_densify_stats(self.ws, *dens)
+        L.sdgr_set_schedule(self.ws, L.SCHEDULES[self.schedule])
 
     def workspace_bytes(self):
         return 0 if self.buf is None else self.buf.numel()
@@ -144,6 +149,27 @@ class Renderer:
                           degree)
         if self.ws is not None:
             L.sdgr_set_sh(self.ws, *self._sh_state)
+
+    def set_densify_stats(self, accum=None, count=None):
+        """Bind (or with None, unbind) the densification statistics buffers,
+        cuda float32 [N]; every following backward() adds |dL/du_I| and 1 per
+        (view, Gaussian) with image-plane weight."""
+        self._dens = (accum, count)
+        self._dens_state = (accum.data_ptr() if accum is not None else None,
+                            count.data_ptr() if count is not None else None)
+        if self.ws is not None:
+            L.sdgr_set_densify_stats(self.ws, *self._dens_state)
+
+    def set_schedule(self, name):
+        """Raster launch policy: 'tiles' (one CTA per tile), 'ordered' (one
+        CTA per non-empty tile, longest list first) or 'persistent' (resident
+        CTAs pulling the ordered list).  Applies to the following forward /
+        backward calls."""
+        if name not in L.SCHEDULES:
+            raise ValueError(f"unknown schedule {name!r}")
+        self.schedule = name
+        if self.ws is not None:
+            L.sdgr_set_schedule(self.ws, L.SCHEDULES[name])
 
     def count_pairs(self, stream=None):
         """In-cutoff (pixel, Gaussian) pairs (computation plane, imaging plane)

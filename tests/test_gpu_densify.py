@@ -83,7 +83,7 @@ def test_gradient_statistics():
     r.prepare(p, views)
     accum = torch.zeros(600, device="cuda")
     count = torch.zeros(600, device="cuda")
-    L.sdgr_set_densify_stats(r.ws, accum.data_ptr(), count.data_ptr())
+    r.set_densify_stats(accum, count)
     r.forward()
     g = torch.from_numpy(np.concatenate([x.ravel() for x in G]).astype(np.float32)).cuda()
     for _ in range(2):  # two backward calls accumulate
