@@ -38,12 +38,14 @@ UNIT = "views/s"
 
 # Algorithmic work per in-cutoff (pixel, Gaussian) pair: (FP32 ops, MUFU ops).
 # FP32-pipe-equivalent ops = fp32 + 8 * mufu (the SFU has 16 lanes per SM,
-# the FP32 pipe 128).  Derivation in the design notes.
+# the FP32 pipe 128).  The exponent counts 5 ops (a quadratic in the pixel's
+# tile-local coordinates with per-tile coefficients).  Derivation in the
+# design notes.
 ALG_OPS = {
-    "intensity_fwd": (13, 1),
-    "splat_fwd": (9, 1),
-    "splat_bwd": (20, 1),
-    "intensity_bwd": (28, 2),
+    "intensity_fwd": (11, 1),
+    "splat_fwd": (7, 1),
+    "splat_bwd": (18, 1),
+    "intensity_bwd": (26, 2),
 }
 PLANE = {"intensity_fwd": 0, "splat_fwd": 1, "splat_bwd": 1, "intensity_bwd": 0}
 KERNEL_NAME = {"intensity_fwd": "k_intensity_fwd", "splat_fwd": "k_splat_fwd", "splat_bwd": "k_splat_bwd",
