@@ -41,6 +41,7 @@ class OrcCfg(ctypes.Structure):
     _fields_ = [
         ("K", ctypes.c_double), ("eps", ctypes.c_double), ("T_min", ctypes.c_double),
         ("norm_mode", ctypes.c_int32), ("sh_degree", ctypes.c_int32),
+        ("alpha_mode", ctypes.c_int32), ("pad", ctypes.c_int32),
         ("sh", ctypes.POINTER(ctypes.c_double)), ("dsh", ctypes.POINTER(ctypes.c_double)),
         ("duI", ctypes.POINTER(ctypes.c_double)),
     ]
@@ -89,10 +90,12 @@ def set_threads(n: int) -> int:
     return lib().orc_set_threads(int(n))
 
 
-def cfg(K=5.0, eps=0.3, T_min=0.0, norm_mode=0, sh=None, sh_degree=0) -> OrcCfg:
+def cfg(K=5.0, eps=0.3, T_min=0.0, norm_mode=0, sh=None, sh_degree=0, alpha_mode=0) -> OrcCfg:
     """sh: optional [N,16] float64 coefficients of the SH degrees 1..3
-    (view-dependent scattering), used up to sh_degree."""
-    c = OrcCfg(K=float(K), eps=float(eps), T_min=float(T_min), norm_mode=int(norm_mode), sh_degree=int(sh_degree))
+    (view-dependent scattering), used up to sh_degree.  alpha_mode 1: the
+    Beer-Lambert opacity 1 - exp(-tau G), tau = softplus(opacity logit)."""
+    c = OrcCfg(K=float(K), eps=float(eps), T_min=float(T_min), norm_mode=int(norm_mode), sh_degree=int(sh_degree),
+               alpha_mode=int(alpha_mode))
     if sh is not None:
         a = np.ascontiguousarray(sh, dtype=np.float64)
         assert a.ndim == 2 and a.shape[1] == 16

@@ -35,6 +35,11 @@
  *   R5  alpha_i = o_i exp(-delta/2) with o_i = sigmoid(opacity logit) standing
  *       for 1 - exp(-(k_e+ + k_e-) ...) (the two extinctions only enter as a
  *       sum); T_i = prod_{j<i} (1 - alpha_j); I_i = P_i sum_rays alpha_i T_i.
+ *       Variant (alpha_mode 1, Beer-Lambert): the extinction exponent of the
+ *       paper's attenuation factor is an optical depth tau_i times the
+ *       Gaussian's profile along the ray, alpha_i = 1 - exp(-tau_i
+ *       exp(-delta/2)), with tau_i = softplus(opacity logit) =
+ *       -log(1 - sigmoid(logit)): the peak opacity equals o_i of the default.
  *   R6  beta = c_i exp(-delta/2), delta = d^T Sigma'^{-1} d, c_i = 1 / (2 pi
  *       sqrt(det Sigma'_I)) (energy mode) or 1 (peak mode).
  *   R7  contributions with delta > K^2 are zero on both planes (K <= 0: no
@@ -72,6 +77,8 @@ typedef struct {
     double T_min;      /* ray stops once T < T_min (0: never) */
     int32_t norm_mode; /* 0: energy-normalised beta, 1: peak (c_i = 1) */
     int32_t sh_degree; /* 0..3: degree of the view-dependent scattering */
+    int32_t alpha_mode; /* 0: alpha = o G; 1: alpha = 1 - exp(-tau G) (R5) */
+    int32_t pad;
     const double *sh;  /* [N][16] SH coefficients of degrees 1..3 (NULL: none) */
     double *dsh;       /* [N][16] out: dL/dsh (orc_grad only; NULL: not wanted) */
     double *duI;       /* [V][N][2] out: dL/du_I per view (orc_grad only; NULL: not wanted) */
@@ -115,6 +122,7 @@ int orc_sh_basis(const double *d, double *Y) {
 typedef struct {
     /* activations (C1) */
     double s[3], qhat[4], qlen, o, P;
+    double tau;       /* optical depth softplus(logit) (alpha_mode 1) */
     double R[3][3];   /* rotation of the Gaussian */
     double Sig[3][3]; /* 3D covariance Sigma = R diag(s^2) R^T */
     /* radar frame (eqs. W, R_r, x_r) */
@@ -193,6 +201,7 @@ static void project(const double *p, const orc_view *v, const orc_cfg *cfg, orc_
     g->qlen = sqrt(p[8] * p[8] + p[9] * p[9] + p[10] * p[10] + p[11] * p[11]);
     for (k = 0; k < 4; ++k) g->qhat[k] = p[8 + k] / g->qlen;
     g->o = 1.0 / (1.0 + exp(-p[3]));
+    g->tau = p[3] > 0.0 ? p[3] + log1p(exp(-p[3])) : log1p(exp(p[3]));
     g->P = p[7];
     quat_to_rot(g->qhat, g->R);
     memset(g->Ysh, 0, sizeof(g->Ysh));
@@ -363,6 +372,12 @@ static void free_cands(cand_lists *cl) { free(cl->start); free(cl->idx); }
  * of the computation plane the Gaussians are visited front to back; the ray
  * deposits alpha_i T_i on Gaussian i and is attenuated by (1 - alpha_i).
  * A[i] = sum over rays of alpha_i T_i; I_i = P_i A_i. */
+/* Opacity of Gaussian q on a ray where its profile exp(-delta/2) is G
+ * (reading R5 and its Beer-Lambert variant). */
+static double alpha_of(const orc_gauss *q, const orc_cfg *cfg, double G) {
+    return cfg->alpha_mode ? -expm1(-q->tau * G) : q->o * G;
+}
+
 static void intensity_pass(const orc_gauss *g, int N, const int *order, const orc_view *v, const orc_cfg *cfg,
                            int culled, double *A, double *Tfin) {
     int nt = n_threads();
@@ -386,7 +401,7 @@ static void intensity_pass(const orc_gauss *g, int N, const int *order, const or
                 double dx = m - q->u[0][0], dy = n - q->u[0][1];
                 double delta = mahal(q->C2[0], dx, dy);
                 if (delta > K2) continue;
-                double alpha = q->o * exp(-0.5 * delta);
+                double alpha = alpha_of(q, cfg, exp(-0.5 * delta));
                 Ap[i] += alpha * T;
                 T *= (1.0 - alpha);
                 if (cfg->T_min > 0.0 && T < cfg->T_min) break;
@@ -541,7 +556,7 @@ typedef struct {
     double cI;       /* dL/dc_i */
     double uC[2];    /* dL/du on the computation plane */
     double CC[2][2]; /* dL/d(conic) on the computation plane */
-    double o;        /* dL/do */
+    double o;        /* dL/do (alpha_mode 1: dL/dtau) */
 } orc_adj;
 
 /* Adjoint of one view, given its forward state (projections g, depth order,
@@ -614,7 +629,7 @@ static int view_adjoint(int N, const orc_view *v, const orc_cfg *cfg, int culled
                 double dx = m - q->u[0][0], dy = n - q->u[0][1];
                 double delta = mahal(q->C2[0], dx, dy);
                 if (delta > K2) continue;
-                double alpha = q->o * exp(-0.5 * delta);
+                double alpha = alpha_of(q, cfg, exp(-0.5 * delta));
                 hit[cnt] = j; al[cnt] = alpha; Ts[cnt] = T; ++cnt;
                 T *= (1.0 - alpha);
                 if (cfg->T_min > 0.0 && T < cfg->T_min) break;
@@ -627,10 +642,17 @@ static int view_adjoint(int N, const orc_view *v, const orc_cfg *cfg, int culled
                 double galpha = Ts[k] * (chat[j] - B);
                 B = chat[j] * al[k] + (1.0 - al[k]) * B;
                 double d[2] = {m - q->u[0][0], n - q->u[0][1]};
-                double e1 = al[k] / q->o; /* exp(-delta/2) */
+                double e1 = exp(-0.5 * mahal(q->C2[0], d[0], d[1])); /* exp(-delta/2) */
                 double *acc = Pp + (size_t)j * 7;
-                acc[0] += galpha * e1;                                /* dL/do */
-                double gE = galpha * q->o;                            /* dL/de */
+                double gE;                                            /* dL/de */
+                if (cfg->alpha_mode) {
+                    /* alpha = 1 - exp(-tau e): d alpha/d tau = e (1 - alpha), d alpha/d e = tau (1 - alpha) */
+                    acc[0] += galpha * e1 * (1.0 - al[k]);            /* dL/dtau */
+                    gE = galpha * q->tau * (1.0 - al[k]);
+                } else {
+                    acc[0] += galpha * e1;                            /* dL/do */
+                    gE = galpha * q->o;
+                }
                 acc[1] += gE * e1 * (q->C2[0][0][0] * d[0] + q->C2[0][0][1] * d[1]);
                 acc[2] += gE * e1 * (q->C2[0][1][0] * d[0] + q->C2[0][1][1] * d[1]);
                 acc[3] += gE * (-0.5 * e1 * d[0] * d[0]);
@@ -716,7 +738,8 @@ static int view_adjoint(int N, const orc_view *v, const orc_cfg *cfg, int culled
         for (a = 0; a < 3; ++a)
             for (k = 0; k < 2; ++k) dxr[a] += q->J[0][k][a] * ad->uC[k] + q->J[1][k][a] * ad->uI[k];
         for (a = 0; a < 3; ++a) gr[a] += q->Rr[0][a] * dxr[0] + q->Rr[1][a] * dxr[1] + q->Rr[2][a] * dxr[2];
-        gr[3] += ad->o * q->o * (1.0 - q->o);
+        /* d o / d logit = o (1 - o); d tau / d logit = sigmoid(logit) = o */
+        gr[3] += ad->o * (cfg->alpha_mode ? q->o : q->o * (1.0 - q->o));
         for (k = 0; k < 3; ++k) gr[4 + k] += ds[k] * q->s[k];
         gr[7] += ad->gI * A[i];
         if (cfg->dsh) {

@@ -14,6 +14,9 @@ Which pin covers which step of the method (Section II of the paper):
       - test_p4: Gaussians stacked on one line of sight, binomial closed form
       - test_p5: telescoping sum_i A_i + sum_rays T_final = #rays (P = 1)
       - test_p9: faint limit o -> 0, every Gaussian at its closed form
+      - test_bl_*: Beer-Lambert opacity 1 - exp(-tau G): isolated and stacked
+        Gaussians against the entire exponential integral Ein (scipy's E1),
+        telescoping, and the adjoint against central differences
   imaging pass (eq. S_{n,m})
       - test_p2: splat integral equals the intensity (energy normalisation)
       - test_p6: layover additivity, permutation invariance
@@ -219,6 +222,68 @@ def test_p4_stacked_shadow(orc, k):
     assert abs(A[1] / A[0] - (1 - o / 2)) < 1e-9
 
 
+def _ein(x):
+    """Entire exponential integral Ein(x) = int_0^x (1 - e^-t) / t dt =
+    gamma + ln x + E1(x) (x > 0)."""
+    from scipy.special import exp1
+    return np.euler_gamma + math.log(x) + float(exp1(x))
+
+
+@pytest.mark.parametrize("o", [0.2, 0.6, 0.95])
+def test_bl_isolated_intensity(orc, o):
+    """Beer-Lambert opacity: the ray sum of 1 - exp(-tau exp(-delta/2)) over
+    the plane is 2 pi sqrt(det Sigma'_C) int_0^inf (1 - exp(-tau e^-s)) ds =
+    2 pi sqrt(det) Ein(tau), with tau = -log(1 - o) (peak opacity o)."""
+    v = sc.make_view(33.0, 45.0, 0.05, 0.06, 128, 256)
+    s, P, eps = 0.2, 0.8, 0.3
+    p = one((0.05, -0.03, 0.02), s=s, o=o, P=P)
+    _, A, _ = orc.render(p, [v], orc.cfg(K=0.0, eps=eps, alpha_mode=1))
+    cy = v["dR"] * math.tan(v["theta"])
+    det = (s * s / v["dA"] ** 2 + eps) * (s * s / cy ** 2 + eps)
+    expect = 2 * math.pi * math.sqrt(det) * _ein(-math.log1p(-o))
+    assert abs(A[0, 0] - expect) <= 1e-9 * expect
+    # the default opacity o exp(-delta/2) gives a different profile with the same peak
+    _, A0, _ = orc.render(p, [v], orc.cfg(K=0.0, eps=eps))
+    assert abs(A0[0, 0] - o * 2 * math.pi * math.sqrt(det)) <= 1e-9 * A0[0, 0]
+    assert A[0, 0] > A0[0, 0]  # 1 - (1 - o)^G > o G for 0 < G < 1
+
+
+@pytest.mark.parametrize("k", [2, 3])
+def test_bl_stacked_shadow(orc, k):
+    """Identical Gaussians on one line of sight, Beer-Lambert opacity: the
+    j-th receives sum_rays (1 - e^{-tau G}) e^{-j tau G} = 2 pi sqrt(det)
+    (Ein((j + 1) tau) - Ein(j tau))."""
+    v = sc.make_view(70.0, 40.0, 0.05, 0.05, 96, 96)
+    s, o, eps = 0.25, 0.6, 0.3
+    tau = -math.log1p(-o)
+    los = los_dir(v["phi"], v["theta"])
+    pts = stack(*[one(0.3 * j * los, s=s, o=o, P=1.0) for j in range(k)])[::-1].copy()
+    _, A, _ = orc.render(pts, [v], orc.cfg(K=0.0, eps=eps, alpha_mode=1))
+    A = A[0][::-1]
+    cy = v["dR"] * math.tan(v["theta"])
+    base = 2 * math.pi * math.sqrt((s * s / v["dA"] ** 2 + eps) * (s * s / cy ** 2 + eps))
+    for j in range(k):
+        expect = base * (_ein((j + 1) * tau) - (_ein(j * tau) if j else 0.0))
+        assert abs(A[j] - expect) <= 1e-9 * base, (j, A[j], expect)
+
+
+def test_bl_telescoping(orc):
+    params, views = sc.config1()
+    params = params[:300].copy()
+    params[:, 7] = 1.0
+    views = [dict(views[0], NA=64, NR=48, dA=0.2, dR=0.25)]
+    _, A, Tf = orc.render(params, views, orc.cfg(alpha_mode=1))
+    nrays = views[0]["NA"] * views[0]["NR"]
+    assert abs(A.sum() + Tf[0].sum() - nrays) <= 1e-12 * nrays
+
+
+def test_bl_gradients_fd(orc):
+    params = sc.vehicle_box_scene(6, seed=23, extent=(1.0, 0.8, 0.6), log_s_mean=math.log(0.15), center=(0, 0, 0))
+    views = [sc.make_view(25.0, 40.0, 0.06, 0.07, 24, 20), sc.make_view(160.0, 55.0, 0.07, 0.06, 20, 24)]
+    # step 1e-5: at 1e-6 the differences of this scene carry ~1.5e-6 of roundoff in both opacity modes
+    _fd_check(orc, params, views, orc.cfg(K=0.0, alpha_mode=1), h_rel=1e-5)
+
+
 def test_p5_telescoping(orc):
     params, views = sc.config1()
     params = params[:300].copy()
@@ -389,12 +454,12 @@ def test_depth_order_ties(orc):
     assert list(orc.depth_order(q, v)) == [1, 0, 2, 3]
 
 
-def _fd_check(orc, params, views, cfg, rel=1e-6):
+def _fd_check(orc, params, views, cfg, rel=1e-6, h_rel=1e-6):
     rng = np.random.default_rng(1)
     G = [rng.normal(size=(v["NR"], v["NA"])) for v in views]
     g_an, _ = orc.grad(params, views, G, cfg)
     idx = [(i, j) for i in range(params.shape[0]) for j in range(12)]
-    fd, bad = orc.linear_loss_grad_fd(params, views, G, cfg, idx=idx)
+    fd, bad = orc.linear_loss_grad_fd(params, views, G, cfg, idx=idx, h_rel=h_rel)
     groups = {"mean": [0, 1, 2], "opacity": [3], "scale": [4, 5, 6], "P": [7], "quat": [8, 9, 10, 11]}
     an = np.array([g_an[i, j] for (i, j) in idx])
     comp = np.array([j for (_, j) in idx])
