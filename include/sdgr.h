@@ -79,12 +79,18 @@ typedef struct {
  *               the remaining contributions are below float32 resolution)
  * norm_mode     0: beta = exp(-delta/2) / (2 pi sqrt(det Sigma'_I)), so a
  *               Gaussian deposits its intensity in the image (default);
- *               1: beta = exp(-delta/2) (peak-normalised) */
+ *               1: beta = exp(-delta/2) (peak-normalised)
+ * alpha_mode    opacity of Gaussian i on a ray where its profile
+ *               exp(-delta/2) is G (attenuation factor of eq. I_i):
+ *               0: alpha = o G, o = sigmoid(opacity logit) (default);
+ *               1: alpha = 1 - exp(-tau G), tau = softplus(opacity logit)
+ *               (Beer-Lambert; the peak opacity is again sigmoid(logit)) */
 typedef struct {
     float cutoff_K;
     float dilation_eps;
     float T_min;
     int32_t norm_mode;
+    int32_t alpha_mode;
 } sdgr_cfg;
 
 /* Workspace capacities.  A workspace created for these capacities accepts

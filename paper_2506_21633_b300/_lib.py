@@ -47,7 +47,7 @@ class SdgrView(ctypes.Structure):
 class SdgrCfg(ctypes.Structure):
     _fields_ = [
         ("cutoff_K", ctypes.c_float), ("dilation_eps", ctypes.c_float),
-        ("T_min", ctypes.c_float), ("norm_mode", ctypes.c_int32),
+        ("T_min", ctypes.c_float), ("norm_mode", ctypes.c_int32), ("alpha_mode", ctypes.c_int32),
     ]
 
 
@@ -146,8 +146,9 @@ def make_offsets(scene_offsets):
     return arr
 
 
-def make_cfg(cutoff_K=5.0, dilation_eps=0.3, T_min=0.0, norm_mode=0):
-    return SdgrCfg(cutoff_K=cutoff_K, dilation_eps=dilation_eps, T_min=T_min, norm_mode=norm_mode)
+def make_cfg(cutoff_K=5.0, dilation_eps=0.3, T_min=0.0, norm_mode=0, alpha_mode=0):
+    return SdgrCfg(cutoff_K=cutoff_K, dilation_eps=dilation_eps, T_min=T_min, norm_mode=norm_mode,
+                   alpha_mode=alpha_mode)
 
 
 # -- thin wrappers with the C names ------------------------------------------

@@ -96,7 +96,7 @@ Layout make_layout(const sdgr_caps *c) {
 bool cfg_ok(const sdgr_cfg *cfg) {
     return cfg && cfg->cutoff_K > 0.f && isfinite(cfg->cutoff_K) && cfg->dilation_eps >= 0.f &&
            isfinite(cfg->dilation_eps) && cfg->T_min >= 0.f && cfg->T_min < 1.f &&
-           (cfg->norm_mode == 0 || cfg->norm_mode == 1);
+           (cfg->norm_mode == 0 || cfg->norm_mode == 1) && (cfg->alpha_mode == 0 || cfg->alpha_mode == 1);
 }
 
 bool view_ok(const sdgr_view &v) {
@@ -377,7 +377,7 @@ sdgr_status sdgr_preprocess(sdgr_ws *ws, const float *params, const int64_t *sce
     CK(launch_preprocess(reinterpret_cast<const float4 *>(params),
                          sh_count > 0 ? reinterpret_cast<const float4 *>(ws->sh) : nullptr, sh_count,
                          ws->at<ViewDev>(L.views), V, vg, c.cutoff_K,
-                         c.dilation_eps, c.norm_mode, ws->at<CompRec>(L.comp), ws->at<ImgRec>(L.img),
+                         c.dilation_eps, c.norm_mode, c.alpha_mode, ws->at<CompRec>(L.comp), ws->at<ImgRec>(L.img),
                          ws->at<uint2>(L.rectC), ws->at<uint2>(L.rectI), ws->at<uint32_t>(L.cntC),
                          ws->at<uint32_t>(L.cntI), ws->at<uint32_t>(L.dk0), ws->at<uint32_t>(L.dv0), ws->sms, s));
     prof_end(ws, pk, s);
@@ -469,7 +469,8 @@ sdgr_status sdgr_render_fwd(sdgr_ws *ws, float *images, float *intensity, void *
     CK(raster_sched(ws, 0, s, sc));
     int pk = prof_begin(ws, SDGR_STAGE_INTENSITY_FWD, s);
     CK(launch_intensity_fwd(ranges, ws->inst_vals, ws->at<CompRec>(L.comp), views, ws->V, ws->tiles, cut,
-                            t_floor(ws->cfg.T_min), st, A, ws->at<float>(L.Tstop), ws->at<int32_t>(L.last), sc, s));
+                            t_floor(ws->cfg.T_min), ws->cfg.alpha_mode, st, A, ws->at<float>(L.Tstop),
+                            ws->at<int32_t>(L.last), sc, s));
     prof_end(ws, pk, s);
     CK(raster_sched(ws, 1, s, sc));
     pk = prof_begin(ws, SDGR_STAGE_SPLAT_FWD, s);
@@ -509,13 +510,14 @@ sdgr_status sdgr_render_bwd(sdgr_ws *ws, const float *dL_dimages, float *grads, 
     CK(raster_sched(ws, 3, s, sc));
     pk = prof_begin(ws, SDGR_STAGE_INTENSITY_BWD, s);
     CK(launch_intensity_bwd(ranges, ws->inst_vals, ws->at<CompRec>(L.comp), ws->at<ImgRec>(L.img), accI,
-                            ws->at<float>(L.Tstop), ws->at<int32_t>(L.last), views, ws->V, ws->tiles, cut, st, accC,
-                            sc, s));
+                            ws->at<float>(L.Tstop), ws->at<int32_t>(L.last), views, ws->V, ws->tiles, cut,
+                            ws->cfg.alpha_mode, st, accC, sc, s));
     prof_end(ws, pk, s);
     pk = prof_begin(ws, SDGR_STAGE_PARAM_BWD, s);
     CK(launch_param_bwd(reinterpret_cast<const float4 *>(ws->params), views, ws->at<SceneDev>(L.scenes),
                         ws->at<int32_t>(L.scene_views), ws->n_scenes, ws->n_gauss, ws->cfg.dilation_eps,
-                        ws->cfg.norm_mode, ws->at<float>(L.A), ws->at<CompRec>(L.comp), accI, accC, st,
+                        ws->cfg.norm_mode, ws->cfg.alpha_mode, ws->at<float>(L.A), ws->at<CompRec>(L.comp), accI,
+                        accC, st,
                         reinterpret_cast<float4 *>(grads),
                         reinterpret_cast<float4 *>(dsh), ws->dens_accum, ws->dens_count, ws->sms, s));
     prof_end(ws, pk, s);

@@ -31,7 +31,7 @@ __device__ __forceinline__ void neg_cgc(float a, float b, float c, float p, floa
 __global__ void __launch_bounds__(256)
 k_param_bwd(const float4 *__restrict__ params, const ViewDev *__restrict__ views, const SceneDev *__restrict__ scenes,
             const int32_t *__restrict__ scene_views, int n_scenes, int64_t n_gauss, float eps, int norm_mode,
-            const float *__restrict__ A, const CompRec *__restrict__ comp, const float4 *__restrict__ accI,
+            int alpha_mode, const float *__restrict__ A, const CompRec *__restrict__ comp, const float4 *__restrict__ accI,
             const float4 *__restrict__ accC, const StatusDev *st, float4 *__restrict__ grads,
             float4 *__restrict__ dsh, float *__restrict__ dens_accum, float *__restrict__ dens_count) {
     if (st->code != SDGR_OK) return;
@@ -43,7 +43,12 @@ k_param_bwd(const float4 *__restrict__ params, const ViewDev *__restrict__ views
         const float sx = expf(p1.x), sy = expf(p1.y), sz = expf(p1.z);
         const float qn = 1.0f / sqrtf(p2.x * p2.x + p2.y * p2.y + p2.z * p2.z + p2.w * p2.w);
         const float w = p2.x * qn, x = p2.y * qn, y = p2.z * qn, z = p2.w * qn;
-        const float o = 1.0f / (1.0f + expf(-p0.w));
+        const float osig = 1.0f / (1.0f + expf(-p0.w));
+        // factor of the computation-plane geometry: d alpha / d G is o (default)
+        // or tau (1 - alpha) with the (1 - alpha) already inside the moments
+        const float o = alpha_mode ? softplus(p0.w) : osig;
+        // d o / d logit = o (1 - o); d tau / d logit = sigmoid(logit)
+        const float dlogit = alpha_mode ? osig : osig * (1.f - osig);
         float R[3][3];
         R[0][0] = 1.f - 2.f * (y * y + z * z); R[0][1] = 2.f * (x * y - w * z); R[0][2] = 2.f * (x * z + w * y);
         R[1][0] = 2.f * (x * y + w * z); R[1][1] = 1.f - 2.f * (x * x + z * z); R[1][2] = 2.f * (y * z - w * x);
@@ -152,7 +157,7 @@ k_param_bwd(const float4 *__restrict__ params, const ViewDev *__restrict__ views
         const float4 dq = quat_grad(w, x, y, z, qn, dR);
         // accumulate (the caller zeroed grads unless it asked to accumulate)
         float4 a0 = grads[3 * g], a1 = grads[3 * g + 1], a2 = grads[3 * g + 2];
-        a0.x += dmu[0]; a0.y += dmu[1]; a0.z += dmu[2]; a0.w += go * o * (1.f - o);
+        a0.x += dmu[0]; a0.y += dmu[1]; a0.z += dmu[2]; a0.w += go * dlogit;
         a1.x += ds[0] * sx; a1.y += ds[1] * sy; a1.z += ds[2] * sz; a1.w += gP;
         a2.x += dq.x; a2.y += dq.y; a2.z += dq.z; a2.w += dq.w;
         grads[3 * g] = a0;
@@ -178,14 +183,14 @@ k_param_bwd(const float4 *__restrict__ params, const ViewDev *__restrict__ views
 
 cudaError_t launch_param_bwd(const float4 *params, const ViewDev *views, const SceneDev *scenes,
                              const int32_t *scene_views, int n_scenes, int64_t n_gauss, float eps, int norm_mode,
-                             const float *A, const CompRec *comp, const float4 *accI, const float4 *accC,
+                             int alpha_mode, const float *A, const CompRec *comp, const float4 *accI, const float4 *accC,
                              const StatusDev *st, float4 *grads, float4 *dsh, float *dens_accum,
                              float *dens_count, int sms, cudaStream_t s) {
     if (n_gauss <= 0) return cudaSuccess;
     int64_t blocks = (n_gauss + 255) / 256;
     if (blocks > (int64_t)sms * 8) blocks = (int64_t)sms * 8;
     k_param_bwd<<<(unsigned)blocks, 256, 0, s>>>(params, views, scenes, scene_views, n_scenes, n_gauss, eps, norm_mode,
-                                                  A, comp, accI, accC, st, grads, dsh, dens_accum, dens_count);
+                                                  alpha_mode, A, comp, accI, accC, st, grads, dsh, dens_accum, dens_count);
     note_launch();
     return cudaGetLastError();
 }

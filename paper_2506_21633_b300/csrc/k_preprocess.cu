@@ -72,7 +72,8 @@ __device__ __forceinline__ uint32_t tile_rect(float ux, float uy, float sxx, flo
 __global__ void __launch_bounds__(256)
 k_preprocess(const float4 *__restrict__ params, const float4 *__restrict__ sh, int sh_count,
              const ViewDev *__restrict__ views, int V, int64_t VG, float K,
-             float eps, int norm_mode, CompRec *__restrict__ comp, ImgRec *__restrict__ img, uint2 *__restrict__ rectC,
+             float eps, int norm_mode, int alpha_mode, CompRec *__restrict__ comp, ImgRec *__restrict__ img,
+             uint2 *__restrict__ rectC,
              uint2 *__restrict__ rectI, uint32_t *__restrict__ cntC, uint32_t *__restrict__ cntI,
              uint32_t *__restrict__ dkey, uint32_t *__restrict__ dval) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -88,7 +89,9 @@ k_preprocess(const float4 *__restrict__ params, const float4 *__restrict__ sh, i
         const float s0 = expf(p1.x), s1 = expf(p1.y), s2 = expf(p1.z);
         const float qn = 1.0f / sqrtf(p2.x * p2.x + p2.y * p2.y + p2.z * p2.z + p2.w * p2.w);
         const float w = p2.x * qn, x = p2.y * qn, y = p2.z * qn, z = p2.w * qn;
-        const float o = 1.0f / (1.0f + expf(-p0.w));
+        // the record's opacity field: o = sigmoid(logit), or the optical depth
+        // tau = softplus(logit) of the Beer-Lambert opacity
+        const float o = alpha_mode ? softplus(p0.w) : 1.0f / (1.0f + expf(-p0.w));
         float R[3][3];
         R[0][0] = 1.f - 2.f * (y * y + z * z); R[0][1] = 2.f * (x * y - w * z); R[0][2] = 2.f * (x * z + w * y);
         R[1][0] = 2.f * (x * y + w * z); R[1][1] = 1.f - 2.f * (x * x + z * z); R[1][2] = 2.f * (y * z - w * x);
@@ -182,13 +185,15 @@ k_preprocess(const float4 *__restrict__ params, const float4 *__restrict__ sh, i
 }
 
 cudaError_t launch_preprocess(const float4 *params, const float4 *sh, int sh_count, const ViewDev *views, int V,
-                              int64_t VG, float K, float eps, int norm_mode, CompRec *comp, ImgRec *img, uint2 *rectC, uint2 *rectI, uint32_t *cntC,
+                              int64_t VG, float K, float eps, int norm_mode, int alpha_mode, CompRec *comp, ImgRec *img,
+                              uint2 *rectC, uint2 *rectI, uint32_t *cntC,
                               uint32_t *cntI, uint32_t *dkey, uint32_t *dval, int sms, cudaStream_t s) {
     if (VG <= 0) return cudaSuccess;
     int64_t blocks = (VG + 255) / 256;
     int64_t cap = (int64_t)sms * 8;
     if (blocks > cap) blocks = cap;
-    k_preprocess<<<(unsigned)blocks, 256, 0, s>>>(params, sh, sh_count, views, V, VG, K, eps, norm_mode, comp, img,
+    k_preprocess<<<(unsigned)blocks, 256, 0, s>>>(params, sh, sh_count, views, V, VG, K, eps, norm_mode, alpha_mode,
+                                                   comp, img,
                                                    rectC, rectI,
                                                    cntC, cntI, dkey, dval);
     note_launch();

@@ -221,6 +221,26 @@ __device__ __forceinline__ void order_by_blocks(const uint32_t *sM, int k0, int 
     perm[rank] = (uint8_t)lane;
 }
 
+// Opacity of a pair from the record's opacity field o (o itself, or the
+// optical depth tau of the Beer-Lambert mode AM = 1) and the profile
+// e = exp(-delta/2) (0 for a pair that is skipped).  Explicit round-to-nearest
+// operations: the intensity pass and its adjoint must get the same bits.
+template <int AM>
+__device__ __forceinline__ float alpha_of(float o, float e) {
+    if (AM == 0) return __fmul_rn(o, e);
+    const float y = __fmul_rn(o, e);  // tau G
+    // 1 - exp(-y): below 1/8 a series (no cancellation; truncation below
+    // y^7 / 5040), above it through ex2
+    float p = __fmaf_rn(y, -1.f / 720.f, 1.f / 120.f);
+    p = __fmaf_rn(y, p, -1.f / 24.f);
+    p = __fmaf_rn(y, p, 1.f / 6.f);
+    p = __fmaf_rn(y, p, -0.5f);
+    p = __fmaf_rn(y, p, 1.f);
+    const float series = __fmul_rn(y, p);
+    const float direct = __fsub_rn(1.f, ex2_approx(__fmul_rn(-LOG2E, y)));
+    return y < 0.125f ? series : direct;
+}
+
 // Runs body(tile) for the tiles this CTA owns under the launch's schedule.
 template <typename F>
 __device__ __forceinline__ void for_tiles(const TileSched &sc, F &&body) {
@@ -266,6 +286,7 @@ __device__ __forceinline__ void stage_comp(const CompRec *__restrict__ comp, uin
 // branch-free: a pair outside the cutoff (or on a stopped ray) gets weight 0,
 // which leaves T unchanged.
 // ---------------------------------------------------------------------------
+template <int AM>
 __device__ __forceinline__ void
 intensity_fwd_tile(const int tile, const uint2 *__restrict__ ranges, const uint32_t *__restrict__ vals,
                    const CompRec *__restrict__ comp, const ViewDev *__restrict__ views, int V, float cut, float Tfloor,
@@ -312,8 +333,7 @@ intensity_fwd_tile(const int tile, const uint2 *__restrict__ ranges, const uint3
                 const float4 Q = sQ[sub + jj];
                 const float q = poly_q(P, Q.x, Q.y, L);
                 const bool in = (q >= cut) & (T >= Tfloor);
-                const float e = in ? ex2_approx(q) : 0.f;
-                const float alpha = __fmul_rn(Q.z, e);
+                const float alpha = alpha_of<AM>(Q.z, in ? ex2_approx(q) : 0.f);
                 W[jj * WSTRIDE + c.toff] = __fmul_rn(alpha, T);
                 Tprev = in ? T : Tprev;
                 lastj = in ? kb + jj : lastj;
@@ -345,12 +365,15 @@ intensity_fwd_tile(const int tile, const uint2 *__restrict__ ranges, const uint3
     }
 }
 
+template <int AM>
 __global__ void __launch_bounds__(256)
 k_intensity_fwd(const uint2 *__restrict__ ranges, const uint32_t *__restrict__ vals, const CompRec *__restrict__ comp,
                 const ViewDev *__restrict__ views, int V, float cut, float Tfloor, const StatusDev *st,
                 float *__restrict__ A, float *__restrict__ Tstop, int32_t *__restrict__ last, const TileSched sc) {
     if (st->code != SDGR_OK) return;
-    for_tiles(sc, [&](int tile) { intensity_fwd_tile(tile, ranges, vals, comp, views, V, cut, Tfloor, A, Tstop, last); });
+    for_tiles(sc, [&](int tile) {
+        intensity_fwd_tile<AM>(tile, ranges, vals, comp, views, V, cut, Tfloor, A, Tstop, last);
+    });
 }
 
 // Grid of a raster launch: one CTA per tile (or work item), or the persistent grid.
@@ -359,11 +382,15 @@ static unsigned raster_grid(int tiles, const TileSched &sc) {
 }
 
 cudaError_t launch_intensity_fwd(const uint2 *ranges, const uint32_t *vals, const CompRec *comp, const ViewDev *views,
-                                 int V, int tiles, float cut, float Tfloor, const StatusDev *st, float *A,
-                                 float *Tstop, int32_t *last, const TileSched &sched, cudaStream_t s) {
+                                 int V, int tiles, float cut, float Tfloor, int alpha_mode, const StatusDev *st,
+                                 float *A, float *Tstop, int32_t *last, const TileSched &sched, cudaStream_t s) {
     if (tiles <= 0) return cudaSuccess;
-    k_intensity_fwd<<<raster_grid(tiles, sched), TILE_PIX, 0, s>>>(ranges, vals, comp, views, V, cut, Tfloor, st, A,
-                                                                   Tstop, last, sched);
+    if (alpha_mode)
+        k_intensity_fwd<1><<<raster_grid(tiles, sched), TILE_PIX, 0, s>>>(ranges, vals, comp, views, V, cut, Tfloor,
+                                                                          st, A, Tstop, last, sched);
+    else
+        k_intensity_fwd<0><<<raster_grid(tiles, sched), TILE_PIX, 0, s>>>(ranges, vals, comp, views, V, cut, Tfloor,
+                                                                          st, A, Tstop, last, sched);
     note_launch();
     return cudaGetLastError();
 }
@@ -572,6 +599,7 @@ cudaError_t launch_splat_bwd(const uint2 *rangesI, const uint32_t *vals, const I
 // (weight 0 outside the cutoff leaves B and T unchanged).  Per
 // (view, Gaussian) the moments of w = dL/dalpha exp(-delta_C/2).
 // ---------------------------------------------------------------------------
+template <int AM>
 __device__ __forceinline__ void
 intensity_bwd_tile(const int tile, const uint2 *__restrict__ ranges, const uint32_t *__restrict__ vals,
                    const CompRec *__restrict__ comp, const ImgRec *__restrict__ img, const float4 *__restrict__ accI,
@@ -647,26 +675,29 @@ intensity_bwd_tile(const int tile, const uint2 *__restrict__ ranges, const uint3
                 {
                     const bool in = (q0 >= cut) & (sub + j0 < lim);
                     const float e = in ? ex2_approx(q0) : 0.f;
-                    const float alpha = __fmul_rn(Q0.z, e);
+                    const float alpha = alpha_of<AM>(Q0.z, e);
                     // relative error of a few ulp per step; the factor 1 - alpha is
                     // the forward's (same alpha bits, same rounding)
-                    const float Td = T * rcp_approx(__fsub_rn(1.f, alpha));
+                    const float om = __fsub_rn(1.f, alpha);
+                    const float Td = T * rcp_approx(om);
                     T = (in & !first) ? Td : T;
                     first = first & !in;
                     const float d = Q0.w - B;
                     B = fmaf(alpha, d, B);
-                    W[j0 * WSTRIDE + c.toff] = T * d * e;
+                    // weight of the profile: d alpha / d G = o, or tau (1 - alpha)
+                    W[j0 * WSTRIDE + c.toff] = T * d * (AM ? e * om : e);
                 }
                 {
                     const bool in = two & (q1 >= cut) & (sub + j1 < lim);
                     const float e = in ? ex2_approx(q1) : 0.f;
-                    const float alpha = __fmul_rn(Q1.z, e);
-                    const float Td = T * rcp_approx(__fsub_rn(1.f, alpha));
+                    const float alpha = alpha_of<AM>(Q1.z, e);
+                    const float om = __fsub_rn(1.f, alpha);
+                    const float Td = T * rcp_approx(om);
                     T = (in & !first) ? Td : T;
                     first = first & !in;
                     const float d = Q1.w - B;
                     B = fmaf(alpha, d, B);
-                    if (two) W[j1 * WSTRIDE + c.toff] = T * d * e;
+                    if (two) W[j1 * WSTRIDE + c.toff] = T * d * (AM ? e * om : e);
                 }
             }
             __syncthreads();
@@ -691,6 +722,7 @@ intensity_bwd_tile(const int tile, const uint2 *__restrict__ ranges, const uint3
     }
 }
 
+template <int AM>
 __global__ void __launch_bounds__(256)
 k_intensity_bwd(const uint2 *__restrict__ ranges, const uint32_t *__restrict__ vals, const CompRec *__restrict__ comp,
                 const ImgRec *__restrict__ img, const float4 *__restrict__ accI, const float *__restrict__ Tstop,
@@ -698,17 +730,21 @@ k_intensity_bwd(const uint2 *__restrict__ ranges, const uint32_t *__restrict__ v
                 const StatusDev *st, float4 *__restrict__ accC, const TileSched sc) {
     if (st->code != SDGR_OK) return;
     for_tiles(sc, [&](int tile) {
-        intensity_bwd_tile(tile, ranges, vals, comp, img, accI, Tstop, last, views, V, cut, accC);
+        intensity_bwd_tile<AM>(tile, ranges, vals, comp, img, accI, Tstop, last, views, V, cut, accC);
     });
 }
 
 cudaError_t launch_intensity_bwd(const uint2 *ranges, const uint32_t *vals, const CompRec *comp, const ImgRec *img,
                                  const float4 *accI, const float *Tstop, const int32_t *last, const ViewDev *views,
-                                 int V, int tiles, float cut, const StatusDev *st, float4 *accC,
+                                 int V, int tiles, float cut, int alpha_mode, const StatusDev *st, float4 *accC,
                                  const TileSched &sched, cudaStream_t s) {
     if (tiles <= 0) return cudaSuccess;
-    k_intensity_bwd<<<raster_grid(tiles, sched), TILE_PIX, 0, s>>>(ranges, vals, comp, img, accI, Tstop, last, views,
-                                                                   V, cut, st, accC, sched);
+    if (alpha_mode)
+        k_intensity_bwd<1><<<raster_grid(tiles, sched), TILE_PIX, 0, s>>>(ranges, vals, comp, img, accI, Tstop, last,
+                                                                          views, V, cut, st, accC, sched);
+    else
+        k_intensity_bwd<0><<<raster_grid(tiles, sched), TILE_PIX, 0, s>>>(ranges, vals, comp, img, accI, Tstop, last,
+                                                                          views, V, cut, st, accC, sched);
     note_launch();
     return cudaGetLastError();
 }
@@ -720,10 +756,10 @@ int raster_blocks_per_sm(int kernel) {
     int n = 0;
     cudaError_t e = cudaErrorInvalidValue;
     switch (kernel) {
-        case 0: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_intensity_fwd, TILE_PIX, 0); break;
+        case 0: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_intensity_fwd<0>, TILE_PIX, 0); break;
         case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_splat_fwd, TILE_PIX, 0); break;
         case 2: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_splat_bwd, TILE_PIX, 0); break;
-        default: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_intensity_bwd, TILE_PIX, 0); break;
+        default: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_intensity_bwd<0>, TILE_PIX, 0); break;
     }
     if (e != cudaSuccess || n < 1) {
         (void)cudaGetLastError();

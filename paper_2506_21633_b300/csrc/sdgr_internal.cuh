@@ -111,6 +111,10 @@ struct alignas(16) ImgRec {
 // entry is syy (same margin as the tile rectangles).
 __device__ __forceinline__ float ellipse_ry(float syy, float K) { return K * sqrtf(syy) * 1.0001f + 1e-3f; }
 
+// softplus(x) = log(1 + e^x) = -log(1 - sigmoid(x)): the optical depth of the
+// Beer-Lambert opacity (alpha_mode 1).
+__device__ __forceinline__ float softplus(float x) { return x > 0.f ? x + log1pf(expf(-x)) : log1pf(expf(x)); }
+
 __device__ __forceinline__ float ex2_approx(float x) {
     float y;
     asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
@@ -167,7 +171,7 @@ void note_launch();
 cudaError_t launch_upload(const void *host_src, size_t bytes, void *dev_dst, cudaStream_t s);
 
 cudaError_t launch_preprocess(const float4 *params, const float4 *sh, int sh_count, const ViewDev *views, int V,
-                              int64_t VG, float K, float eps, int norm_mode, CompRec *comp, ImgRec *img, uint2 *rectC, uint2 *rectI, uint32_t *cntC,
+                              int64_t VG, float K, float eps, int norm_mode, int alpha_mode, CompRec *comp, ImgRec *img, uint2 *rectC, uint2 *rectI, uint32_t *cntC,
                               uint32_t *cntI, uint32_t *dkey, uint32_t *dval, int sms, cudaStream_t s);
 
 // exclusive scans (scratch: see scan_scratch_elems)
@@ -197,7 +201,7 @@ cudaError_t launch_ranges(const uint32_t *keys, const StatusDev *st, int64_t cap
 
 // raster passes
 cudaError_t launch_intensity_fwd(const uint2 *ranges, const uint32_t *vals, const CompRec *comp, const ViewDev *views,
-                                 int V, int tiles, float cut, float Tfloor, const StatusDev *st, float *A,
+                                 int V, int tiles, float cut, float Tfloor, int alpha_mode, const StatusDev *st, float *A,
                                  float *Tstop, int32_t *last, const TileSched &sched, cudaStream_t s);
 cudaError_t launch_splat_fwd(const uint2 *rangesI, const uint32_t *vals, const ImgRec *img, const CompRec *comp,
                              const float *A, const ViewDev *views, int V, int tiles, float cut, const StatusDev *st,
@@ -207,7 +211,8 @@ cudaError_t launch_splat_bwd(const uint2 *rangesI, const uint32_t *vals, const I
                              const TileSched &sched, cudaStream_t s);
 cudaError_t launch_intensity_bwd(const uint2 *ranges, const uint32_t *vals, const CompRec *comp, const ImgRec *img,
                                  const float4 *accI, const float *Tstop, const int32_t *last, const ViewDev *views,
-                                 int V, int tiles, float cut, const StatusDev *st, float4 *accC, const TileSched &sched, cudaStream_t s);
+                                 int V, int tiles, float cut, int alpha_mode, const StatusDev *st, float4 *accC,
+                                 const TileSched &sched, cudaStream_t s);
 // CTAs per SM of a raster kernel at 256 threads (occupancy query, cached).
 int raster_blocks_per_sm(int kernel);
 cudaError_t launch_count_pairs(const uint2 *ranges, const uint32_t *vals, const CompRec *comp, const ImgRec *img,
@@ -217,6 +222,7 @@ cudaError_t launch_intensity_out(const CompRec *comp, const float *A, int64_t VG
 // parameter adjoint, optimiser, loss
 cudaError_t launch_param_bwd(const float4 *params, const ViewDev *views, const SceneDev *scenes,
                              const int32_t *scene_views, int n_scenes, int64_t n_gauss, float eps, int norm_mode,
+                             int alpha_mode,
                              const float *A, const CompRec *comp, const float4 *accI, const float4 *accC,
                              const StatusDev *st, float4 *grads, float4 *dsh, float *dens_accum,
                              float *dens_count, int sms, cudaStream_t s);

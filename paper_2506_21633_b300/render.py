@@ -39,9 +39,10 @@ class Renderer:
     scene/view set is learned from the device status word (one host sync in
     `prepare(check=True)`)."""
 
-    def __init__(self, cutoff_K=5.0, dilation_eps=0.3, T_min=0.0, norm_mode=0, device=None, inst_slack=1.15):
+    def __init__(self, cutoff_K=5.0, dilation_eps=0.3, T_min=0.0, norm_mode=0, device=None, inst_slack=1.15,
+                 alpha_mode=0):
         L.lib()  # fail loudly if the library is missing
-        self.cfg = L.make_cfg(cutoff_K, dilation_eps, T_min, norm_mode)
+        self.cfg = L.make_cfg(cutoff_K, dilation_eps, T_min, norm_mode, alpha_mode)
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
         self.inst_slack = inst_slack
         self.ws = None

@@ -22,7 +22,7 @@ def _upstream(views, seed):
 
 def _ref(p64, views, G, culled=True, **cfg):
     ocfg = oracle.cfg(K=cfg.get("cutoff_K", 5.0), eps=cfg.get("dilation_eps", 0.3), T_min=cfg.get("T_min", 0.0),
-                      norm_mode=cfg.get("norm_mode", 0))
+                      norm_mode=cfg.get("norm_mode", 0), alpha_mode=cfg.get("alpha_mode", 0))
     return oracle.grad(p64, views, G, ocfg, culled=culled)[0]
 
 
@@ -73,7 +73,8 @@ def test_config2_view_l1():
     assert_grads(g_gpu, g_an)
 
 
-@pytest.mark.parametrize("cfg", [dict(norm_mode=1), dict(T_min=1e-4)])
+@pytest.mark.parametrize("cfg", [dict(norm_mode=1), dict(T_min=1e-4), dict(alpha_mode=1),
+                                 dict(alpha_mode=1, T_min=1e-4)])
 def test_options(cfg):
     params = sc.vehicle_box_scene(500, seed=33, extent=(2.0, 1.5, 1.0), log_s_mean=math.log(0.1), center=(0, 0, 0))
     views = sc.random_views(2, seed=34, size=48, res=0.08, center=(0, 0, 0))

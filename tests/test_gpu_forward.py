@@ -18,7 +18,7 @@ def _check(params, views, scene_offsets=None, culled=True, **cfg):
     p32, p64 = f32(params)
     ims, inten, _, _ = gpu_forward(p32, views, scene_offsets, **cfg)
     ocfg = oracle.cfg(K=cfg.get("cutoff_K", 5.0), eps=cfg.get("dilation_eps", 0.3), T_min=cfg.get("T_min", 0.0),
-                      norm_mode=cfg.get("norm_mode", 0))
+                      norm_mode=cfg.get("norm_mode", 0), alpha_mode=cfg.get("alpha_mode", 0))
     offs = scene_offsets or [0, p64.shape[0]]
     ref_imgs, ref_I = [], []
     for v in views:
@@ -69,7 +69,8 @@ def test_config3_shaped():
     _check(params, views)
 
 
-@pytest.mark.parametrize("cfg", [dict(norm_mode=1), dict(cutoff_K=3.0), dict(dilation_eps=0.0), dict(T_min=1e-4)])
+@pytest.mark.parametrize("cfg", [dict(norm_mode=1), dict(cutoff_K=3.0), dict(dilation_eps=0.0), dict(T_min=1e-4),
+                                 dict(alpha_mode=1), dict(alpha_mode=1, norm_mode=1)])
 def test_options(cfg):
     params = sc.vehicle_box_scene(1500, seed=5, log_s_mean=math.log(0.1))
     views = sc.random_views(2, seed=8, size=72, res=0.08)
