@@ -281,6 +281,15 @@ sdgr_status sdgr_densify(const float *params, const float *grads, const float *a
 sdgr_status sdgr_adam_step(float *params, const float *grads, float *m, float *v, int64_t N, const float *lr,
                            float b1, float b2, float eps, int32_t step, void *stream);
 
+/* Step a13 for any other trained float32 array (the SH coefficients of the
+ * view-dependent scattering): the same Adam update with one learning rate
+ * for every element.  x, grads, m, v: device [n] float32, 16-byte aligned,
+ * n a multiple of 4; x, m, v updated in place.
+ * Errors: SDGR_ERR_INVALID (n < 0 or not a multiple of 4, step < 1,
+ * misaligned pointers). */
+sdgr_status sdgr_adam_step_flat(float *x, const float *grads, float *m, float *v, int64_t n, float lr, float b1,
+                                float b2, float eps, int32_t step, void *stream);
+
 /* Step a13, graph-replayable form: as sdgr_adam_step, but the 1-based step
  * count lives in device memory.  step: device int32; the call increments
  * *step first and uses the new value, so a captured CUDA graph that

@@ -23,7 +23,7 @@ EXPORTS = (
     "sdgr_read_status", "sdgr_status_string", "sdgr_profile_enable", "sdgr_profile_read",
     "sdgr_count_pairs", "sdgr_launch_count", "sdgr_render_fwd_noalloc", "sdgr_adam_step_device",
     "sdgr_copy_status_async", "sdgr_set_sh", "sdgr_set_densify_stats", "sdgr_densify_scratch_bytes",
-    "sdgr_densify", "sdgr_set_schedule",
+    "sdgr_densify", "sdgr_set_schedule", "sdgr_adam_step_flat",
 )
 
 SCHED_ORDERED = 1
@@ -95,6 +95,7 @@ def lib():
         L.sdgr_launch_count.argtypes = []
         L.sdgr_render_fwd_noalloc.argtypes = [vp, i64, P(SdgrView), i32, P(SdgrCfg), vp, vp, vp]
         L.sdgr_adam_step.argtypes = [vp, vp, vp, vp, i64, P(ctypes.c_float), f32, f32, f32, i32, vp]
+        L.sdgr_adam_step_flat.argtypes = [vp, vp, vp, vp, i64, f32, f32, f32, f32, i32, vp]
         L.sdgr_l1_loss.argtypes = [vp, vp, i64, vp, vp, vp]
         L.sdgr_adam_step_device.argtypes = [vp, vp, vp, vp, i64, P(ctypes.c_float), f32, f32, f32, vp, vp]
         L.sdgr_read_status.argtypes = [vp, P(ctypes.c_int64)]
@@ -212,6 +213,12 @@ def sdgr_adam_step(p, g, m, v, N, lr, b1, b2, eps, step, stream):
     _check("sdgr_adam_step", lib().sdgr_adam_step(ctypes.c_void_p(p), ctypes.c_void_p(g), ctypes.c_void_p(m),
                                                   ctypes.c_void_p(v), int(N), lr_arr, b1, b2, eps, int(step),
                                                   ctypes.c_void_p(stream)))
+
+
+def sdgr_adam_step_flat(x, g, m, v, n, lr, b1, b2, eps, step, stream):
+    _check("sdgr_adam_step_flat", lib().sdgr_adam_step_flat(ctypes.c_void_p(x), ctypes.c_void_p(g), ctypes.c_void_p(m),
+                                                            ctypes.c_void_p(v), int(n), float(lr), b1, b2, eps,
+                                                            int(step), ctypes.c_void_p(stream)))
 
 
 def sdgr_adam_step_device(p, g, m, v, N, lr, b1, b2, eps, step_ptr, stream):

@@ -564,6 +564,23 @@ sdgr_status sdgr_adam_step(float *params, const float *grads, float *m, float *v
     return SDGR_OK;
 }
 
+sdgr_status sdgr_adam_step_flat(float *x, const float *grads, float *m, float *v, int64_t n, float lr, float b1,
+                                float b2, float eps, int32_t step, void *stream) {
+    if (n < 0 || n % 4 != 0 || step < 1) return SDGR_ERR_INVALID;
+    if (n == 0) return SDGR_OK;
+    if (!x || !grads || !m || !v) return SDGR_ERR_INVALID;
+    if (((uintptr_t)x | (uintptr_t)grads | (uintptr_t)m | (uintptr_t)v) % 16 != 0) return SDGR_ERR_INVALID;
+    if (!(b1 >= 0.f && b1 < 1.f && b2 >= 0.f && b2 < 1.f && eps >= 0.f)) return SDGR_ERR_INVALID;
+    int dev = 0, sms = 148;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const float lr5[5] = {lr, lr, lr, lr, lr};  // one rate for every component
+    CK(launch_adam(reinterpret_cast<float4 *>(x), reinterpret_cast<const float4 *>(grads),
+                   reinterpret_cast<float4 *>(m), reinterpret_cast<float4 *>(v), n / 4, lr5, b1, b2, eps, step, sms,
+                   static_cast<cudaStream_t>(stream)));
+    return SDGR_OK;
+}
+
 sdgr_status sdgr_adam_step_device(float *params, const float *grads, float *m, float *v, int64_t N, const float *lr,
                                   float b1, float b2, float eps, int32_t *step, void *stream) {
     if (N < 0 || !lr || !step) return SDGR_ERR_INVALID;

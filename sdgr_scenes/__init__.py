@@ -142,6 +142,26 @@ def box_surface_scene(n, boxes, rng, s_lo=0.05, s_hi=0.3, s_normal=0.01, ground=
     return _pack(mu, opa, log_s, P, q)
 
 
+def tank_scene(n, seed, s_lo=0.03, s_hi=0.12):
+    """Vehicle-shaped reconstruction target (stand-in for the paper's tank
+    CAD renders): Gaussians on the faces of a lower hull with tracks, an upper
+    hull, a turret and a gun barrel (metres, ground at z = 0, centred on the
+    origin)."""
+    rng = np.random.default_rng(seed)
+    boxes = [(-3.4, -1.8, 0.0, 6.8, 3.6, 0.5),    # tracks / lower hull
+             (-3.1, -1.5, 0.5, 6.2, 3.0, 0.8),    # upper hull
+             (-1.4, -1.1, 1.3, 2.4, 2.2, 0.7),    # turret
+             (1.0, -0.12, 1.62, 3.2, 0.24, 0.24)]  # barrel
+    return box_surface_scene(n, boxes, rng, s_lo=s_lo, s_hi=s_hi, s_normal=0.01)
+
+
+def circular_views(thetas_deg, n_az, size, res, center=(0.0, 0.0, 0.8), phase_deg=0.0):
+    """Circular tracks: n_az azimuths 360/n_az apart at each grazing angle
+    (the multi-view acquisition of the paper's simulated targets)."""
+    return [make_view(phase_deg + 360.0 * k / n_az, t, res, res, size, size, center)
+            for t in thetas_deg for k in range(n_az)]
+
+
 def config2(n=50000, n_views=72):
     """Forward+backward: 50k Gaussians on the faces of 3 boxes (5-20 m sides)
     in a 60x60 m area, 512x512 at 0.15 m, 72 views every 5 deg at 40 deg."""
