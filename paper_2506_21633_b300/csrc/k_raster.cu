@@ -297,7 +297,9 @@ intensity_fwd_tile(const int tile, const uint2 *__restrict__ ranges, const uint3
     __shared__ uint32_t sid[BATCH];
     __shared__ uint8_t sperm[BATCH];
     __shared__ __align__(16) float W[SUB * WSTRIDE];
+    __shared__ __align__(16) float zero4[4];
     const int t = threadIdx.x, warp = t >> 5;
+    if (t < 4) zero4[t] = 0.f;
     const TileCtx c = tile_ctx(views, V, tile);
     const LaneXY L = lane_xy();
     const uint2 r = ranges[tile];
@@ -344,13 +346,14 @@ intensity_fwd_tile(const int tile, const uint2 *__restrict__ ranges, const uint3
             uint32_t mb = j < ns ? sM[sub + j] : 0u;
             const float *wr = W + j * WSTRIDE + 4 * cc;
             float s = 0.f;
-            while (__any_sync(0xffffffffu, mb)) {
-                if (mb) {
-                    const int b = __ffs(mb) - 1;
-                    mb &= mb - 1;
-                    const float4 w4 = *reinterpret_cast<const float4 *>(wr + 32 * b);
-                    s += (w4.x + w4.y) + (w4.z + w4.w);
-                }
+            // as many rounds as the warp's largest block count; a group out of
+            // blocks reads a zero float4
+            const int rounds = __reduce_max_sync(0xffffffffu, __popc(mb));
+            for (int i = 0; i < rounds; ++i) {
+                const float *src = mb ? wr + 32 * (__ffs(mb) - 1) : zero4;
+                mb &= mb - 1;
+                const float4 w4 = *reinterpret_cast<const float4 *>(src);
+                s += (w4.x + w4.y) + (w4.z + w4.w);
             }
             s += __shfl_xor_sync(0xffffffffu, s, 1);
             s += __shfl_xor_sync(0xffffffffu, s, 2);
@@ -502,7 +505,9 @@ splat_bwd_tile(const int tile, const uint2 *__restrict__ rangesI, const uint32_t
     __shared__ uint32_t sid[BATCH];
     __shared__ uint8_t sperm[BATCH];
     __shared__ __align__(16) float sg[TILE_PIX];  // dL/dS of the tile's pixels, in table layout
+    __shared__ __align__(16) float zero4[4];
     const int t = threadIdx.x, warp = t >> 5;
+    if (t < 4) zero4[t] = 0.f;
     const TileCtx c = tile_ctx(views, V, tile);
     const uint2 r = rangesI[tile];
     const float g = c.inside ? dLdS[c.pix] : 0.f;
@@ -538,13 +543,16 @@ splat_bwd_tile(const int tile, const uint2 *__restrict__ rangesI, const uint32_t
             const float2 uv = sU[ks];
             const float dx0 = (float)cc - uv.x, dy00 = -uv.y;
             float m[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-            while (__any_sync(0xffffffffu, mb)) {
-                if (mb) {
-                    const int b = __ffs(mb) - 1;
+            const float dx1 = dx0 + 8.f;
+            const int rounds = __reduce_max_sync(0xffffffffu, __popc(mb));
+            for (int i = 0; i < rounds; ++i) {
+                {
+                    const int b = mb ? __ffs(mb) - 1 : 0;
+                    const float *src = mb ? sg + 32 * b + 4 * cc : zero4;  // no block left: dL/dS = 0
                     mb &= mb - 1;
-                    const float dx = dx0 + (float)(8 * (b & 1));
-                    const float dy0 = dy00 + (float)(4 * (b >> 1));
-                    const float4 g4 = *reinterpret_cast<const float4 *>(sg + 32 * b + 4 * cc);
+                    const float dx = (b & 1) ? dx1 : dx0;
+                    const float dy0 = fmaf(4.f, (float)(b >> 1), dy00);
+                    const float4 g4 = *reinterpret_cast<const float4 *>(src);
                     // exponent along the column: qa dx^2 + (qb dx) dy + qc dy^2
                     const float Aq = G.x * dx * dx, Bq = G.y * dx;
                     float4 w;
@@ -612,8 +620,10 @@ intensity_bwd_tile(const int tile, const uint2 *__restrict__ ranges, const uint3
     __shared__ uint32_t sid[BATCH];
     __shared__ uint8_t sperm[BATCH];
     __shared__ __align__(16) float W[SUB * WSTRIDE];
+    __shared__ __align__(16) float zero4[4];
     __shared__ int smax;
     const int t = threadIdx.x, warp = t >> 5;
+    if (t < 4) zero4[t] = 0.f;
     const TileCtx c = tile_ctx(views, V, tile);
     const LaneXY L = lane_xy();
     const uint2 r = ranges[tile];
@@ -707,13 +717,14 @@ intensity_bwd_tile(const int tile, const uint2 *__restrict__ ranges, const uint3
             const float dx0 = (float)cc - uv.x, dy00 = -uv.y;
             const float *wr = W + j * WSTRIDE + 4 * cc;
             float m[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-            while (__any_sync(0xffffffffu, mb)) {
-                if (mb) {
-                    const int b = __ffs(mb) - 1;
-                    mb &= mb - 1;
-                    const float4 w4 = *reinterpret_cast<const float4 *>(wr + 32 * b);
-                    block_moments(w4, dx0 + (float)(8 * (b & 1)), dy00 + (float)(4 * (b >> 1)), m);
-                }
+            const float dx1 = dx0 + 8.f;
+            const int rounds = __reduce_max_sync(0xffffffffu, __popc(mb));
+            for (int i = 0; i < rounds; ++i) {
+                const int b = mb ? __ffs(mb) - 1 : 0;
+                const float *src = mb ? wr + 32 * b : zero4;
+                mb &= mb - 1;
+                const float4 w4 = *reinterpret_cast<const float4 *>(src);
+                block_moments(w4, (b & 1) ? dx1 : dx0, fmaf(4.f, (float)(b >> 1), dy00), m);
             }
             reduce8(m);
             if (cc == 0 && j < ns) add_moments(accC, sid[sub + j], m);
