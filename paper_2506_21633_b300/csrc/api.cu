@@ -28,7 +28,7 @@ struct Layout {
     size_t dk0, dv0, dk1, dv1;
     size_t scnt, soff, scan64;
     size_t ik0, iv0, ik1, iv1;
-    size_t hist, scan32, ranges, segs, order, work;
+    size_t hist, scan32, ranges, segs, order, work, vhist, voff, vt, vbase, vscan;
     size_t A, Tstop, last, accI, accC;
     size_t total;
 };
@@ -84,6 +84,11 @@ Layout make_layout(const sdgr_caps *c) {
     L.segs = take((2 * V + 2) * sizeof(SegDev));
     L.order = take(2 * NT * 4);
     L.work = take(sizeof(TileWorkDev));
+    L.vhist = take(2 * V * 32 * 4);
+    L.voff = take(2 * V * 32 * 4);
+    L.vt = take(2 * V * 4);
+    L.vbase = take(2 * V * 4);
+    L.vscan = take(scan_scratch_elems((int64_t)(2 * V)) * 4);
     L.A = take(VG * 4);
     L.Tstop = take(NP * 4);
     L.last = take(NP * 4);
@@ -419,7 +424,9 @@ sdgr_status sdgr_bin_sort(sdgr_ws *ws, void *stream) {
     uint2 *ranges = ws->at<uint2>(L.ranges);
     CK(cudaMemsetAsync(ranges, 0, (size_t)2 * ws->tiles * sizeof(uint2), s));
     CK(launch_ranges(ws->inst_keys, st, ws->caps.max_instances, ranges, ws->sms, s));
-    CK(launch_tile_order(ranges, ws->tiles, ws->at<TileWorkDev>(L.work), ws->at<int32_t>(L.order), ws->sms, s));
+    CK(launch_tile_order(ranges, ws->tiles, views, ws->V, ws->at<TileWorkDev>(L.work), ws->at<int32_t>(L.order),
+                         ws->at<uint32_t>(L.vhist), ws->at<uint32_t>(L.voff), ws->at<uint32_t>(L.vt),
+                         ws->at<uint32_t>(L.vbase), ws->at<uint32_t>(L.vscan), ws->sms, s));
     prof_end(ws, pk1, s);
     ws->stage = 2;
     return SDGR_OK;

@@ -494,81 +494,88 @@ cudaError_t launch_ranges(const uint32_t *keys, const StatusDev *st, int64_t cap
 namespace sdgr {
 
 // ---------------------------------------------------------------------------
-// Raster work lists.  Per plane: the tiles with a non-empty list, in
-// descending order of the bit length of the list size (a bucketed
-// longest-processing-time order: long tiles start first, short ones fill the
-// tail).  Three passes over the 2 x tiles ranges: bucket histogram, bucket
-// offsets, scatter with block-aggregated slot reservations.  The order within
-// a bucket depends on atomic timing; a tile's result does not depend on when
-// it runs.
+// Raster work lists.  Per plane: the tiles with a non-empty list, views in
+// order, and inside each view in descending order of the bit length of the
+// list size (a bucketed longest-processing-time order that keeps the tiles
+// of one view -- and the records they share -- together on the GPU).
+// Passes: per (plane, view, bucket) histogram; per (plane, view) totals;
+// exclusive scan of the totals; per-view bucket offsets; scatter.  The
+// order inside a bucket depends on atomic timing; a tile's result does not
+// depend on when it runs.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ int order_bucket(uint2 r) { return 31 - __clz((int)(r.y - r.x)); }
 
-__global__ void k_order_hist(const uint2 *__restrict__ ranges, int tiles, TileWorkDev *w) {
-    __shared__ int h[64];
-    if (threadIdx.x < 64) h[threadIdx.x] = 0;
-    __syncthreads();
+__global__ void k_order_hist(const uint2 *__restrict__ ranges, int tiles, const ViewDev *__restrict__ views, int V,
+                             uint32_t *vhist) {
     const int64_t n = 2 * (int64_t)tiles, stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += stride) {
         const uint2 r = ranges[k];
-        if (r.y > r.x) atomicAdd(&h[(k >= tiles ? 32 : 0) + order_bucket(r)], 1);
+        if (r.y <= r.x) continue;
+        const int p = k >= tiles;
+        const int v = view_of_tile(views, V, k - (int64_t)p * tiles);
+        atomicAdd(&vhist[((int64_t)p * V + v) * 32 + order_bucket(r)], 1u);
     }
-    __syncthreads();
-    if (threadIdx.x < 64 && h[threadIdx.x]) atomicAdd(&w->hist[0][0] + threadIdx.x, h[threadIdx.x]);
 }
 
-__global__ void k_order_offsets(TileWorkDev *w) {
-    if (threadIdx.x < 2) {
-        const int p = threadIdx.x;
-        int acc = 0;
+__global__ void k_order_totals(const uint32_t *__restrict__ vhist, int V, uint32_t *vt) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= 2 * (int64_t)V) return;
+    uint32_t acc = 0;
+    for (int b = 0; b < 32; ++b) acc += vhist[i * 32 + b];
+    vt[i] = acc;
+}
+
+__global__ void k_order_offsets(const uint32_t *__restrict__ vhist, const uint32_t *__restrict__ vt,
+                                const uint32_t *__restrict__ vbase, int V, uint32_t *voff, TileWorkDev *w) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < 2 * (int64_t)V) {
+        const int p = i >= V;
+        uint32_t acc = vbase[i] - (p ? vbase[V] : 0u);  // plane-local base
         for (int b = 31; b >= 0; --b) {
-            w->off[p][b] = acc;
-            acc += w->hist[p][b];
+            voff[i * 32 + b] = acc;
+            acc += vhist[i * 32 + b];
         }
-        w->count[p] = acc;
     }
-    if (threadIdx.x < 4) w->next[threadIdx.x] = 0;
+    if (i == 0) {
+        w->count[0] = (int32_t)vbase[V];
+        w->count[1] = (int32_t)(vbase[2 * V - 1] + vt[2 * V - 1] - vbase[V]);
+        for (int k = 0; k < 4; ++k) w->next[k] = 0;
+    }
 }
 
-__global__ void k_order_scatter(const uint2 *__restrict__ ranges, int tiles, TileWorkDev *w, int32_t *order) {
-    __shared__ int h[64], base[64];
+__global__ void k_order_scatter(const uint2 *__restrict__ ranges, int tiles, const ViewDev *__restrict__ views, int V,
+                                uint32_t *voff, int32_t *order) {
     const int64_t n = 2 * (int64_t)tiles, stride = (int64_t)gridDim.x * blockDim.x;
-    const int64_t first = (int64_t)blockIdx.x * blockDim.x;
-    for (int64_t k0 = first; k0 < n; k0 += stride) {  // block-uniform rounds
-        if (threadIdx.x < 64) h[threadIdx.x] = 0;
-        __syncthreads();
-        const int64_t k = k0 + threadIdx.x;
-        int slot = -1, local = 0;
-        if (k < n) {
-            const uint2 r = ranges[k];
-            if (r.y > r.x) {
-                slot = (k >= tiles ? 32 : 0) + order_bucket(r);
-                local = atomicAdd(&h[slot], 1);
-            }
-        }
-        __syncthreads();
-        if (threadIdx.x < 64 && h[threadIdx.x]) base[threadIdx.x] = atomicAdd(&w->off[0][0] + threadIdx.x, h[threadIdx.x]);
-        __syncthreads();
-        if (slot >= 0) {
-            const int p = slot >> 5;
-            order[(int64_t)p * tiles + base[slot] + local] = (int32_t)(k - (int64_t)p * tiles);
-        }
-        __syncthreads();
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += stride) {
+        const uint2 r = ranges[k];
+        if (r.y <= r.x) continue;
+        const int p = k >= tiles;
+        const int64_t lt = k - (int64_t)p * tiles;
+        const int v = view_of_tile(views, V, lt);
+        const uint32_t slot = atomicAdd(&voff[((int64_t)p * V + v) * 32 + order_bucket(r)], 1u);
+        order[(int64_t)p * tiles + slot] = (int32_t)lt;
     }
 }
 
-cudaError_t launch_tile_order(const uint2 *ranges, int tiles, TileWorkDev *work, int32_t *order, int sms,
-                              cudaStream_t s) {
+cudaError_t launch_tile_order(const uint2 *ranges, int tiles, const ViewDev *views, int V, TileWorkDev *work,
+                              int32_t *order, uint32_t *vhist, uint32_t *voff, uint32_t *vt, uint32_t *vbase,
+                              uint32_t *scratch, int sms, cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(work, 0, sizeof(TileWorkDev), s);
+    if (e != cudaSuccess || tiles <= 0 || V <= 0) return e;
+    e = cudaMemsetAsync(vhist, 0, (size_t)2 * V * 32 * sizeof(uint32_t), s);
     if (e != cudaSuccess) return e;
-    if (tiles <= 0) return cudaSuccess;
     int64_t blocks = (2 * (int64_t)tiles + 255) / 256;
     if (blocks > (int64_t)sms * 4) blocks = (int64_t)sms * 4;
-    k_order_hist<<<(unsigned)blocks, 256, 0, s>>>(ranges, tiles, work);
+    const unsigned vblocks = (unsigned)((2 * (int64_t)V + 255) / 256);
+    k_order_hist<<<(unsigned)blocks, 256, 0, s>>>(ranges, tiles, views, V, vhist);
     note_launch();
-    k_order_offsets<<<1, 32, 0, s>>>(work);
+    k_order_totals<<<vblocks, 256, 0, s>>>(vhist, V, vt);
     note_launch();
-    k_order_scatter<<<(unsigned)blocks, 256, 0, s>>>(ranges, tiles, work, order);
+    e = launch_scan_u32(vt, vbase, 2 * (int64_t)V, scratch, s);
+    if (e != cudaSuccess) return e;
+    k_order_offsets<<<vblocks, 256, 0, s>>>(vhist, vt, vbase, V, voff, work);
+    note_launch();
+    k_order_scatter<<<(unsigned)blocks, 256, 0, s>>>(ranges, tiles, views, V, voff, order);
     note_launch();
     return cudaGetLastError();
 }

@@ -63,14 +63,14 @@ struct alignas(16) StatusDev {
 };
 
 // Work list of the raster kernels, rebuilt by every bin/sort: per plane the
-// tiles with a non-empty instance list, longest list first (longest-
-// processing-time order, by the bit length of the list size).
+// tiles with a non-empty instance list, view by view, and inside a view the
+// longest lists first (longest-processing-time order by the bit length of
+// the list size).  Per (plane, view, bucket) counters live in a separate
+// array of 2 x V x 32 entries.
 struct alignas(16) TileWorkDev {
     int32_t count[2];     // non-empty tiles per plane
     int32_t next[4];      // item counters of the persistent launches (K3, K4, K5, K6)
     int32_t pad[2];
-    int32_t hist[2][32];  // tiles per bucket (bucket = bit length of the list size - 1)
-    int32_t off[2][32];   // next free slot per bucket
 };
 
 // How a raster launch maps CTAs to tiles.  order == nullptr: CTA i takes tile
@@ -194,8 +194,11 @@ cudaError_t launch_check_capacity(const unsigned long long *scnt, const unsigned
 cudaError_t launch_emit(const uint32_t *sorted_vg, const unsigned long long *soff, const uint2 *rectC,
                         const uint2 *rectI, const ViewDev *views, int V, int64_t VG, int total_tiles,
                         const StatusDev *st, uint32_t *keys, uint32_t *vals, int sms, cudaStream_t s);
-cudaError_t launch_tile_order(const uint2 *ranges, int tiles, TileWorkDev *work, int32_t *order, int sms,
-                              cudaStream_t s);
+// vhist, voff: 2 * V * 32 entries; vt, vbase: 2 * V; scratch:
+// scan_scratch_elems(2 * V) entries.
+cudaError_t launch_tile_order(const uint2 *ranges, int tiles, const ViewDev *views, int V, TileWorkDev *work,
+                              int32_t *order, uint32_t *vhist, uint32_t *voff, uint32_t *vt, uint32_t *vbase,
+                              uint32_t *scratch, int sms, cudaStream_t s);
 cudaError_t launch_ranges(const uint32_t *keys, const StatusDev *st, int64_t cap, uint2 *ranges, int sms,
                           cudaStream_t s);
 
