@@ -33,6 +33,8 @@ namespace sdgr {
 constexpr int BATCH = 256;    // Gaussian records staged per batch
 constexpr int SUB = 32;       // Gaussians per weight table
 constexpr int WSTRIDE = 264;  // row stride of the weight table (floats)
+constexpr int SBATCH = 1024;  // records staged per batch by the splat adjoint (no weight table: fewer barriers)
+constexpr int SPER = SBATCH / 256;  // records staged per thread
 
 struct TileCtx {
     int v;
@@ -499,11 +501,11 @@ __device__ __forceinline__ void
 splat_bwd_tile(const int tile, const uint2 *__restrict__ rangesI, const uint32_t *__restrict__ vals,
                const ImgRec *__restrict__ img, const float *__restrict__ dLdS, const ViewDev *__restrict__ views, int V,
                float cut, float4 *__restrict__ accI) {
-    __shared__ float4 sG[BATCH];  // (qa, qb, qc, -)
-    __shared__ float2 sU[BATCH];  // tile-local centre
-    __shared__ uint32_t sM[BATCH];
-    __shared__ uint32_t sid[BATCH];
-    __shared__ uint8_t sperm[BATCH];
+    __shared__ float4 sG[SBATCH];  // (qa, qb, qc, -)
+    __shared__ float2 sU[SBATCH];  // tile-local centre
+    __shared__ uint32_t sM[SBATCH];
+    __shared__ uint32_t sid[SBATCH];
+    __shared__ uint8_t sperm[SBATCH];
     __shared__ __align__(16) float sg[TILE_PIX];  // dL/dS of the tile's pixels, in table layout
     __shared__ __align__(16) float zero4[4];
     const int t = threadIdx.x, warp = t >> 5;
@@ -515,25 +517,31 @@ splat_bwd_tile(const int tile, const uint2 *__restrict__ rangesI, const uint32_t
     if (__syncthreads_count(g != 0.f) == 0) return;
     const float cutm = cut_margin(cut);
     const int cc = t & 7;
-    uint32_t vnext = r.x + t < r.y ? vals[r.x + t] : 0u;
-    for (uint32_t base = r.x; base < r.y; base += BATCH) {
+    uint32_t vnext[SPER];  // next batch's list entries, loaded one batch ahead
+#pragma unroll
+    for (int u = 0; u < SPER; ++u) vnext[u] = r.x + t + 256 * u < r.y ? vals[r.x + t + 256 * u] : 0u;
+    for (uint32_t base = r.x; base < r.y; base += SBATCH) {
         __syncthreads();
-        if (base + t < r.y) {
-            const uint32_t vg = vnext;
-            float4 G;
-            float2 uv;
-            float cn;
-            uint32_t m;
-            stage_img(img, vg, c, cutm, G, uv, cn, m);
-            sG[t] = G;
-            sU[t] = uv;
-            sM[t] = m;
-            sid[t] = vg;
+#pragma unroll
+        for (int u = 0; u < SPER; ++u) {
+            const int k = t + 256 * u;
+            if (base + k < r.y) {
+                const uint32_t vg = vnext[u];
+                float4 G;
+                float2 uv;
+                float cn;
+                uint32_t m;
+                stage_img(img, vg, c, cutm, G, uv, cn, m);
+                sG[k] = G;
+                sU[k] = uv;
+                sM[k] = m;
+                sid[k] = vg;
+            }
+            if (base + SBATCH + k < r.y) vnext[u] = vals[base + SBATCH + k];
         }
-        if (base + BATCH + t < r.y) vnext = vals[base + BATCH + t];
         __syncthreads();
-        const int nb = min(BATCH, (int)(r.y - base));
-        if (warp * 32 < nb) order_by_blocks(sM, warp * 32, min(32, nb - warp * 32), sperm + warp * 32);
+        const int nb = min(SBATCH, (int)(r.y - base));
+        for (int j0 = warp * 32; j0 < nb; j0 += 256) order_by_blocks(sM, j0, min(32, nb - j0), sperm + j0);
         __syncthreads();
         for (int j0 = 0; j0 < nb; j0 += 32) {
             const int k = j0 + sperm[j0 + (t >> 3)];
