@@ -52,7 +52,8 @@ typedef enum {
     SDGR_ERR_CUDA = 2,     /* a CUDA runtime call or launch failed */
     SDGR_ERR_CAPACITY = 3, /* instance capacity exceeded (device status) */
     SDGR_ERR_TIMEOUT = 4,  /* a bounded device wait gave up (device status) */
-    SDGR_ERR_STATE = 5     /* calls made out of order on a workspace */
+    SDGR_ERR_STATE = 5,    /* calls made out of order on a workspace */
+    SDGR_ERR_BOUNDS = 6    /* checked build only: an index left its buffer (device status) */
 } sdgr_status;
 
 /* One radar view (Section II-A-1, eqs. W and R_r).

@@ -12,9 +12,10 @@ import ctypes
 import os
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libsdgr.so")
+# SDGR_CHECKED=1: the build with index checks (see build.py)
+LIB_PATH = os.path.join(_HERE, "libsdgr_checked.so" if os.environ.get("SDGR_CHECKED") == "1" else "libsdgr.so")
 
-SDGR_OK, SDGR_ERR_INVALID, SDGR_ERR_CUDA, SDGR_ERR_CAPACITY, SDGR_ERR_TIMEOUT, SDGR_ERR_STATE = range(6)
+SDGR_OK, SDGR_ERR_INVALID, SDGR_ERR_CUDA, SDGR_ERR_CAPACITY, SDGR_ERR_TIMEOUT, SDGR_ERR_STATE, SDGR_ERR_BOUNDS = range(7)
 
 # every function the header declares (checked by tests/test_abi.py)
 EXPORTS = (
@@ -79,7 +80,8 @@ def lib():
     global _lib
     if _lib is None:
         if not os.path.exists(LIB_PATH):
-            raise ImportError("libsdgr.so is not built (run `python -m paper_2506_21633_b300.build`)")
+            raise ImportError("%s is not built (run `python -m paper_2506_21633_b300.build`)"
+                              % os.path.basename(LIB_PATH))
         L = ctypes.CDLL(LIB_PATH)
         vp, i32, i64, f32 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_float
         P = ctypes.POINTER

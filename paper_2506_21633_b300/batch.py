@@ -158,6 +158,30 @@ class FusedStep:
     def loss_value(self):
         return float(self.loss.item())
 
+    # -- checkpoint / resume ---------------------------------------------------
+    def state_dict(self):
+        """Optimisation state (parameters, Adam moments, device step count,
+        learning rates) as host tensors; `torch.save` writes it."""
+        torch.cuda.synchronize(self.p.device)
+        return {"params": self.p.detach().cpu().clone(), "m": self.m.cpu().clone(), "v": self.v.cpu().clone(),
+                "step": self.step_dev.cpu().clone(), "lr": list(self.lr), "b1": self.b1, "b2": self.b2,
+                "eps": self.eps, "scene_offsets": list(self.scene_offsets)}
+
+    def load_state_dict(self, state):
+        """Restore a state_dict() in place (same Gaussian count); a captured
+        graph stays valid because the tensors keep their storage."""
+        if tuple(state["params"].shape) != tuple(self.p.shape):
+            raise ValueError("checkpoint holds %s parameters, this step %s" % (tuple(state["params"].shape),
+                                                                              tuple(self.p.shape)))
+        with torch.no_grad():
+            self.p.copy_(state["params"])
+            self.m.copy_(state["m"])
+            self.v.copy_(state["v"])
+            self.step_dev.copy_(state["step"])
+        self.lr = list(state["lr"])
+        self.b1, self.b2, self.eps = state["b1"], state["b2"], state["eps"]
+        torch.cuda.synchronize(self.p.device)
+
 
 def plain_step(renderer, params, views, targets, grads, images, dLdS, loss, scene_offsets=None, stream=None):
     """Reference schedule without batching: one view at a time (preprocess,

@@ -2,6 +2,12 @@
 
     python -m paper_2506_21633_b300.build            # build if stale
     python -m paper_2506_21633_b300.build --force    # rebuild
+    python -m paper_2506_21633_b300.build --checked  # libsdgr_checked.so: index checks on
+
+The checked library (-DSDGR_CHECKED) verifies the indices the binning and
+raster stages produce against their buffers and reports a bad one through
+the status word (SDGR_ERR_BOUNDS); SDGR_CHECKED=1 in the environment makes
+the Python binding load it instead of libsdgr.so.
 
 nvcc cross-compiles without a GPU.  Extra nvcc flags can be appended through
 the SDGR_NVCC_FLAGS environment variable (e.g. "-Xptxas -v").
@@ -19,6 +25,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(PKG, "libsdgr.so")
+LIB_CHECKED = os.path.join(PKG, "libsdgr_checked.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -26,10 +33,10 @@ def sources():
     return sorted(glob.glob(os.path.join(CSRC, "*.cu")))
 
 
-def _stale():
-    if not os.path.exists(LIB):
+def _stale(lib=LIB):
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     deps = sources() + glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(INCLUDE, "*.h"))
     return any(os.path.getmtime(p) > t for p in deps)
 
@@ -41,19 +48,22 @@ def nvcc():
     return "nvcc"
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    if not force and not _stale():
-        return LIB
-    tmp = LIB + ".tmp%d" % os.getpid()
+def build(force: bool = False, verbose: bool = False, checked: bool = False) -> str:
+    lib = LIB_CHECKED if checked else LIB
+    if not force and not _stale(lib):
+        return lib
+    tmp = lib + ".tmp%d" % os.getpid()
     cmd = [nvcc(), "-O3", "-std=c++17", *ARCH, "-lineinfo", "-Xcompiler", "-fPIC", "-shared",
            "-I", INCLUDE, "-o", tmp, *sources()]
+    if checked:
+        cmd.append("-DSDGR_CHECKED")
     cmd += shlex.split(os.environ.get("SDGR_NVCC_FLAGS", ""))
     if verbose:
         print(" ".join(cmd))
     subprocess.check_call(cmd)
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose=True))
+    print(build(force="--force" in sys.argv, verbose=True, checked="--checked" in sys.argv))

@@ -202,6 +202,7 @@ const char *sdgr_status_string(sdgr_status s) {
         case SDGR_ERR_CAPACITY: return "instance capacity exceeded";
         case SDGR_ERR_TIMEOUT: return "bounded device wait timed out";
         case SDGR_ERR_STATE: return "calls out of order on this workspace";
+        case SDGR_ERR_BOUNDS: return "checked build: an index left its buffer";
     }
     return "unknown status";
 }
@@ -413,7 +414,7 @@ sdgr_status sdgr_bin_sort(sdgr_ws *ws, void *stream) {
     CK(launch_scan_u64(scnt, soff, 2 * ws->VG, ws->at<unsigned long long>(L.scan64), s));
     CK(launch_check_capacity(scnt, soff, ws->VG, ws->caps.max_instances, st, s));
     CK(launch_emit(sorted_vg, soff, ws->at<uint2>(L.rectC), ws->at<uint2>(L.rectI), views, ws->V, ws->VG, ws->tiles,
-                   st, ws->at<uint32_t>(L.ik0), ws->at<uint32_t>(L.iv0), ws->sms, s));
+                   st, ws->caps.max_instances, ws->at<uint32_t>(L.ik0), ws->at<uint32_t>(L.iv0), ws->sms, s));
     int final1 = 0;
     CK(launch_inst_sort(st, soff, scnt, ws->VG, views, ws->V, ws->tiles, ws->caps.max_instances, ws->key_bits,
                         ws->at<SegDev>(L.segs), ws->at<uint32_t>(L.ik0), ws->at<uint32_t>(L.iv0),
@@ -423,7 +424,7 @@ sdgr_status sdgr_bin_sort(sdgr_ws *ws, void *stream) {
     ws->inst_vals = ws->at<uint32_t>(final1 ? L.iv1 : L.iv0);
     uint2 *ranges = ws->at<uint2>(L.ranges);
     CK(cudaMemsetAsync(ranges, 0, (size_t)2 * ws->tiles * sizeof(uint2), s));
-    CK(launch_ranges(ws->inst_keys, st, ws->caps.max_instances, ranges, ws->sms, s));
+    CK(launch_ranges(ws->inst_keys, st, ws->caps.max_instances, 2 * (int64_t)ws->tiles, ranges, ws->sms, s));
     CK(launch_tile_order(ranges, ws->tiles, views, ws->V, ws->at<TileWorkDev>(L.work), ws->at<int32_t>(L.order),
                          ws->at<uint32_t>(L.vhist), ws->at<uint32_t>(L.voff), ws->at<uint32_t>(L.vt),
                          ws->at<uint32_t>(L.vbase), ws->at<uint32_t>(L.vscan), ws->sms, s));
@@ -444,6 +445,7 @@ static cudaError_t raster_sched(sdgr_ws *ws, int kernel, cudaStream_t s, TileSch
     sc.plane = plane;
     sc.slot = kernel;
     sc.persistent_grid = 0;
+    sc.ntiles = ws->tiles;
     if (!(ws->sched & SDGR_SCHED_ORDERED)) return cudaSuccess;
     sc.order = ws->at<int32_t>(ws->L.order) + (size_t)plane * ws->tiles;
     if (ws->sched & SDGR_SCHED_PERSISTENT) {

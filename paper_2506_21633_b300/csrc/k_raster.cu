@@ -245,14 +245,17 @@ __device__ __forceinline__ float alpha_of(float o, float e) {
 
 // Runs body(tile) for the tiles this CTA owns under the launch's schedule.
 template <typename F>
-__device__ __forceinline__ void for_tiles(const TileSched &sc, F &&body) {
+__device__ __forceinline__ void for_tiles(const TileSched &sc, const StatusDev *st, F &&body) {
     if (!sc.order) {
         body((int)blockIdx.x);
         return;
     }
     const int n = sc.work->count[sc.plane];
     if (sc.persistent_grid == 0) {
-        if ((int)blockIdx.x < n) body(sc.order[blockIdx.x]);
+        if ((int)blockIdx.x < n) {
+            const int tile = sc.order[blockIdx.x];
+            if (SDGR_IN_BOUNDS(st, (unsigned)tile < (unsigned)sc.ntiles)) body(tile);
+        }
         return;
     }
     __shared__ int s_item;
@@ -262,8 +265,18 @@ __device__ __forceinline__ void for_tiles(const TileSched &sc, F &&body) {
         const int item = s_item;
         __syncthreads();  // every thread has read s_item before it is overwritten
         if (item >= n) break;
-        body(sc.order[item]);
+        const int tile = sc.order[item];
+        if (SDGR_IN_BOUNDS(st, (unsigned)tile < (unsigned)sc.ntiles)) body(tile);
     }
+    (void)st;
+}
+
+// A staged list entry must be a (view, Gaussian) slot of the tile's view.
+__device__ __forceinline__ bool vg_ok(const StatusDev *st, const ViewDev &vd, uint32_t vg) {
+    (void)st;
+    (void)vd;
+    (void)vg;
+    return SDGR_IN_BOUNDS(st, (uint64_t)((int64_t)vg - vd.vg_off) < (uint64_t)(uint32_t)vd.N);
 }
 
 // Stage one computation-plane record: exponent coefficients, block set and
@@ -290,7 +303,7 @@ __device__ __forceinline__ void stage_comp(const CompRec *__restrict__ comp, uin
 // ---------------------------------------------------------------------------
 template <int AM>
 __device__ __forceinline__ void
-intensity_fwd_tile(const int tile, const uint2 *__restrict__ ranges, const uint32_t *__restrict__ vals,
+intensity_fwd_tile(const int tile, const StatusDev *st, const uint2 *__restrict__ ranges, const uint32_t *__restrict__ vals,
                    const CompRec *__restrict__ comp, const ViewDev *__restrict__ views, int V, float cut, float Tfloor,
                    float *__restrict__ A, float *__restrict__ Tstop, int32_t *__restrict__ last) {
     __shared__ float4 sP[BATCH];  // (qa, qb, qc, l1)
@@ -315,8 +328,8 @@ intensity_fwd_tile(const int tile, const uint2 *__restrict__ ranges, const uint3
             const uint32_t vg = vnext;
             float4 P;
             float2 Q, uv, oP;
-            uint32_t m;
-            stage_comp(comp, vg, c, cutm, P, Q, m, uv, oP);
+            uint32_t m = 0;
+            if (vg_ok(st, views[c.v], vg)) stage_comp(comp, vg, c, cutm, P, Q, m, uv, oP);
             sP[t] = P;
             sQ[t] = make_float4(Q.x, Q.y, oP.x, 0.f);
             sM[t] = m;
@@ -376,8 +389,8 @@ k_intensity_fwd(const uint2 *__restrict__ ranges, const uint32_t *__restrict__ v
                 const ViewDev *__restrict__ views, int V, float cut, float Tfloor, const StatusDev *st,
                 float *__restrict__ A, float *__restrict__ Tstop, int32_t *__restrict__ last, const TileSched sc) {
     if (st->code != SDGR_OK) return;
-    for_tiles(sc, [&](int tile) {
-        intensity_fwd_tile<AM>(tile, ranges, vals, comp, views, V, cut, Tfloor, A, Tstop, last);
+    for_tiles(sc, st, [&](int tile) {
+        intensity_fwd_tile<AM>(tile, st, ranges, vals, comp, views, V, cut, Tfloor, A, Tstop, last);
     });
 }
 
@@ -417,7 +430,7 @@ __device__ __forceinline__ void stage_img(const ImgRec *__restrict__ img, uint32
 // Each pixel gathers over its warp's hit list; no reduction is needed.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void
-splat_fwd_tile(const int tile, const uint2 *__restrict__ rangesI, const uint32_t *__restrict__ vals,
+splat_fwd_tile(const int tile, const StatusDev *st, const uint2 *__restrict__ rangesI, const uint32_t *__restrict__ vals,
                const ImgRec *__restrict__ img, const CompRec *__restrict__ comp, const float *__restrict__ A,
                const ViewDev *__restrict__ views, int V, float cut, bool ok, float *__restrict__ images) {
     __shared__ float4 sP[BATCH];  // (qa, qb, qc, l1)
@@ -438,11 +451,15 @@ splat_fwd_tile(const int tile, const uint2 *__restrict__ rangesI, const uint32_t
             float2 uv, Q;
             float cn;
             uint32_t m;
-            stage_img(img, vg, c, cutm, G, uv, cn, m);
-            poly_coeffs(uv.x, uv.y, G.x, G.y, G.z, P, Q);
-            sP[t] = P;
-            sQ[t] = make_float4(Q.x, Q.y, cn * comp[vg].P * A[vg], 0.f);
-            sM[t] = m;
+            if (vg_ok(st, views[c.v], vg)) {
+                stage_img(img, vg, c, cutm, G, uv, cn, m);
+                poly_coeffs(uv.x, uv.y, G.x, G.y, G.z, P, Q);
+                sP[t] = P;
+                sQ[t] = make_float4(Q.x, Q.y, cn * comp[vg].P * A[vg], 0.f);
+                sM[t] = m;
+            } else {
+                sM[t] = 0;  // checked build: an entry of another view stays inert
+            }
         }
         if (base + BATCH + t < r.y) vnext = vals[base + BATCH + t];
         __syncthreads();
@@ -475,7 +492,7 @@ k_splat_fwd(const uint2 *__restrict__ rangesI, const uint32_t *__restrict__ vals
             float cut, const StatusDev *st, float *__restrict__ images, const TileSched sc) {
     const bool ok = st->code == SDGR_OK;
     if (!ok && sc.order) return;
-    for_tiles(sc, [&](int tile) { splat_fwd_tile(tile, rangesI, vals, img, comp, A, views, V, cut, ok, images); });
+    for_tiles(sc, st, [&](int tile) { splat_fwd_tile(tile, st, rangesI, vals, img, comp, A, views, V, cut, ok, images); });
 }
 
 cudaError_t launch_splat_fwd(const uint2 *rangesI, const uint32_t *vals, const ImgRec *img, const CompRec *comp,
@@ -498,7 +515,7 @@ cudaError_t launch_splat_fwd(const uint2 *rangesI, const uint32_t *vals, const I
 // the eight partial moments.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void
-splat_bwd_tile(const int tile, const uint2 *__restrict__ rangesI, const uint32_t *__restrict__ vals,
+splat_bwd_tile(const int tile, const StatusDev *st, const uint2 *__restrict__ rangesI, const uint32_t *__restrict__ vals,
                const ImgRec *__restrict__ img, const float *__restrict__ dLdS, const ViewDev *__restrict__ views, int V,
                float cut, float4 *__restrict__ accI) {
     __shared__ float4 sG[SBATCH];  // (qa, qb, qc, -)
@@ -530,8 +547,8 @@ splat_bwd_tile(const int tile, const uint2 *__restrict__ rangesI, const uint32_t
                 float4 G;
                 float2 uv;
                 float cn;
-                uint32_t m;
-                stage_img(img, vg, c, cutm, G, uv, cn, m);
+                uint32_t m = 0;
+                if (vg_ok(st, views[c.v], vg)) stage_img(img, vg, c, cutm, G, uv, cn, m);
                 sG[k] = G;
                 sU[k] = uv;
                 sM[k] = m;
@@ -590,7 +607,7 @@ k_splat_bwd(const uint2 *__restrict__ rangesI, const uint32_t *__restrict__ vals
             const float *__restrict__ dLdS, const ViewDev *__restrict__ views, int V, float cut, const StatusDev *st,
             float4 *__restrict__ accI, const TileSched sc) {
     if (st->code != SDGR_OK) return;
-    for_tiles(sc, [&](int tile) { splat_bwd_tile(tile, rangesI, vals, img, dLdS, views, V, cut, accI); });
+    for_tiles(sc, st, [&](int tile) { splat_bwd_tile(tile, st, rangesI, vals, img, dLdS, views, V, cut, accI); });
 }
 
 cudaError_t launch_splat_bwd(const uint2 *rangesI, const uint32_t *vals, const ImgRec *img, const float *dLdS,
@@ -617,7 +634,7 @@ cudaError_t launch_splat_bwd(const uint2 *rangesI, const uint32_t *vals, const I
 // ---------------------------------------------------------------------------
 template <int AM>
 __device__ __forceinline__ void
-intensity_bwd_tile(const int tile, const uint2 *__restrict__ ranges, const uint32_t *__restrict__ vals,
+intensity_bwd_tile(const int tile, const StatusDev *st, const uint2 *__restrict__ ranges, const uint32_t *__restrict__ vals,
                    const CompRec *__restrict__ comp, const ImgRec *__restrict__ img, const float4 *__restrict__ accI,
                    const float *__restrict__ Tstop, const int32_t *__restrict__ last,
                    const ViewDev *__restrict__ views, int V, float cut, float4 *__restrict__ accC) {
@@ -655,9 +672,12 @@ intensity_bwd_tile(const int tile, const uint2 *__restrict__ ranges, const uint3
             const uint32_t vg = vnext;
             float4 P;
             float2 Q, uv, oP;
-            uint32_t m;
-            stage_comp(comp, vg, c, cutm, P, Q, m, uv, oP);
-            const float dLdI = accI[2 * (size_t)vg].x * img[vg].cn;
+            uint32_t m = 0;
+            float dLdI = 0.f;
+            if (vg_ok(st, views[c.v], vg)) {
+                stage_comp(comp, vg, c, cutm, P, Q, m, uv, oP);
+                dLdI = accI[2 * (size_t)vg].x * img[vg].cn;
+            }
             sP[t] = P;
             sQ[t] = make_float4(Q.x, Q.y, oP.x, dLdI * oP.y);
             sU[t] = uv;
@@ -748,8 +768,8 @@ k_intensity_bwd(const uint2 *__restrict__ ranges, const uint32_t *__restrict__ v
                 const int32_t *__restrict__ last, const ViewDev *__restrict__ views, int V, float cut,
                 const StatusDev *st, float4 *__restrict__ accC, const TileSched sc) {
     if (st->code != SDGR_OK) return;
-    for_tiles(sc, [&](int tile) {
-        intensity_bwd_tile<AM>(tile, ranges, vals, comp, img, accI, Tstop, last, views, V, cut, accC);
+    for_tiles(sc, st, [&](int tile) {
+        intensity_bwd_tile<AM>(tile, st, ranges, vals, comp, img, accI, Tstop, last, views, V, cut, accC);
     });
 }
 

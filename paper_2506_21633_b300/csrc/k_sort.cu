@@ -428,21 +428,27 @@ cudaError_t launch_check_capacity(const unsigned long long *scnt, const unsigned
 }
 
 __device__ __forceinline__ void emit_rect(uint2 rect, unsigned long long base, uint32_t tile_base, int tiles_x,
-                                          uint32_t vg, uint32_t *keys, uint32_t *vals) {
+                                          uint32_t vg, uint32_t *keys, uint32_t *vals, const StatusDev *st,
+                                          int64_t cap) {
     const int tx0 = rect.x & 0xffff, tx1 = rect.x >> 16, ty0 = rect.y & 0xffff, ty1 = rect.y >> 16;
     unsigned long long p = base;
     for (int ty = ty0; ty <= ty1; ++ty)
         for (int tx = tx0; tx <= tx1; ++tx) {
-            keys[p] = tile_base + (uint32_t)(ty * tiles_x + tx);
-            vals[p] = vg;
+            if (SDGR_IN_BOUNDS(st, p < (unsigned long long)cap)) {
+                keys[p] = tile_base + (uint32_t)(ty * tiles_x + tx);
+                vals[p] = vg;
+            }
             ++p;
         }
+    (void)st;
+    (void)cap;
 }
 
 __global__ void __launch_bounds__(256)
 k_emit(const uint32_t *__restrict__ sorted_vg, const unsigned long long *__restrict__ soff,
        const uint2 *__restrict__ rectC, const uint2 *__restrict__ rectI, const ViewDev *__restrict__ views, int V,
-       int64_t VG, int total_tiles, const StatusDev *st, uint32_t *__restrict__ keys, uint32_t *__restrict__ vals) {
+       int64_t VG, int total_tiles, const StatusDev *st, int64_t cap, uint32_t *__restrict__ keys,
+       uint32_t *__restrict__ vals) {
     if (st->code != SDGR_OK) return;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < VG; k += stride) {
@@ -450,41 +456,45 @@ k_emit(const uint32_t *__restrict__ sorted_vg, const unsigned long long *__restr
         const int v = view_of_vg(views, V, k);
         const ViewDev &vd = views[v];
         const uint2 rc = rectC[vg];
-        if (rc.x != 0xffffffffu) emit_rect(rc, soff[k], (uint32_t)vd.tile_off, vd.tiles_x, vg, keys, vals);
+        if (rc.x != 0xffffffffu) emit_rect(rc, soff[k], (uint32_t)vd.tile_off, vd.tiles_x, vg, keys, vals, st, cap);
         const uint2 ri = rectI[vg];
         if (ri.x != 0xffffffffu)
-            emit_rect(ri, soff[VG + k], (uint32_t)(total_tiles + vd.tile_off), vd.tiles_x, vg, keys, vals);
+            emit_rect(ri, soff[VG + k], (uint32_t)(total_tiles + vd.tile_off), vd.tiles_x, vg, keys, vals, st, cap);
     }
 }
 
 cudaError_t launch_emit(const uint32_t *sorted_vg, const unsigned long long *soff, const uint2 *rectC,
                         const uint2 *rectI, const ViewDev *views, int V, int64_t VG, int total_tiles,
-                        const StatusDev *st, uint32_t *keys, uint32_t *vals, int sms, cudaStream_t s) {
+                        const StatusDev *st, int64_t cap, uint32_t *keys, uint32_t *vals, int sms, cudaStream_t s) {
     if (VG <= 0) return cudaSuccess;
     int64_t blocks = (VG + 255) / 256;
     if (blocks > (int64_t)sms * 8) blocks = (int64_t)sms * 8;
-    k_emit<<<(unsigned)blocks, 256, 0, s>>>(sorted_vg, soff, rectC, rectI, views, V, VG, total_tiles, st, keys, vals);
+    k_emit<<<(unsigned)blocks, 256, 0, s>>>(sorted_vg, soff, rectC, rectI, views, V, VG, total_tiles, st, cap, keys,
+                                            vals);
     note_launch();
     return cudaGetLastError();
 }
 
-__global__ void k_ranges(const uint32_t *__restrict__ keys, const StatusDev *st, int64_t cap, uint2 *ranges) {
+__global__ void k_ranges(const uint32_t *__restrict__ keys, StatusDev *st, int64_t cap, int64_t nranges,
+                         uint2 *ranges) {
     int64_t n = st->code == SDGR_OK ? st->n_inst : 0;
     if (n > cap) n = cap;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
         const uint32_t k = keys[i];
+        if (!SDGR_IN_BOUNDS(st, (int64_t)k < nranges)) continue;
+        (void)nranges;
         if (i == 0 || keys[i - 1] != k) ranges[k].x = (uint32_t)i;
         if (i == n - 1 || keys[i + 1] != k) ranges[k].y = (uint32_t)(i + 1);
     }
 }
 
-cudaError_t launch_ranges(const uint32_t *keys, const StatusDev *st, int64_t cap, uint2 *ranges, int sms,
+cudaError_t launch_ranges(const uint32_t *keys, StatusDev *st, int64_t cap, int64_t nranges, uint2 *ranges, int sms,
                           cudaStream_t s) {
     int64_t blocks = (cap + 255) / 256;
     if (blocks > (int64_t)sms * 16) blocks = (int64_t)sms * 16;
     if (blocks < 1) blocks = 1;
-    k_ranges<<<(unsigned)blocks, 256, 0, s>>>(keys, st, cap, ranges);
+    k_ranges<<<(unsigned)blocks, 256, 0, s>>>(keys, st, cap, nranges, ranges);
     note_launch();
     return cudaGetLastError();
 }

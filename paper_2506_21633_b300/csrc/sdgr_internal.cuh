@@ -18,6 +18,16 @@ constexpr int SORT_THREADS = 256;
 constexpr int SCAN_IPB = 4096;   // items per scan block
 constexpr int SCAN_THREADS = 256;
 
+// Checked build (-DSDGR_CHECKED, libsdgr_checked.so): the stages that produce
+// indices verify each one against its buffer; a bad index records
+// SDGR_ERR_BOUNDS in the status word (the first error wins) and the access is
+// skipped.  Nothing traps.  In the default build the checks compile away.
+#ifdef SDGR_CHECKED
+#define SDGR_IN_BOUNDS(st, cond) ::sdgr::check_bounds((st), (cond))
+#else
+#define SDGR_IN_BOUNDS(st, cond) true
+#endif
+
 // log2(e)
 constexpr float LOG2E = 1.4426950408889634f;
 
@@ -83,10 +93,18 @@ struct TileSched {
     int plane;              // 0 computation, 1 imaging
     int slot;               // item counter used by this launch
     int persistent_grid;    // > 0: persistent launch with this many CTAs
+    int ntiles;             // tiles of the plane (bound of every work-list entry)
 };
 
 // One segment of a segmented radix sort: items [start, start + len), digits
 // taken from (key - key_base); blk_start = first block of the segment.
+#ifdef SDGR_CHECKED
+__device__ __forceinline__ bool check_bounds(const StatusDev *st, bool ok) {
+    if (!ok) atomicCAS(const_cast<int32_t *>(&st->code), (int32_t)SDGR_OK, (int32_t)SDGR_ERR_BOUNDS);
+    return ok;
+}
+#endif
+
 struct alignas(16) SegDev {
     uint32_t start, len, key_base, blk_start;
 };
@@ -193,13 +211,13 @@ cudaError_t launch_check_capacity(const unsigned long long *scnt, const unsigned
                                   int64_t cap, StatusDev *st, cudaStream_t s);
 cudaError_t launch_emit(const uint32_t *sorted_vg, const unsigned long long *soff, const uint2 *rectC,
                         const uint2 *rectI, const ViewDev *views, int V, int64_t VG, int total_tiles,
-                        const StatusDev *st, uint32_t *keys, uint32_t *vals, int sms, cudaStream_t s);
+                        const StatusDev *st, int64_t cap, uint32_t *keys, uint32_t *vals, int sms, cudaStream_t s);
 // vhist, voff: 2 * V * 32 entries; vt, vbase: 2 * V; scratch:
 // scan_scratch_elems(2 * V) entries.
 cudaError_t launch_tile_order(const uint2 *ranges, int tiles, const ViewDev *views, int V, TileWorkDev *work,
                               int32_t *order, uint32_t *vhist, uint32_t *voff, uint32_t *vt, uint32_t *vbase,
                               uint32_t *scratch, int sms, cudaStream_t s);
-cudaError_t launch_ranges(const uint32_t *keys, const StatusDev *st, int64_t cap, uint2 *ranges, int sms,
+cudaError_t launch_ranges(const uint32_t *keys, StatusDev *st, int64_t cap, int64_t nranges, uint2 *ranges, int sms,
                           cudaStream_t s);
 
 // raster passes

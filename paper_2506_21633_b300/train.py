@@ -180,6 +180,27 @@ class Trainer:
         self._alloc(new_n)
         self.densify_events.append((self.t, n, new_n, thr))
 
+    def state_dict(self):
+        """Everything a resumed run needs: parameters, SH coefficients, Adam
+        moments of both, the iteration count and the densification threshold."""
+        torch.cuda.synchronize(self.dev)
+        cpu = lambda x: x.detach().cpu().clone()  # noqa: E731
+        return {"params": cpu(self.p), "sh": cpu(self.sh), "m": cpu(self.m), "v": cpu(self.v), "msh": cpu(self.msh),
+                "vsh": cpu(self.vsh), "t": self.t, "thr": self.thr, "lr": list(self.lr), "sh_lr": self.sh_lr}
+
+    def load_state_dict(self, state):
+        n = int(state["params"].shape[0])
+        self.p = state["params"].to(self.dev).contiguous()
+        self._alloc(n, keep=False)
+        with torch.no_grad():
+            self.sh.copy_(state["sh"])
+            self.m.copy_(state["m"])
+            self.v.copy_(state["v"])
+            self.msh.copy_(state["msh"])
+            self.vsh.copy_(state["vsh"])
+        self.t, self.thr = int(state["t"]), state["thr"]
+        self.lr, self.sh_lr = list(state["lr"]), float(state["sh_lr"])
+
     def render(self, views):
         """Images of `views` (list of [NR, NA] NumPy arrays) with the current
         parameters and SH degree."""
