@@ -310,20 +310,20 @@ intensity_fwd_tile(const int tile, const StatusDev *st, const uint2 *__restrict_
     __shared__ float4 sQ[BATCH];  // (l2, c0, o, -)
     __shared__ uint32_t sM[BATCH];
     __shared__ uint32_t sid[BATCH];
-    __shared__ uint8_t sperm[BATCH];
-    __shared__ __align__(16) float W[SUB * WSTRIDE];
-    __shared__ __align__(16) float zero4[4];
-    const int t = threadIdx.x, warp = t >> 5;
-    if (t < 4) zero4[t] = 0.f;
+    __shared__ unsigned long long sAcc[BATCH];  // sum of alpha T over the tile's rays, in units of 2^-26
+    const int t = threadIdx.x, lane = t & 31;
     const TileCtx c = tile_ctx(views, V, tile);
     const LaneXY L = lane_xy();
     const uint2 r = ranges[tile];
     const float cutm = cut_margin(cut);
     float T = c.inside ? 1.f : 0.f, Tprev = 1.f;  // a ray outside the image takes no pair
     int32_t lastj = 0;
+    int nb = 0;  // Gaussians staged in the current batch
     uint32_t vnext = r.x + t < r.y ? vals[r.x + t] : 0u;  // next batch's list entry, loaded one batch ahead
     for (uint32_t base = r.x; base < r.y; base += BATCH) {
         if (__syncthreads_count(T < Tfloor) == (int)blockDim.x) break;
+        // the previous batch's sums: one global atomic per (tile, Gaussian)
+        if (t < nb && sAcc[t] != 0ull) atomicAdd(&A[sid[t]], __ull2float_rn(sAcc[t]) * (1.f / 67108864.f));
         if (base + t < r.y) {
             const uint32_t vg = vnext;
             float4 P;
@@ -335,13 +335,12 @@ intensity_fwd_tile(const int tile, const StatusDev *st, const uint2 *__restrict_
             sM[t] = m;
             sid[t] = vg;
         }
+        sAcc[t] = 0ull;
         if (base + BATCH + t < r.y) vnext = vals[base + BATCH + t];
         __syncthreads();
-        const int nb = min(BATCH, (int)(r.y - base));
-        if (warp * SUB < nb) order_by_blocks(sM, warp * SUB, min(SUB, nb - warp * SUB), sperm + warp * SUB);
-        for (int sub = 0; sub < nb; sub += SUB) {
-            const int ns = min(SUB, nb - sub);
-            uint32_t hm = warp_hits(sM, sub, ns);
+        nb = min(BATCH, (int)(r.y - base));
+        for (int sub = 0; sub < nb; sub += 32) {
+            uint32_t hm = warp_hits(sM, sub, min(32, nb - sub));
             const int32_t kb = (int32_t)(base + sub + 1);
             while (hm) {
                 const int jj = __ffs(hm) - 1;
@@ -351,32 +350,19 @@ intensity_fwd_tile(const int tile, const StatusDev *st, const uint2 *__restrict_
                 const float q = poly_q(P, Q.x, Q.y, L);
                 const bool in = (q >= cut) & (T >= Tfloor);
                 const float alpha = alpha_of<AM>(Q.z, in ? ex2_approx(q) : 0.f);
-                W[jj * WSTRIDE + c.toff] = __fmul_rn(alpha, T);
+                // the warp's 32 rays summed in fixed point (0 <= alpha T <= 1, so
+                // 32 lanes of 2^26 fit 32 bits): one redux instead of a table
+                const uint32_t fx = __float2uint_rn(__fmul_rn(alpha, T) * 67108864.f);
+                const uint32_t ws = __reduce_add_sync(0xffffffffu, fx);
+                if (lane == 0 && ws != 0u) atomicAdd(&sAcc[sub + jj], (unsigned long long)ws);
                 Tprev = in ? T : Tprev;
                 lastj = in ? kb + jj : lastj;
                 T = __fmul_rn(T, __fsub_rn(1.f, alpha));
             }
-            __syncthreads();
-            const int j = sperm[sub + (t >> 3)], cc = t & 7;
-            uint32_t mb = j < ns ? sM[sub + j] : 0u;
-            const float *wr = W + j * WSTRIDE + 4 * cc;
-            float s = 0.f;
-            // as many rounds as the warp's largest block count; a group out of
-            // blocks reads a zero float4
-            const int rounds = __reduce_max_sync(0xffffffffu, __popc(mb));
-            for (int i = 0; i < rounds; ++i) {
-                const float *src = mb ? wr + 32 * (__ffs(mb) - 1) : zero4;
-                mb &= mb - 1;
-                const float4 w4 = *reinterpret_cast<const float4 *>(src);
-                s += (w4.x + w4.y) + (w4.z + w4.w);
-            }
-            s += __shfl_xor_sync(0xffffffffu, s, 1);
-            s += __shfl_xor_sync(0xffffffffu, s, 2);
-            s += __shfl_xor_sync(0xffffffffu, s, 4);
-            if (cc == 0 && j < ns && s != 0.f) atomicAdd(&A[sid[sub + j]], s);
-            __syncthreads();
         }
     }
+    __syncthreads();
+    if (t < nb && sAcc[t] != 0ull) atomicAdd(&A[sid[t]], __ull2float_rn(sAcc[t]) * (1.f / 67108864.f));
     if (c.inside) {
         Tstop[c.pix] = Tprev;
         last[c.pix] = lastj;
