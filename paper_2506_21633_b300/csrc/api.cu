@@ -413,7 +413,7 @@ sdgr_status sdgr_bin_sort(sdgr_ws *ws, void *stream) {
                             s));
     CK(launch_scan_u64(scnt, soff, 2 * ws->VG, ws->at<unsigned long long>(L.scan64), s));
     CK(launch_check_capacity(scnt, soff, ws->VG, ws->caps.max_instances, st, s));
-    CK(launch_emit(sorted_vg, soff, ws->at<uint2>(L.rectC), ws->at<uint2>(L.rectI), views, ws->V, ws->VG, ws->tiles,
+    CK(launch_emit(sorted_vg, soff, scnt, ws->at<uint2>(L.rectC), ws->at<uint2>(L.rectI), views, ws->V, ws->VG, ws->tiles,
                    st, ws->caps.max_instances, ws->at<uint32_t>(L.ik0), ws->at<uint32_t>(L.iv0), ws->sms, s));
     int final1 = 0;
     CK(launch_inst_sort(st, soff, scnt, ws->VG, views, ws->V, ws->tiles, ws->caps.max_instances, ws->key_bits,

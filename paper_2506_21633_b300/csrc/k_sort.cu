@@ -427,50 +427,80 @@ cudaError_t launch_check_capacity(const unsigned long long *scnt, const unsigned
     return cudaGetLastError();
 }
 
-__device__ __forceinline__ void emit_rect(uint2 rect, unsigned long long base, uint32_t tile_base, int tiles_x,
-                                          uint32_t vg, uint32_t *keys, uint32_t *vals, const StatusDev *st,
-                                          int64_t cap) {
-    const int tx0 = rect.x & 0xffff, tx1 = rect.x >> 16, ty0 = rect.y & 0xffff, ty1 = rect.y >> 16;
-    unsigned long long p = base;
-    for (int ty = ty0; ty <= ty1; ++ty)
-        for (int tx = tx0; tx <= tx1; ++tx) {
-            if (SDGR_IN_BOUNDS(st, p < (unsigned long long)cap)) {
-                keys[p] = tile_base + (uint32_t)(ty * tiles_x + tx);
-                vals[p] = vg;
-            }
-            ++p;
+// Instance emission, warp-cooperative: the 32 depth-sorted slots of a warp
+// own one contiguous output range per plane (the counts' exclusive scan), and
+// the warp writes that range with consecutive lanes on consecutive items.
+// Item i belongs to the last lane whose range starts at or before i (five
+// shuffle steps); inside a Gaussian's tile rectangle the items run row by row.
+__global__ void __launch_bounds__(256)
+k_emit(const uint32_t *__restrict__ sorted_vg, const unsigned long long *__restrict__ soff,
+       const unsigned long long *__restrict__ scnt, const uint2 *__restrict__ rectC, const uint2 *__restrict__ rectI,
+       const ViewDev *__restrict__ views, int V, int64_t VG, int total_tiles, const StatusDev *st, int64_t cap,
+       uint32_t *__restrict__ keys, uint32_t *__restrict__ vals) {
+    if (st->code != SDGR_OK) return;
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t k0 = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32; k0 < VG; k0 += nwarps * 32) {
+        const int64_t k = k0 + lane;
+        const bool valid = k < VG;
+        uint32_t vg = 0, tbase = 0;
+        int tiles_x = 1;
+        if (valid) {
+            vg = sorted_vg[k];
+            const ViewDev &vd = views[view_of_vg(views, V, k)];
+            tiles_x = vd.tiles_x;
+            tbase = (uint32_t)vd.tile_off;
         }
-    (void)st;
+#pragma unroll
+        for (int p = 0; p < 2; ++p) {
+            const uint2 rect = valid ? (p ? rectI[vg] : rectC[vg]) : make_uint2(0u, 0u);
+            const unsigned long long off = valid ? soff[(int64_t)p * VG + k] : 0ull;
+            const uint32_t cnt = valid ? (uint32_t)scnt[(int64_t)p * VG + k] : 0u;
+            const unsigned long long off0 = __shfl_sync(full, off, 0);
+            // start of this lane's range relative to lane 0 (an invalid lane
+            // gets a start no item reaches)
+            const uint32_t rel = valid ? (uint32_t)(off - off0) : 0xffffffffu;
+            const uint32_t total = __reduce_max_sync(full, valid ? rel + cnt : 0u);
+            const uint32_t key_base = (uint32_t)(p ? total_tiles : 0) + tbase;
+            for (uint32_t i0 = 0; i0 < total; i0 += 32) {
+                const uint32_t i = i0 + (uint32_t)lane;
+                int o = 0;
+#pragma unroll
+                for (int step = 16; step > 0; step >>= 1) {
+                    const uint32_t r2 = __shfl_sync(full, rel, (o + step) & 31);
+                    if (o + step < 32 && r2 <= i) o += step;
+                }
+                const uint32_t o_rel = __shfl_sync(full, rel, o);
+                const uint32_t o_rx = __shfl_sync(full, rect.x, o), o_ry = __shfl_sync(full, rect.y, o);
+                const uint32_t o_kb = __shfl_sync(full, key_base, o), o_vg = __shfl_sync(full, vg, o);
+                const int o_tx = __shfl_sync(full, tiles_x, o);
+                if (i < total) {
+                    const uint32_t d = i - o_rel;
+                    const uint32_t tx0 = o_rx & 0xffffu, w = (o_rx >> 16) - tx0 + 1u, ty0 = o_ry & 0xffffu;
+                    const uint32_t q = d / w;
+                    const uint32_t tx = tx0 + (d - q * w);
+                    const unsigned long long pos = off0 + i;
+                    if (SDGR_IN_BOUNDS(st, pos < (unsigned long long)cap)) {
+                        keys[pos] = o_kb + (ty0 + q) * (uint32_t)o_tx + tx;
+                        vals[pos] = o_vg;
+                    }
+                }
+            }
+        }
+    }
     (void)cap;
 }
 
-__global__ void __launch_bounds__(256)
-k_emit(const uint32_t *__restrict__ sorted_vg, const unsigned long long *__restrict__ soff,
-       const uint2 *__restrict__ rectC, const uint2 *__restrict__ rectI, const ViewDev *__restrict__ views, int V,
-       int64_t VG, int total_tiles, const StatusDev *st, int64_t cap, uint32_t *__restrict__ keys,
-       uint32_t *__restrict__ vals) {
-    if (st->code != SDGR_OK) return;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < VG; k += stride) {
-        const uint32_t vg = sorted_vg[k];
-        const int v = view_of_vg(views, V, k);
-        const ViewDev &vd = views[v];
-        const uint2 rc = rectC[vg];
-        if (rc.x != 0xffffffffu) emit_rect(rc, soff[k], (uint32_t)vd.tile_off, vd.tiles_x, vg, keys, vals, st, cap);
-        const uint2 ri = rectI[vg];
-        if (ri.x != 0xffffffffu)
-            emit_rect(ri, soff[VG + k], (uint32_t)(total_tiles + vd.tile_off), vd.tiles_x, vg, keys, vals, st, cap);
-    }
-}
-
-cudaError_t launch_emit(const uint32_t *sorted_vg, const unsigned long long *soff, const uint2 *rectC,
-                        const uint2 *rectI, const ViewDev *views, int V, int64_t VG, int total_tiles,
-                        const StatusDev *st, int64_t cap, uint32_t *keys, uint32_t *vals, int sms, cudaStream_t s) {
+cudaError_t launch_emit(const uint32_t *sorted_vg, const unsigned long long *soff, const unsigned long long *scnt,
+                        const uint2 *rectC, const uint2 *rectI, const ViewDev *views, int V, int64_t VG,
+                        int total_tiles, const StatusDev *st, int64_t cap, uint32_t *keys, uint32_t *vals, int sms,
+                        cudaStream_t s) {
     if (VG <= 0) return cudaSuccess;
     int64_t blocks = (VG + 255) / 256;
     if (blocks > (int64_t)sms * 8) blocks = (int64_t)sms * 8;
-    k_emit<<<(unsigned)blocks, 256, 0, s>>>(sorted_vg, soff, rectC, rectI, views, V, VG, total_tiles, st, cap, keys,
-                                            vals);
+    k_emit<<<(unsigned)blocks, 256, 0, s>>>(sorted_vg, soff, scnt, rectC, rectI, views, V, VG, total_tiles, st, cap,
+                                            keys, vals);
     note_launch();
     return cudaGetLastError();
 }

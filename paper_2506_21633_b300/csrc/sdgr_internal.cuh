@@ -209,9 +209,10 @@ cudaError_t launch_gather_counts(const uint32_t *sorted_vg, const uint32_t *cntC
                                  unsigned long long *scnt, int sms, cudaStream_t s);
 cudaError_t launch_check_capacity(const unsigned long long *scnt, const unsigned long long *soff, int64_t VG,
                                   int64_t cap, StatusDev *st, cudaStream_t s);
-cudaError_t launch_emit(const uint32_t *sorted_vg, const unsigned long long *soff, const uint2 *rectC,
-                        const uint2 *rectI, const ViewDev *views, int V, int64_t VG, int total_tiles,
-                        const StatusDev *st, int64_t cap, uint32_t *keys, uint32_t *vals, int sms, cudaStream_t s);
+cudaError_t launch_emit(const uint32_t *sorted_vg, const unsigned long long *soff, const unsigned long long *scnt,
+                        const uint2 *rectC, const uint2 *rectI, const ViewDev *views, int V, int64_t VG,
+                        int total_tiles, const StatusDev *st, int64_t cap, uint32_t *keys, uint32_t *vals, int sms,
+                        cudaStream_t s);
 // vhist, voff: 2 * V * 32 entries; vt, vbase: 2 * V; scratch:
 // scan_scratch_elems(2 * V) entries.
 cudaError_t launch_tile_order(const uint2 *ranges, int tiles, const ViewDev *views, int V, TileWorkDev *work,
