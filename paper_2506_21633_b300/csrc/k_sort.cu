@@ -162,7 +162,8 @@ struct BlockSeg {
     int64_t hbase;
 };
 
-__device__ __forceinline__ bool block_seg(const SegDev *segs, int nseg, int b, BlockSeg &o) {
+// R: digit values of the pass (the histogram has R entries per block).
+__device__ __forceinline__ bool block_seg(const SegDev *segs, int nseg, int b, BlockSeg &o, int R) {
     if ((uint32_t)b >= segs[nseg].blk_start) return false;  // sentinel holds the block total
     const int s = seg_of_block(segs, nseg, b);
     const SegDev sg = segs[s];
@@ -172,34 +173,41 @@ __device__ __forceinline__ bool block_seg(const SegDev *segs, int nseg, int b, B
     const uint32_t rem = sg.len - (uint32_t)o.lb * SORT_IPB;
     o.count = rem < (uint32_t)SORT_IPB ? rem : (uint32_t)SORT_IPB;
     o.key_base = sg.key_base;
-    o.hbase = (int64_t)sg.blk_start * RADIX;
+    o.hbase = (int64_t)sg.blk_start * R;
     return true;
 }
 
+// Digit width BITS (4..8) per pass: the instance sort splits its key bits
+// evenly over its passes, so no pass has more buckets than it needs (fewer
+// buckets per block = longer coalesced runs in the scatter).
+template <int BITS>
 __global__ void __launch_bounds__(SORT_THREADS)
 k_radix_hist(const uint32_t *__restrict__ keys, int shift, const SegDev *__restrict__ segs, int nseg,
              uint32_t *__restrict__ hist) {
-    __shared__ uint32_t cnt[RADIX];
+    constexpr int R = 1 << BITS;
+    __shared__ uint32_t cnt[R];
     BlockSeg bs;
-    if (!block_seg(segs, nseg, blockIdx.x, bs)) return;
-    for (int d = threadIdx.x; d < RADIX; d += blockDim.x) cnt[d] = 0;
+    if (!block_seg(segs, nseg, blockIdx.x, bs, R)) return;
+    for (int d = threadIdx.x; d < R; d += blockDim.x) cnt[d] = 0;
     __syncthreads();
     for (uint32_t i = threadIdx.x; i < bs.count; i += blockDim.x)
-        atomicAdd(&cnt[((keys[bs.start + i] - bs.key_base) >> shift) & (RADIX - 1)], 1u);
+        atomicAdd(&cnt[((keys[bs.start + i] - bs.key_base) >> shift) & (R - 1)], 1u);
     __syncthreads();
-    for (int d = threadIdx.x; d < RADIX; d += blockDim.x) hist[bs.hbase + (int64_t)d * bs.nb + bs.lb] = cnt[d];
+    for (int d = threadIdx.x; d < R; d += blockDim.x) hist[bs.hbase + (int64_t)d * bs.nb + bs.lb] = cnt[d];
 }
 
+template <int BITS>
 __global__ void __launch_bounds__(SORT_THREADS)
 k_radix_scatter(const uint32_t *__restrict__ kin, const uint32_t *__restrict__ vin, uint32_t *__restrict__ kout,
                 uint32_t *__restrict__ vout, int shift, const SegDev *__restrict__ segs, int nseg,
                 const uint32_t *__restrict__ hscan) {
+    constexpr int RADIX = 1 << BITS;  // digit values of this pass
     extern __shared__ uint32_t sm[];
     uint32_t *sk = sm, *sv = sm + SORT_IPB, *ok = sm + 2 * SORT_IPB, *ov = sm + 3 * SORT_IPB;
     __shared__ uint32_t wcnt[SORT_WARPS][RADIX];
     __shared__ uint32_t dstart[RADIX], gbase[RADIX];
     BlockSeg bs;
-    if (!block_seg(segs, nseg, blockIdx.x, bs)) return;
+    if (!block_seg(segs, nseg, blockIdx.x, bs, RADIX)) return;
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const uint32_t n = bs.count;
     for (uint32_t i = t; i < n; i += SORT_THREADS) {
@@ -326,28 +334,52 @@ static bool g_sort_attr_done = false;
 
 static cudaError_t sort_attrs() {
     if (g_sort_attr_done) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(k_radix_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SORT_SMEM);
+    const int smem = (int)SORT_SMEM;
+    cudaError_t e = cudaFuncSetAttribute(k_radix_scatter<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_radix_scatter<5>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_radix_scatter<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_radix_scatter<7>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_radix_scatter<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     g_sort_attr_done = true;
     return cudaSuccess;
 }
 
+template <int BITS>
+static cudaError_t radix_pass(int nblocks, int nseg, const SegDev *segs, int shift, const uint32_t *kin,
+                              const uint32_t *vin, uint32_t *kout, uint32_t *vout, uint32_t *hist,
+                              uint32_t *scan_scratch, cudaStream_t s) {
+    k_radix_hist<BITS><<<nblocks, SORT_THREADS, 0, s>>>(kin, shift, segs, nseg, hist);
+    note_launch();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if ((e = launch_scan_u32(hist, hist, (int64_t)nblocks * (1 << BITS), scan_scratch, s)) != cudaSuccess) return e;
+    k_radix_scatter<BITS><<<nblocks, SORT_THREADS, SORT_SMEM, s>>>(kin, vin, kout, vout, shift, segs, nseg, hist);
+    note_launch();
+    return cudaGetLastError();
+}
+
+// LSD passes over the low `bits` bits: ceil(bits / 8) passes with the bits
+// split evenly (at least 4 per pass).
 static cudaError_t radix_passes(int nblocks, int nseg, const SegDev *segs, int bits, uint32_t *k0, uint32_t *v0,
                                 uint32_t *k1, uint32_t *v1, uint32_t *hist, uint32_t *scan_scratch, int *passes_out,
                                 cudaStream_t s) {
     cudaError_t e = sort_attrs();
     if (e != cudaSuccess) return e;
     uint32_t *kin = k0, *vin = v0, *kout = k1, *vout = v1;
-    const int64_t hn = (int64_t)nblocks * RADIX;
+    const int npass = bits <= 0 ? 0 : (bits + RADIX_BITS - 1) / RADIX_BITS;
+    int digit = npass ? (bits + npass - 1) / npass : RADIX_BITS;
+    if (digit < 4) digit = 4;
     int passes = 0;
-    for (int shift = 0; shift < bits; shift += RADIX_BITS, ++passes) {
-        k_radix_hist<<<nblocks, SORT_THREADS, 0, s>>>(kin, shift, segs, nseg, hist);
-        note_launch();
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        if ((e = launch_scan_u32(hist, hist, hn, scan_scratch, s)) != cudaSuccess) return e;
-        k_radix_scatter<<<nblocks, SORT_THREADS, SORT_SMEM, s>>>(kin, vin, kout, vout, shift, segs, nseg, hist);
-        note_launch();
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    for (int shift = 0; passes < npass; shift += digit, ++passes) {
+        switch (digit) {
+            case 4: e = radix_pass<4>(nblocks, nseg, segs, shift, kin, vin, kout, vout, hist, scan_scratch, s); break;
+            case 5: e = radix_pass<5>(nblocks, nseg, segs, shift, kin, vin, kout, vout, hist, scan_scratch, s); break;
+            case 6: e = radix_pass<6>(nblocks, nseg, segs, shift, kin, vin, kout, vout, hist, scan_scratch, s); break;
+            case 7: e = radix_pass<7>(nblocks, nseg, segs, shift, kin, vin, kout, vout, hist, scan_scratch, s); break;
+            default: e = radix_pass<8>(nblocks, nseg, segs, shift, kin, vin, kout, vout, hist, scan_scratch, s); break;
+        }
+        if (e != cudaSuccess) return e;
         uint32_t *tk = kin, *tv = vin;
         kin = kout; vin = vout; kout = tk; vout = tv;
     }
