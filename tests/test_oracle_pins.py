@@ -23,6 +23,7 @@ Which pin covers which step of the method (Section II of the paper):
   depth order
       - test_depth_order_ties: index tie-break on equal float32 keys
   gradients (Section II-B)
+      - test_grad_uI_closed_form: dL/du_I equals (I, 0) / (0, I) for linear ramps
       - test_p10: analytic adjoint vs FP64 central differences, all 12 raw
         parameters, two views
   cutoff / culling, loss, optimiser
@@ -282,6 +283,23 @@ def test_bl_gradients_fd(orc):
     views = [sc.make_view(25.0, 40.0, 0.06, 0.07, 24, 20), sc.make_view(160.0, 55.0, 0.07, 0.06, 20, 24)]
     # step 1e-5: at 1e-6 the differences of this scene carry ~1.5e-6 of roundoff in both opacity modes
     _fd_check(orc, params, views, orc.cfg(K=0.0, alpha_mode=1), h_rel=1e-5)
+
+
+def test_grad_uI_closed_form(orc):
+    """dL/du_I, the image-plane position gradient behind the densification
+    statistic: with the upstream image equal to the column index x, L = I sum_pix
+    x beta(x - u) = I u_x sum beta = I u_x (energy normalisation, sigma >= 1.5
+    px), so dL/du_I = (I, 0); with the row index y, (0, I)."""
+    v = sc.make_view(33.0, 45.0, 0.05, 0.06, 96, 112)
+    p = one((0.05, -0.03, 0.02), s=0.2, o=0.4, P=0.7)
+    c = orc.cfg(K=0.0)
+    _, A, _ = orc.render(p, [v], c)
+    I = 0.7 * A[0, 0]
+    X, Y = np.meshgrid(np.arange(v["NA"], dtype=float), np.arange(v["NR"], dtype=float))
+    _, _, dx = orc.grad_uI(p, [v], [X], c)
+    _, _, dy = orc.grad_uI(p, [v], [Y], c)
+    assert np.allclose(dx[0, 0], [I, 0.0], rtol=1e-9, atol=1e-9 * I)
+    assert np.allclose(dy[0, 0], [0.0, I], rtol=1e-9, atol=1e-9 * I)
 
 
 def test_p5_telescoping(orc):
