@@ -62,8 +62,13 @@ _lib = None
 def lib():
     global _lib
     if _lib is None:
-        build()
-        L = ctypes.CDLL(_LIB)
+        # SDGR_ORACLE_LIB: another build of sdgr_oracle.c (the mutation test
+        # plants mistakes in copies of the source and runs the pins on them)
+        path = os.environ.get("SDGR_ORACLE_LIB")
+        if not path:
+            build()
+            path = _LIB
+        L = ctypes.CDLL(path)
         dp = ctypes.POINTER(ctypes.c_double)
         L.orc_render.argtypes = [dp, ctypes.c_int32, ctypes.POINTER(OrcView), ctypes.c_int32,
                                  ctypes.POINTER(OrcCfg), ctypes.c_int32, dp, dp, dp]

@@ -24,6 +24,7 @@ Which pin covers which step of the method (Section II of the paper):
       - test_depth_order_ties: index tie-break on equal float32 keys
   gradients (Section II-B)
       - test_grad_uI_closed_form: dL/du_I equals (I, 0) / (0, I) for linear ramps
+      - test_sh_basis_matches_scipy: SH basis against SciPy (constants, signs, order)
       - test_p10: analytic adjoint vs FP64 central differences, all 12 raw
         parameters, two views
   cutoff / culling, loss, optimiser
@@ -593,6 +594,26 @@ def test_sh_basis_orthonormal(orc):
             Y = orc.sh_basis([r * math.cos(ph), r * math.sin(ph), zi])
             G += wi * (2 * math.pi / nphi) * np.outer(Y, Y)
     assert np.abs(G - np.eye(15)).max() < 1e-12
+
+
+def test_sh_basis_matches_scipy(orc):
+    """The 15 basis values against SciPy's complex spherical harmonics turned
+    real (m > 0: sqrt2 (-1)^m Re Y_l^m, m < 0: sqrt2 (-1)^m Im Y_l^|m|, m = 0:
+    Y_l^0 -- the (-1)^m removes the Condon-Shortley phase), in the order
+    l = 1..3, m = -l..l.  Pins every constant, sign and the ordering, which
+    orthonormality alone leaves free."""
+    from scipy.special import sph_harm_y
+    rng = np.random.default_rng(7)
+    for _ in range(20):
+        d = rng.normal(size=3)
+        d /= np.linalg.norm(d)
+        theta, phi = math.acos(d[2]), math.atan2(d[1], d[0])
+        ref = []
+        for l in (1, 2, 3):
+            for m in range(-l, l + 1):
+                c = sph_harm_y(l, abs(m), theta, phi)
+                ref.append(math.sqrt(2) * (-1) ** m * (c.real if m > 0 else c.imag) if m else c.real)
+        assert np.abs(np.asarray(orc.sh_basis(d)) - np.array(ref)).max() < 1e-13
 
 
 def test_sh_degree_zero_and_direction(orc):
