@@ -49,12 +49,16 @@ def assert_images(gpu, ref, tol=IMG_TOL):
 
 
 def assert_grads(gpu, ref, tol=GRAD_TOL, mask=None):
+    # a group whose reference is exactly zero (a symmetry of the scene, e.g. the
+    # rotation of isotropic Gaussians) has no scale of its own: it is held to
+    # tol times the largest reference gradient of any group
+    overall = max(np.abs(ref[:, cols]).max() if ref.size else 0.0 for cols in GROUPS.values())
     for name, cols in GROUPS.items():
         r = ref[:, cols]
         gpu_g = gpu[:, cols]
         scale = np.abs(r).max()
         if scale == 0:
-            assert np.abs(gpu_g).max() == 0
+            assert np.abs(gpu_g).max() <= tol * overall, "%s: reference 0, gpu %.3e" % (name, np.abs(gpu_g).max())
             continue
         d = np.abs(gpu_g - r)
         if mask is not None:
