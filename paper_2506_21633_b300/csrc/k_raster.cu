@@ -297,9 +297,9 @@ __device__ __forceinline__ void stage_comp(const CompRec *__restrict__ comp, uin
 // depth order: alpha = o exp(-delta/2) within the cutoff; the Gaussian
 // receives alpha T; T *= 1 - alpha.  The ray stops once T < Tfloor.  For the
 // adjoint each ray records the index just past its last in-cutoff Gaussian
-// and the transmittance in front of that Gaussian.  The pair update is
-// branch-free: a pair outside the cutoff (or on a stopped ray) gets weight 0,
-// which leaves T unchanged.
+// (negated if the ray stopped at the floor) and the transmittance in front of
+// that Gaussian.  The pair update is branch-free: a pair outside the cutoff
+// (or on a stopped ray) gets weight 0, which leaves T unchanged.
 // ---------------------------------------------------------------------------
 template <int AM>
 __device__ __forceinline__ void
@@ -365,7 +365,7 @@ intensity_fwd_tile(const int tile, const StatusDev *st, const uint2 *__restrict_
     if (t < nb && sAcc[t] != 0ull) atomicAdd(&A[sid[t]], __ull2float_rn(sAcc[t]) * (1.f / 67108864.f));
     if (c.inside) {
         Tstop[c.pix] = Tprev;
-        last[c.pix] = lastj;
+        last[c.pix] = T < Tfloor ? -lastj : lastj;  // negative: the ray stopped at the floor
     }
 }
 
@@ -638,9 +638,11 @@ intensity_bwd_tile(const int tile, const StatusDev *st, const uint2 *__restrict_
     const TileCtx c = tile_ctx(views, V, tile);
     const LaneXY L = lane_xy();
     const uint2 r = ranges[tile];
-    const int32_t mylast = c.inside ? last[c.pix] : 0;
-    float T = c.inside ? Tstop[c.pix] : 0.f;
-    bool first = true;
+    const int32_t rec = c.inside ? last[c.pix] : 0;
+    const int32_t mylast = rec < 0 ? -rec : rec;
+    const bool stopped = rec < 0;
+    float T = c.inside ? Tstop[c.pix] : 0.f;  // 0 outside the image: such a lane adds nothing
+    bool first = mylast > 0;  // a ray without in-cutoff pairs never meets one here either
     if (t == 0) smax = 0;
     __syncthreads();
     if (mylast > 0) atomicMax(&smax, mylast);
@@ -685,43 +687,87 @@ intensity_bwd_tile(const int tile, const StatusDev *st, const uint2 *__restrict_
             const int send = nb - sl * SUB, sub = max(0, send - SUB);
             const int ns = send - sub;
             uint32_t hm = warp_hits(sM, sub, ns);
-            while (hm) {
-                // two hits per iteration, back to front (the second may be absent)
-                const int j0 = 31 - __clz(hm);
-                hm ^= 1u << j0;
-                const bool two = hm != 0u;
-                const int j1 = two ? 31 - __clz(hm) : j0;
-                if (two) hm ^= 1u << j1;
-                const float4 P0 = sP[sub + j0], Q0 = sQ[sub + j0];
-                const float4 P1 = sP[sub + j1], Q1 = sQ[sub + j1];
-                const float q0 = poly_q(P0, Q0.x, Q0.y, L);
-                const float q1 = poly_q(P1, Q1.x, Q1.y, L);
-                {
-                    const bool in = (q0 >= cut) & (sub + j0 < lim);
-                    const float e = in ? ex2_approx(q0) : 0.f;
-                    const float alpha = alpha_of<AM>(Q0.z, e);
-                    // relative error of a few ulp per step; the factor 1 - alpha is
-                    // the forward's (same alpha bits, same rounding)
-                    const float om = __fsub_rn(1.f, alpha);
-                    const float Td = T * rcp_approx(om);
-                    T = (in & !first) ? Td : T;
-                    first = first & !in;
-                    const float d = Q0.w - B;
-                    B = fmaf(alpha, d, B);
-                    // weight of the profile: d alpha / d G = o, or tau (1 - alpha)
-                    W[j0 * WSTRIDE + c.toff] = T * d * (AM ? e * om : e);
+            // fast path: every ray of the warp is past its first in-cutoff
+            // Gaussian and none stopped at the floor -- then every later pair
+            // of the list that is in the cutoff was taken by the forward pass
+            // (no index bound) and T is always rebuilt by division
+            if (__all_sync(0xffffffffu, !first && !stopped)) {
+                while (hm) {
+                    // two hits per iteration, back to front (the second may be absent)
+                    const int j0 = 31 - __clz(hm);
+                    hm ^= 1u << j0;
+                    const bool two = hm != 0u;
+                    const int j1 = two ? 31 - __clz(hm) : j0;
+                    if (two) hm ^= 1u << j1;
+                    const float4 P0 = sP[sub + j0], Q0 = sQ[sub + j0];
+                    const float4 P1 = sP[sub + j1], Q1 = sQ[sub + j1];
+                    const float q0 = poly_q(P0, Q0.x, Q0.y, L);
+                    const float q1 = poly_q(P1, Q1.x, Q1.y, L);
+                    {
+                        const bool in = q0 >= cut;
+                        const float e = in ? ex2_approx(q0) : 0.f;
+                        const float alpha = alpha_of<AM>(Q0.z, e);
+                        // relative error of a few ulp per step; the factor 1 - alpha is
+                        // the forward's (same alpha bits, same rounding)
+                        const float om = __fsub_rn(1.f, alpha);
+                        const float Td = T * rcp_approx(om);
+                        T = in ? Td : T;
+                        const float d = Q0.w - B;
+                        B = fmaf(alpha, d, B);
+                        // weight of the profile: d alpha / d G = o, or tau (1 - alpha)
+                        W[j0 * WSTRIDE + c.toff] = T * d * (AM ? e * om : e);
+                    }
+                    {
+                        const bool in = two & (q1 >= cut);
+                        const float e = in ? ex2_approx(q1) : 0.f;
+                        const float alpha = alpha_of<AM>(Q1.z, e);
+                        const float om = __fsub_rn(1.f, alpha);
+                        const float Td = T * rcp_approx(om);
+                        T = in ? Td : T;
+                        const float d = Q1.w - B;
+                        B = fmaf(alpha, d, B);
+                        if (two) W[j1 * WSTRIDE + c.toff] = T * d * (AM ? e * om : e);
+                    }
                 }
-                {
-                    const bool in = two & (q1 >= cut) & (sub + j1 < lim);
-                    const float e = in ? ex2_approx(q1) : 0.f;
-                    const float alpha = alpha_of<AM>(Q1.z, e);
-                    const float om = __fsub_rn(1.f, alpha);
-                    const float Td = T * rcp_approx(om);
-                    T = (in & !first) ? Td : T;
-                    first = first & !in;
-                    const float d = Q1.w - B;
-                    B = fmaf(alpha, d, B);
-                    if (two) W[j1 * WSTRIDE + c.toff] = T * d * (AM ? e * om : e);
+            } else {
+                while (hm) {
+                    // two hits per iteration, back to front (the second may be absent)
+                    const int j0 = 31 - __clz(hm);
+                    hm ^= 1u << j0;
+                    const bool two = hm != 0u;
+                    const int j1 = two ? 31 - __clz(hm) : j0;
+                    if (two) hm ^= 1u << j1;
+                    const float4 P0 = sP[sub + j0], Q0 = sQ[sub + j0];
+                    const float4 P1 = sP[sub + j1], Q1 = sQ[sub + j1];
+                    const float q0 = poly_q(P0, Q0.x, Q0.y, L);
+                    const float q1 = poly_q(P1, Q1.x, Q1.y, L);
+                    {
+                        const bool in = (q0 >= cut) & (sub + j0 < lim);
+                        const float e = in ? ex2_approx(q0) : 0.f;
+                        const float alpha = alpha_of<AM>(Q0.z, e);
+                        // relative error of a few ulp per step; the factor 1 - alpha is
+                        // the forward's (same alpha bits, same rounding)
+                        const float om = __fsub_rn(1.f, alpha);
+                        const float Td = T * rcp_approx(om);
+                        T = (in & !first) ? Td : T;
+                        first = first & !in;
+                        const float d = Q0.w - B;
+                        B = fmaf(alpha, d, B);
+                        // weight of the profile: d alpha / d G = o, or tau (1 - alpha)
+                        W[j0 * WSTRIDE + c.toff] = T * d * (AM ? e * om : e);
+                    }
+                    {
+                        const bool in = two & (q1 >= cut) & (sub + j1 < lim);
+                        const float e = in ? ex2_approx(q1) : 0.f;
+                        const float alpha = alpha_of<AM>(Q1.z, e);
+                        const float om = __fsub_rn(1.f, alpha);
+                        const float Td = T * rcp_approx(om);
+                        T = (in & !first) ? Td : T;
+                        first = first & !in;
+                        const float d = Q1.w - B;
+                        B = fmaf(alpha, d, B);
+                        if (two) W[j1 * WSTRIDE + c.toff] = T * d * (AM ? e * om : e);
+                    }
                 }
             }
             __syncthreads();
