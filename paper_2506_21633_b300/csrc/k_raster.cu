@@ -3,9 +3,12 @@
 // Section II-A-2, eq. I_i) and the layover splat on the imaging plane
 // (Section II-A-3, eq. S_{n,m}), and their adjoints (Section II-B-1/2).
 //
-// One CTA per 16x16 tile, one thread per pixel (ray); warp w covers the 8x4
-// pixel block with columns 8 (w & 1) .. +7 and rows 4 (w >> 1) .. +3.  The
-// tile's instance list is staged through shared memory in batches of 256.
+// A CTA works on one 16x16 tile at a time, one thread per pixel (ray); warp w
+// covers the 8x4 pixel block with columns 8 (w & 1) .. +7 and rows
+// 4 (w >> 1) .. +3.  Which tiles a CTA takes follows the launch's schedule
+// (for_tiles): one CTA per tile, one per item of the longest-first work list,
+// or resident CTAs pulling items.  The tile's instance list is staged through
+// shared memory in batches (256 records; 1024 in the splat adjoint).
 //
 // Culling: when a batch is staged, each Gaussian gets the set of the tile's
 // eight pixel blocks that its K-ellipse reaches (found from the ellipse's
@@ -18,14 +21,16 @@
 // pixel's tile-local coordinates (X, Y); the six coefficients are formed when
 // the batch is staged, so a pair costs five FMAs on per-thread constants.
 //
-// Sums over the tile's pixels per Gaussian (the ray sums A_i of the intensity
-// pass and the six moments of the adjoints) use a two-phase transpose instead
-// of warp-shuffle reductions: in phase 1 every pixel writes its weight for
-// each of its hit Gaussians into a 32 x 256 shared-memory table; in phase 2
-// eight threads per Gaussian read the table's entries of that Gaussian's hit
-// blocks (one float4 per thread per block: four rows of one column) and
-// three shuffles combine the eight partial sums.  Entries of blocks that a
-// Gaussian does not reach are never written and never read.
+// Sums over the tile's pixels per Gaussian.  The intensity pass needs only
+// sum_rays alpha T (non-negative, each term <= 1): one redux.sync per hit on
+// 2^-26 fixed point into a 64-bit shared slot.  The intensity adjoint needs
+// six signed moments and uses a two-phase transpose: in phase 1 every pixel
+// writes its weight for each of its hit Gaussians into a 32 x 256 shared-
+// memory table; in phase 2 eight threads per Gaussian read the table's entries
+// of that Gaussian's hit blocks (one float4 per thread per block: four rows of
+// one column) and three shuffles combine the eight partial sums.  Entries of
+// blocks that a Gaussian does not reach are never written and never read.  The
+// splat adjoint is Gaussian-parallel over the same hit blocks.
 #include "sdgr_internal.cuh"
 
 namespace sdgr {

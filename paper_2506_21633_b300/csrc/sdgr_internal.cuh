@@ -139,10 +139,9 @@ __device__ __forceinline__ float ex2_approx(float x) {
     return y;
 }
 
-// exp2 argument of the Gaussian weight at offset (dx, dy).  Written with
-// explicit round-to-nearest intrinsics so that every kernel that evaluates a
-// pair obtains the same bits (the backward reconstructs the transmittance by
-// dividing by the very (1 - alpha) factors the forward multiplied by).
+// exp2 argument of the Gaussian weight at offset (dx, dy), with explicit
+// round-to-nearest intrinsics.  Used by the pair-count diagnostic; the raster
+// kernels evaluate the same quadratic in tile-local polynomial form.
 __device__ __forceinline__ float gauss_q(float qa, float qb, float qc, float dx, float dy) {
     float t = __fmul_rn(qa, dx);
     t = __fmaf_rn(qb, dy, t);
