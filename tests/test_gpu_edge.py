@@ -88,8 +88,6 @@ def test_single_row_and_column_images():
 
 
 def test_empty_scene_in_a_batch():
-    import torch
-    from paper_2506_21633_b300.render import Renderer, split_images
     a = sc.vehicle_box_scene(300, seed=9, extent=(1.0, 1.0, 0.5), log_s_mean=math.log(0.08), center=(0, 0, 0))
     b = sc.vehicle_box_scene(200, seed=10, extent=(1.0, 1.0, 0.5), log_s_mean=math.log(0.08), center=(0, 0, 0))
     params = np.concatenate([a, b])
@@ -105,9 +103,6 @@ def test_empty_scene_in_a_batch():
 
 
 def test_nan_gaussian_stays_local():
-    import torch
-    from paper_2506_21633_b300 import _lib as L
-    from paper_2506_21633_b300.render import Renderer, split_images
     params = sc.vehicle_box_scene(400, seed=11, extent=(1.0, 1.0, 0.5), log_s_mean=math.log(0.08), center=(0, 0, 0))
     views = [sc.make_view(30.0, 40.0, 0.05, 0.05, 48, 40), sc.make_view(200.0, 55.0, 0.05, 0.05, 40, 48)]
     bad = params.copy()

@@ -86,7 +86,6 @@ def test_served_render_matches_oracle():
 
 
 def test_failures_stay_local():
-    import concurrent.futures
     from paper_2506_21633_b300.serve import AdmissionError, Server
     scenes = _scenes()
     srv = Server(scenes, hbm_budget_bytes=64 << 20, n_slots=2)

@@ -3,7 +3,6 @@ scheduler object is built without its device state; only host-side
 capacity arithmetic of the C ABI is used)."""
 import collections
 
-import pytest
 
 import sdgr_scenes as sc
 

@@ -5,7 +5,6 @@ initialisation."""
 import math
 
 import numpy as np
-import pytest
 
 
 def test_psnr_closed_forms():
