@@ -185,20 +185,22 @@ __device__ __forceinline__ void block_moments(const float4 &w, float dx, float d
     m[5] += pyy;
 }
 
-__device__ __forceinline__ void reduce8(float m[6]) {
+// Sum of the six moments over a group of eight threads (cc = 0..7) and one
+// atomic per moment: each thread stores its partial moments into `scr` (48
+// floats owned by the group, moment-major), then thread cc < 6 adds the eight
+// partials of moment cc (two float4 loads) and issues that moment's atomic.
+// `scr` must be 16-byte aligned; the whole warp calls this.
+__device__ __forceinline__ void moments_out(float *scr, int cc, const float m[6], bool valid, float4 *acc,
+                                            uint32_t vg) {
+    __syncwarp();
 #pragma unroll
-    for (int q = 0; q < 6; ++q) {
-        m[q] += __shfl_xor_sync(0xffffffffu, m[q], 1);
-        m[q] += __shfl_xor_sync(0xffffffffu, m[q], 2);
-        m[q] += __shfl_xor_sync(0xffffffffu, m[q], 4);
-    }
-}
-
-__device__ __forceinline__ void add_moments(float4 *acc, uint32_t vg, const float m[6]) {
-    if (m[0] != 0.f || m[1] != 0.f || m[2] != 0.f || m[3] != 0.f || m[4] != 0.f || m[5] != 0.f) {
-        float *p = reinterpret_cast<float *>(acc + 2 * (size_t)vg);
-#pragma unroll
-        for (int q = 0; q < 6; ++q) atomicAdd(p + q, m[q]);
+    for (int q = 0; q < 6; ++q) scr[q * 8 + cc] = m[q];
+    __syncwarp();
+    if (cc < 6) {
+        const float4 a = *reinterpret_cast<const float4 *>(scr + cc * 8);
+        const float4 b = *reinterpret_cast<const float4 *>(scr + cc * 8 + 4);
+        const float v = ((a.x + a.y) + (a.z + a.w)) + ((b.x + b.y) + (b.z + b.w));
+        if (valid && v != 0.f) atomicAdd(reinterpret_cast<float *>(acc + 2 * (size_t)vg) + cc, v);
     }
 }
 
@@ -516,6 +518,7 @@ splat_bwd_tile(const int tile, const StatusDev *st, const uint2 *__restrict__ ra
     __shared__ uint8_t sperm[SBATCH];
     __shared__ __align__(16) float sg[TILE_PIX];  // dL/dS of the tile's pixels, in table layout
     __shared__ __align__(16) float zero4[4];
+    __shared__ __align__(16) float sred[32 * 48];  // moment reduction scratch, 48 floats per group of 8
     const int t = threadIdx.x, warp = t >> 5;
     if (t < 4) zero4[t] = 0.f;
     const TileCtx c = tile_ctx(views, V, tile);
@@ -587,8 +590,7 @@ splat_bwd_tile(const int tile, const StatusDev *st, const uint2 *__restrict__ ra
                     block_moments(w, dx, dy0, m);
                 }
             }
-            reduce8(m);
-            if (cc == 0 && k < nb) add_moments(accI, sid[k], m);
+            moments_out(sred + (t >> 3) * 48, cc, m, k < nb, accI, sid[ks]);
         }
     }
 }
@@ -791,8 +793,8 @@ intensity_bwd_tile(const int tile, const StatusDev *st, const uint2 *__restrict_
                 const float4 w4 = *reinterpret_cast<const float4 *>(src);
                 block_moments(w4, (b & 1) ? dx1 : dx0, fmaf(4.f, (float)(b >> 1), dy00), m);
             }
-            reduce8(m);
-            if (cc == 0 && j < ns) add_moments(accC, sid[sub + j], m);
+            // the group's table row is free after the reads above: scratch
+            moments_out(W + j * WSTRIDE, cc, m, j < ns, accC, sid[sub + (j < ns ? j : 0)]);
             __syncthreads();
         }
     }
