@@ -28,7 +28,8 @@
 // writes its weight for each of its hit Gaussians into a 32 x 256 shared-
 // memory table; in phase 2 eight threads per Gaussian read the table's entries
 // of that Gaussian's hit blocks (one float4 per thread per block: four rows of
-// one column) and three shuffles combine the eight partial sums.  Entries of
+// one column); the eight partial sums meet in shared memory, one thread per
+// moment adds them and issues its atomic.  Entries of
 // blocks that a Gaussian does not reach are never written and never read.  The
 // splat adjoint is Gaussian-parallel over the same hit blocks.
 #include "sdgr_internal.cuh"
