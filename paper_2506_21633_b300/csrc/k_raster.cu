@@ -505,8 +505,8 @@ cudaError_t launch_splat_fwd(const uint2 *rangesI, const uint32_t *vals, const I
 // dL/dI = c M0, dL/du_I, dL/dconic_I and dL/dc.  No pixel depends on
 // another here, so the kernel is Gaussian-parallel: eight threads per
 // Gaussian walk its hit blocks, each thread one column (four rows) per block,
-// with dL/dS read from shared memory as one float4; three shuffles combine
-// the eight partial moments.
+// with dL/dS read from shared memory as one float4; the eight partial
+// moments meet in shared memory, one thread per moment adds them.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void
 splat_bwd_tile(const int tile, const StatusDev *st, const uint2 *__restrict__ rangesI, const uint32_t *__restrict__ vals,
