@@ -190,7 +190,10 @@ __device__ __forceinline__ void block_moments(const float4 &w, float dx, float d
 // atomic per moment: each thread stores its partial moments into `scr` (48
 // floats owned by the group, moment-major), then thread cc < 6 adds the eight
 // partials of moment cc (two float4 loads) and issues that moment's atomic.
-// `scr` must be 16-byte aligned; the whole warp calls this.
+// `scr` must be 16-byte aligned; the whole warp calls this.  Groups sit
+// RSTRIDE floats apart: the four groups of a warp then store to disjoint
+// banks (offsets 0, 24, 16, 8 mod 32).
+constexpr int RSTRIDE = 56;
 __device__ __forceinline__ void moments_out(float *scr, int cc, const float m[6], bool valid, float4 *acc,
                                             uint32_t vg) {
     __syncwarp();
@@ -519,7 +522,7 @@ splat_bwd_tile(const int tile, const StatusDev *st, const uint2 *__restrict__ ra
     __shared__ uint8_t sperm[SBATCH];
     __shared__ __align__(16) float sg[TILE_PIX];  // dL/dS of the tile's pixels, in table layout
     __shared__ __align__(16) float zero4[4];
-    __shared__ __align__(16) float sred[32 * 48];  // moment reduction scratch, 48 floats per group of 8
+    __shared__ __align__(16) float sred[32 * RSTRIDE];  // moment reduction scratch, one slot per group of 8
     const int t = threadIdx.x, warp = t >> 5;
     if (t < 4) zero4[t] = 0.f;
     const TileCtx c = tile_ctx(views, V, tile);
@@ -591,7 +594,7 @@ splat_bwd_tile(const int tile, const StatusDev *st, const uint2 *__restrict__ ra
                     block_moments(w, dx, dy0, m);
                 }
             }
-            moments_out(sred + (t >> 3) * 48, cc, m, k < nb, accI, sid[ks]);
+            moments_out(sred + (t >> 3) * RSTRIDE, cc, m, k < nb, accI, sid[ks]);
         }
     }
 }
@@ -794,8 +797,11 @@ intensity_bwd_tile(const int tile, const StatusDev *st, const uint2 *__restrict_
                 const float4 w4 = *reinterpret_cast<const float4 *>(src);
                 block_moments(w4, (b & 1) ? dx1 : dx0, fmaf(4.f, (float)(b >> 1), dy00), m);
             }
-            // the group's table row is free after the reads above: scratch
-            moments_out(W + j * WSTRIDE, cc, m, j < ns, accC, sid[sub + (j < ns ? j : 0)]);
+            // the group's table row is free after the reads above: scratch, at
+            // an offset that puts the four groups of the warp on disjoint banks
+            // (row j starts at bank 8 j mod 32)
+            moments_out(W + j * WSTRIDE + 8 * ((((t >> 3) & 3) - j) & 3), cc, m, j < ns, accC,
+                        sid[sub + (j < ns ? j : 0)]);
             __syncthreads();
         }
     }
