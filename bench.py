@@ -236,7 +236,7 @@ def run_sdgr(args):
     torch.cuda.set_device(local)
     dist_setup("nccl")
     dev = torch.device("cuda", local)
-    from paper_2506_21633_b300 import _lib
+    from paper_2506_21633_b300 import _lib, tune
     from paper_2506_21633_b300.render import Renderer, adam_step, l1_loss, views_npix
 
     params, start, views, desc = workload(args.workload, rank)
@@ -283,20 +283,12 @@ def run_sdgr(args):
         code, required = r.status()
         assert code == _lib.SDGR_OK, "device status %d" % code
     pairs = r.count_pairs()
-    schedule_ms = None
-    if args.schedule == "auto":  # untimed: two steps per schedule, keep the fastest
-        schedule_ms = {}
-        for name in ("tiles", "ordered", "persistent"):
-            r.set_schedule(name)
-            step()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            for _ in range(2):
-                step()
-            e1.record(stream)
-            e1.synchronize()
-            schedule_ms[name] = round(e0.elapsed_time(e1) / 2, 3)
-        r.set_schedule(min(schedule_ms, key=schedule_ms.get))
+    schedule_ms, stage_batch_ms = None, None
+    if args.schedule == "auto":  # untimed: the schedule, then each raster kernel's staging batch
+        _, schedule_ms = tune.tune_schedule(r, step, steps=2)
+        schedule_ms = {k: round(v, 3) for k, v in schedule_ms.items()}
+        stage_batch_ms = {k: {nb: round(ms, 3) for nb, ms in d.items()}
+                          for k, (_, d) in tune.tune_stage_batches(r, step, steps=2).items()}
     else:
         r.set_schedule(args.schedule)
     r.profile(True)
@@ -423,11 +415,18 @@ def run_sdgr(args):
                    "l2": "inputs larger than L2 (workspace %.1f GB per step)" % (r.workspace_bytes() / 1e9),
                    "pairs_per_step": {"computation_plane": pairs[0], "imaging_plane": pairs[1]},
                    "instances_per_step": int(r.n_inst), "schedule": r.schedule,
-                   "schedule_ms_per_step": schedule_ms},
+                   "schedule_ms_per_step": schedule_ms, "stage_batch": stage_batches(r),
+                   "stage_batch_ms_per_launch": stage_batch_ms},
         "gaussian_pixel_evals_per_s": round((pairs[0] + pairs[1]) * world * args.steps / (ms_max / 1e3), 1),
         "plain": plain, "e2e": e2e, "roofline": roof, "gpu_launches": int(launches), "clocks": clocks,
     }
     return out, params, start, views
+
+
+def stage_batches(r):
+    """Staging batch of each raster kernel in use (chosen, else the default)."""
+    from paper_2506_21633_b300 import _lib
+    return {k: r.stage_batch.get(k, _lib.sdgr_stage_batch_options(k)[0]) for k in _lib.RASTER_KERNELS}
 
 
 def cpu_baseline(params, views, npix_view=None):
@@ -557,7 +556,11 @@ def run_uneven(args):
                                       offs[-1], sizes, V),
                        "pairs_per_step": {"computation_plane": pairs[0], "imaging_plane": pairs[1]},
                        "instances_per_step": int(fs.r.n_inst), "schedule": fs.r.schedule,
-                       "schedule_ms_per_step": {k: round(v, 3) for k, v in schedule_ms.items()} if schedule_ms else None},
+                       "schedule_ms_per_step": {k: round(v, 3) for k, v in schedule_ms.items()} if schedule_ms else None,
+                       "stage_batch": stage_batches(fs.r),
+                       "stage_batch_ms_per_launch": {k: {nb: round(ms, 3) for nb, ms in d.items()}
+                                                     for k, (_, d) in getattr(fs, "stage_batch_ms", {}).items()}
+                       or None},
             "plain": {"value": round(V / t_plain, 3), "unit": UNIT, "s_per_step": round(t_plain, 3)},
             "gpu_launches": int(fs.graph_launches) * args.steps,
             "gpu_launches_how": "kernel launches captured in the step's graph x steps"}

@@ -222,6 +222,26 @@ sdgr_status sdgr_set_sh(sdgr_ws *ws, const float *sh, float *dsh, int32_t degree
 #define SDGR_SCHED_PERSISTENT 2
 sdgr_status sdgr_set_schedule(sdgr_ws *ws, int32_t mode);
 
+/* Staging batch of raster kernel `kernel` (0 intensity pass, 1 splat,
+ * 2 splat adjoint, 3 intensity adjoint): the number of Gaussian records a
+ * CTA stages into shared memory before its warps walk them (the tile's
+ * depth-ordered list is processed in such batches, one barrier pair each).
+ * Larger batches mean fewer barriers and less waiting for the slowest warp of
+ * a batch; smaller ones less shared memory per CTA (more resident CTAs) and
+ * less staging past the point where every ray of a tile has stopped.
+ * The result does not depend on it: every pair's arithmetic, the order of
+ * each pixel's and ray's sums and every per-(tile, Gaussian) partial sum are
+ * the same for every size (the order of the float atomics that add those
+ * partial sums across tiles is unordered in any case).
+ * sdgr_stage_batch_options writes up to max_sizes supported sizes of
+ * `kernel` to sizes (the first is the default) and returns how many there are
+ * (0 for an unknown kernel).  sdgr_set_stage_batch selects one of them for
+ * the following sdgr_render_fwd / sdgr_render_bwd calls on ws; records = 0
+ * restores the default.  Errors: SDGR_ERR_INVALID (NULL ws, unknown kernel,
+ * unsupported size). */
+int32_t sdgr_stage_batch_options(int32_t kernel, int32_t *sizes, int32_t max_sizes);
+sdgr_status sdgr_set_stage_batch(sdgr_ws *ws, int32_t kernel, int32_t records);
+
 /* Densification and pruning (the "Densification and Pruning Operation" of
  * Section II-B and the thresholds of Section III-D).  Gradient statistics:
  * while bound, every sdgr_render_bwd adds, for each Gaussian and each view

@@ -24,12 +24,16 @@ EXPORTS = (
     "sdgr_read_status", "sdgr_status_string", "sdgr_profile_enable", "sdgr_profile_read",
     "sdgr_count_pairs", "sdgr_launch_count", "sdgr_render_fwd_noalloc", "sdgr_adam_step_device",
     "sdgr_copy_status_async", "sdgr_set_sh", "sdgr_set_densify_stats", "sdgr_densify_scratch_bytes",
-    "sdgr_densify", "sdgr_set_schedule", "sdgr_adam_step_flat",
+    "sdgr_densify", "sdgr_set_schedule", "sdgr_adam_step_flat", "sdgr_stage_batch_options",
+    "sdgr_set_stage_batch",
 )
 
 SCHED_ORDERED = 1
 SCHED_PERSISTENT = 2
 SCHEDULES = {"tiles": 0, "ordered": SCHED_ORDERED, "persistent": SCHED_ORDERED | SCHED_PERSISTENT}
+
+# raster kernels by their index in sdgr_set_stage_batch
+RASTER_KERNELS = ("intensity_fwd", "splat_fwd", "splat_bwd", "intensity_bwd")
 
 STAGES = ("preprocess", "depth_sort", "bin", "intensity_fwd", "splat_fwd", "splat_bwd", "intensity_bwd",
           "param_bwd")
@@ -105,6 +109,9 @@ def lib():
         L.sdgr_set_sh.argtypes = [vp, vp, vp, i32]
         L.sdgr_set_densify_stats.argtypes = [vp, vp, vp]
         L.sdgr_set_schedule.argtypes = [vp, i32]
+        L.sdgr_stage_batch_options.argtypes = [i32, P(ctypes.c_int32), i32]
+        L.sdgr_stage_batch_options.restype = i32
+        L.sdgr_set_stage_batch.argtypes = [vp, i32, i32]
         L.sdgr_densify_scratch_bytes.argtypes = [i64]
         L.sdgr_densify.argtypes = [vp, vp, vp, vp, vp, vp, vp, i64, P(SdgrDensifyCfg), vp, vp, vp, vp, i64, vp,
                                    P(ctypes.c_int64), vp]
@@ -242,6 +249,20 @@ def sdgr_set_densify_stats(ws, accum_ptr, count_ptr):
 
 def sdgr_set_schedule(ws, mode):
     _check("sdgr_set_schedule", lib().sdgr_set_schedule(ws, int(mode)))
+
+
+def sdgr_stage_batch_options(kernel):
+    """Supported staging batch sizes of raster kernel `kernel` (index or
+    name), the default first."""
+    k = RASTER_KERNELS.index(kernel) if isinstance(kernel, str) else int(kernel)
+    buf = (ctypes.c_int32 * 8)()
+    n = int(lib().sdgr_stage_batch_options(k, buf, 8))
+    return tuple(int(buf[i]) for i in range(min(n, 8)))
+
+
+def sdgr_set_stage_batch(ws, kernel, records):
+    k = RASTER_KERNELS.index(kernel) if isinstance(kernel, str) else int(kernel)
+    _check("sdgr_set_stage_batch", lib().sdgr_set_stage_batch(ws, k, int(records)))
 
 
 def sdgr_densify_scratch_bytes(N):

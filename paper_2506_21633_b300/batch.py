@@ -14,6 +14,7 @@ from __future__ import annotations
 import torch
 
 from . import _lib as L
+from . import tune
 from .render import Renderer, _stream_handle, l1_loss, views_npix
 
 DEFAULT_LR = (1.6e-4, 5e-3, 1e-3, 5e-2, 2.5e-3)  # means, log-scales, quaternions, opacity logit, P
@@ -95,38 +96,32 @@ class FusedStep:
         self.graph = g
         return self
 
-    def autotune(self, schedules=("tiles", "ordered", "persistent"), steps=3):
-        """Time `steps` steps under each raster schedule (re-capturing the
-        graph if one is captured) and keep the fastest.  The optimiser state is
-        restored afterwards, so tuning does not advance the optimisation.
-        Returns (best, {schedule: ms per step})."""
+    def autotune(self, schedules=("tiles", "ordered", "persistent"), steps=3, stage_batches=True):
+        """Pick the raster schedule (whole steps timed under each, re-capturing
+        the graph if one is captured) and then each raster kernel's staging
+        batch (that kernel's device time, eager steps); see `tune`.  The
+        optimiser state is restored afterwards, so tuning does not advance the
+        optimisation.  Returns (best schedule, {schedule: ms per step}); the
+        staging batches chosen and their times are in `self.stage_batch_ms`."""
         state = (self.p, self.m, self.v, self.step_dev)
         saved = [t.clone() for t in state]
         captured = self.graph is not None
-        stream = torch.cuda.current_stream(self.p.device)
-        times = {}
-        for name in schedules:
-            self.r.set_schedule(name)
+
+        def recapture():
             if captured:
                 self.graph = None
                 self.capture()
-            self.step()  # warm-up
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            for _ in range(steps):
-                self.step()
-            e1.record(stream)
-            e1.synchronize()
+
+        best, times = tune.tune_schedule(self.r, self.step, steps=steps, schedules=schedules, on_change=recapture)
+        if not self.check():
+            raise RuntimeError("instance capacity exceeded while tuning")
+        self.stage_batch_ms = {}
+        if stage_batches:
+            self.graph = None  # staging batches are tuned on eager steps
+            self.stage_batch_ms = tune.tune_stage_batches(self.r, self.enqueue, steps=steps)
             if not self.check():
                 raise RuntimeError("instance capacity exceeded while tuning")
-            times[name] = e0.elapsed_time(e1) / steps
-            for t, s0 in zip(state, saved):
-                t.copy_(s0)
-        best = min(times, key=times.get)
-        self.r.set_schedule(best)
-        if captured:
-            self.graph = None
-            self.capture()
+            recapture()
         for t, s0 in zip(state, saved):
             t.copy_(s0)
         torch.cuda.synchronize(self.p.device)

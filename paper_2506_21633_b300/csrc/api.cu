@@ -141,6 +141,7 @@ struct sdgr_ws {
     int sh_degree = 0;
     float *dens_accum = nullptr, *dens_count = nullptr;  // sdgr_set_densify_stats
     int sched = SDGR_SCHED_ORDERED | SDGR_SCHED_PERSISTENT;  // sdgr_set_schedule
+    int stage_batch[4] = {0, 0, 0, 0};  // sdgr_set_stage_batch (0: the kernel's default)
     std::vector<ViewDev> hviews;
     std::vector<SceneDev> hscenes;
     std::vector<int32_t> hscene_views;
@@ -446,10 +447,13 @@ static cudaError_t raster_sched(sdgr_ws *ws, int kernel, cudaStream_t s, TileSch
     sc.slot = kernel;
     sc.persistent_grid = 0;
     sc.ntiles = ws->tiles;
+    const int *sizes = nullptr;
+    stage_batch_options(kernel, &sizes);
+    sc.nb = ws->stage_batch[kernel] > 0 ? ws->stage_batch[kernel] : sizes[0];
     if (!(ws->sched & SDGR_SCHED_ORDERED)) return cudaSuccess;
     sc.order = ws->at<int32_t>(ws->L.order) + (size_t)plane * ws->tiles;
     if (ws->sched & SDGR_SCHED_PERSISTENT) {
-        sc.persistent_grid = ws->sms * raster_blocks_per_sm(kernel);
+        sc.persistent_grid = ws->sms * raster_blocks_per_sm(kernel, sc.nb);
         return cudaMemsetAsync(&sc.work->next[kernel], 0, sizeof(int32_t), s);
     }
     return cudaSuccess;
@@ -539,6 +543,29 @@ sdgr_status sdgr_set_schedule(sdgr_ws *ws, int32_t mode) {
         return SDGR_ERR_INVALID;
     ws->sched = mode;
     return SDGR_OK;
+}
+
+int32_t sdgr_stage_batch_options(int32_t kernel, int32_t *sizes, int32_t max_sizes) {
+    const int *opt = nullptr;
+    const int n = stage_batch_options(kernel, &opt);
+    for (int i = 0; i < n && i < max_sizes && sizes; ++i) sizes[i] = opt[i];
+    return n;
+}
+
+sdgr_status sdgr_set_stage_batch(sdgr_ws *ws, int32_t kernel, int32_t records) {
+    if (!ws || kernel < 0 || kernel > 3) return SDGR_ERR_INVALID;
+    if (records == 0) {
+        ws->stage_batch[kernel] = 0;
+        return SDGR_OK;
+    }
+    const int *opt = nullptr;
+    const int n = stage_batch_options(kernel, &opt);
+    for (int i = 0; i < n; ++i)
+        if (opt[i] == records) {
+            ws->stage_batch[kernel] = records;
+            return SDGR_OK;
+        }
+    return SDGR_ERR_INVALID;
 }
 
 sdgr_status sdgr_set_densify_stats(sdgr_ws *ws, float *accum, float *count) {

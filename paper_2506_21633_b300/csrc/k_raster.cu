@@ -36,11 +36,20 @@
 
 namespace sdgr {
 
-constexpr int BATCH = 256;    // Gaussian records staged per batch
+constexpr int BATCH = 256;    // Gaussian records staged per batch by the intensity adjoint
 constexpr int SUB = 32;       // Gaussians per weight table
 constexpr int WSTRIDE = 264;  // row stride of the weight table (floats)
-constexpr int SBATCH = 1024;  // records staged per batch by the splat adjoint (no weight table: fewer barriers)
-constexpr int SPER = SBATCH / 256;  // records staged per thread
+
+// Staging batch sizes (Gaussian records per CTA batch; a multiple of the 256
+// threads, each thread staging NB / 256 records).  Larger batches mean fewer
+// barriers and shorter waits for the slowest warp of a batch, smaller ones
+// less shared memory (more resident CTAs) and less staging past the point
+// where every ray of a tile has stopped.  The intensity adjoint's weight
+// table and phase-2 mapping are built around one record per thread.
+static const int kStageK3[] = {256, 512};
+static const int kStageK4[] = {256, 512, 1024};
+static const int kStageK5[] = {1024, 512, 256};
+static const int kStageK6[] = {256};
 
 struct TileCtx {
     int v;
@@ -254,6 +263,17 @@ __device__ __forceinline__ float alpha_of(float o, float e) {
     return y < 0.125f ? series : direct;
 }
 
+// Calls f(0), ..., f(N - 1) as straight-line code.  (A `for` loop over a
+// compile-time trip count, even with `#pragma unroll`, costs the staging code
+// six registers here.)
+template <int N, typename F>
+__device__ __forceinline__ void unrolled(F &&f) {
+    if constexpr (N > 0) {
+        unrolled<N - 1>(f);
+        f(N - 1);
+    }
+}
+
 // Runs body(tile) for the tiles this CTA owns under the launch's schedule.
 template <typename F>
 __device__ __forceinline__ void for_tiles(const TileSched &sc, const StatusDev *st, F &&body) {
@@ -312,16 +332,17 @@ __device__ __forceinline__ void stage_comp(const CompRec *__restrict__ comp, uin
 // that Gaussian.  The pair update is branch-free: a pair outside the cutoff
 // (or on a stopped ray) gets weight 0, which leaves T unchanged.
 // ---------------------------------------------------------------------------
-template <int AM>
+template <int AM, int NB>
 __device__ __forceinline__ void
 intensity_fwd_tile(const int tile, const StatusDev *st, const uint2 *__restrict__ ranges, const uint32_t *__restrict__ vals,
                    const CompRec *__restrict__ comp, const ViewDev *__restrict__ views, int V, float cut, float Tfloor,
                    float *__restrict__ A, float *__restrict__ Tstop, int32_t *__restrict__ last) {
-    __shared__ float4 sP[BATCH];  // (qa, qb, qc, l1)
-    __shared__ float4 sQ[BATCH];  // (l2, c0, o, -)
-    __shared__ uint32_t sM[BATCH];
-    __shared__ uint32_t sid[BATCH];
-    __shared__ unsigned long long sAcc[BATCH];  // sum of alpha T over the tile's rays, in units of 2^-26
+    constexpr int PER = NB / 256;  // records staged per thread
+    __shared__ float4 sP[NB];  // (qa, qb, qc, l1)
+    __shared__ float4 sQ[NB];  // (l2, c0, o, -)
+    __shared__ uint32_t sM[NB];
+    __shared__ uint32_t sid[NB];
+    __shared__ unsigned long long sAcc[NB];  // sum of alpha T over the tile's rays, in units of 2^-26
     const int t = threadIdx.x, lane = t & 31;
     const TileCtx c = tile_ctx(views, V, tile);
     const LaneXY L = lane_xy();
@@ -330,26 +351,30 @@ intensity_fwd_tile(const int tile, const StatusDev *st, const uint2 *__restrict_
     float T = c.inside ? 1.f : 0.f, Tprev = 1.f;  // a ray outside the image takes no pair
     int32_t lastj = 0;
     int nb = 0;  // Gaussians staged in the current batch
-    uint32_t vnext = r.x + t < r.y ? vals[r.x + t] : 0u;  // next batch's list entry, loaded one batch ahead
-    for (uint32_t base = r.x; base < r.y; base += BATCH) {
+    uint32_t vnext[PER];  // next batch's list entries, loaded one batch ahead
+    unrolled<PER>([&](int u) { vnext[u] = r.x + t + 256 * u < r.y ? vals[r.x + t + 256 * u] : 0u; });
+    for (uint32_t base = r.x; base < r.y; base += NB) {
         if (__syncthreads_count(T < Tfloor) == (int)blockDim.x) break;
-        // the previous batch's sums: one global atomic per (tile, Gaussian)
-        if (t < nb && sAcc[t] != 0ull) atomicAdd(&A[sid[t]], __ull2float_rn(sAcc[t]) * (1.f / 67108864.f));
-        if (base + t < r.y) {
-            const uint32_t vg = vnext;
-            float4 P;
-            float2 Q, uv, oP;
-            uint32_t m = 0;
-            if (vg_ok(st, views[c.v], vg)) stage_comp(comp, vg, c, cutm, P, Q, m, uv, oP);
-            sP[t] = P;
-            sQ[t] = make_float4(Q.x, Q.y, oP.x, 0.f);
-            sM[t] = m;
-            sid[t] = vg;
-        }
-        sAcc[t] = 0ull;
-        if (base + BATCH + t < r.y) vnext = vals[base + BATCH + t];
+        unrolled<PER>([&](int u) {
+            const int k = t + 256 * u;
+            // the previous batch's sums: one global atomic per (tile, Gaussian)
+            if (k < nb && sAcc[k] != 0ull) atomicAdd(&A[sid[k]], __ull2float_rn(sAcc[k]) * (1.f / 67108864.f));
+            if (base + k < r.y) {
+                const uint32_t vg = vnext[u];
+                float4 P;
+                float2 Q, uv, oP;
+                uint32_t m = 0;
+                if (vg_ok(st, views[c.v], vg)) stage_comp(comp, vg, c, cutm, P, Q, m, uv, oP);
+                sP[k] = P;
+                sQ[k] = make_float4(Q.x, Q.y, oP.x, 0.f);
+                sM[k] = m;
+                sid[k] = vg;
+            }
+            sAcc[k] = 0ull;
+            if (base + NB + k < r.y) vnext[u] = vals[base + NB + k];
+        });
         __syncthreads();
-        nb = min(BATCH, (int)(r.y - base));
+        nb = min(NB, (int)(r.y - base));
         for (int sub = 0; sub < nb; sub += 32) {
             uint32_t hm = warp_hits(sM, sub, min(32, nb - sub));
             const int32_t kb = (int32_t)(base + sub + 1);
@@ -373,21 +398,24 @@ intensity_fwd_tile(const int tile, const StatusDev *st, const uint2 *__restrict_
         }
     }
     __syncthreads();
-    if (t < nb && sAcc[t] != 0ull) atomicAdd(&A[sid[t]], __ull2float_rn(sAcc[t]) * (1.f / 67108864.f));
+    unrolled<PER>([&](int u) {
+        const int k = t + 256 * u;
+        if (k < nb && sAcc[k] != 0ull) atomicAdd(&A[sid[k]], __ull2float_rn(sAcc[k]) * (1.f / 67108864.f));
+    });
     if (c.inside) {
         Tstop[c.pix] = Tprev;
         last[c.pix] = T < Tfloor ? -lastj : lastj;  // negative: the ray stopped at the floor
     }
 }
 
-template <int AM>
+template <int AM, int NB>
 __global__ void __launch_bounds__(256)
 k_intensity_fwd(const uint2 *__restrict__ ranges, const uint32_t *__restrict__ vals, const CompRec *__restrict__ comp,
                 const ViewDev *__restrict__ views, int V, float cut, float Tfloor, const StatusDev *st,
                 float *__restrict__ A, float *__restrict__ Tstop, int32_t *__restrict__ last, const TileSched sc) {
     if (st->code != SDGR_OK) return;
     for_tiles(sc, st, [&](int tile) {
-        intensity_fwd_tile<AM>(tile, st, ranges, vals, comp, views, V, cut, Tfloor, A, Tstop, last);
+        intensity_fwd_tile<AM, NB>(tile, st, ranges, vals, comp, views, V, cut, Tfloor, A, Tstop, last);
     });
 }
 
@@ -400,12 +428,14 @@ cudaError_t launch_intensity_fwd(const uint2 *ranges, const uint32_t *vals, cons
                                  int V, int tiles, float cut, float Tfloor, int alpha_mode, const StatusDev *st,
                                  float *A, float *Tstop, int32_t *last, const TileSched &sched, cudaStream_t s) {
     if (tiles <= 0) return cudaSuccess;
-    if (alpha_mode)
-        k_intensity_fwd<1><<<raster_grid(tiles, sched), TILE_PIX, 0, s>>>(ranges, vals, comp, views, V, cut, Tfloor,
-                                                                          st, A, Tstop, last, sched);
-    else
-        k_intensity_fwd<0><<<raster_grid(tiles, sched), TILE_PIX, 0, s>>>(ranges, vals, comp, views, V, cut, Tfloor,
-                                                                          st, A, Tstop, last, sched);
+    const unsigned grid = raster_grid(tiles, sched);
+    const int v = (alpha_mode ? 2 : 0) + (sched.nb == 512 ? 1 : 0);
+    switch (v) {
+        case 0: k_intensity_fwd<0, 256><<<grid, TILE_PIX, 0, s>>>(ranges, vals, comp, views, V, cut, Tfloor, st, A, Tstop, last, sched); break;
+        case 1: k_intensity_fwd<0, 512><<<grid, TILE_PIX, 0, s>>>(ranges, vals, comp, views, V, cut, Tfloor, st, A, Tstop, last, sched); break;
+        case 2: k_intensity_fwd<1, 256><<<grid, TILE_PIX, 0, s>>>(ranges, vals, comp, views, V, cut, Tfloor, st, A, Tstop, last, sched); break;
+        default: k_intensity_fwd<1, 512><<<grid, TILE_PIX, 0, s>>>(ranges, vals, comp, views, V, cut, Tfloor, st, A, Tstop, last, sched); break;
+    }
     note_launch();
     return cudaGetLastError();
 }
@@ -426,41 +456,47 @@ __device__ __forceinline__ void stage_img(const ImgRec *__restrict__ img, uint32
 // a8: imaging splat.  S[pixel] = sum_i c_i exp(-delta_I/2) I_i, I_i = P_i A_i.
 // Each pixel gathers over its warp's hit list; no reduction is needed.
 // ---------------------------------------------------------------------------
+template <int NB>
 __device__ __forceinline__ void
 splat_fwd_tile(const int tile, const StatusDev *st, const uint2 *__restrict__ rangesI, const uint32_t *__restrict__ vals,
                const ImgRec *__restrict__ img, const CompRec *__restrict__ comp, const float *__restrict__ A,
                const ViewDev *__restrict__ views, int V, float cut, bool ok, float *__restrict__ images) {
-    __shared__ float4 sP[BATCH];  // (qa, qb, qc, l1)
-    __shared__ float4 sQ[BATCH];  // (l2, c0, c I, -)
-    __shared__ uint32_t sM[BATCH];
+    constexpr int PER = NB / 256;  // records staged per thread
+    __shared__ float4 sP[NB];  // (qa, qb, qc, l1)
+    __shared__ float4 sQ[NB];  // (l2, c0, c I, -)
+    __shared__ uint32_t sM[NB];
     const int t = threadIdx.x;
     const TileCtx c = tile_ctx(views, V, tile);
     const LaneXY L = lane_xy();
     const uint2 r = ok ? rangesI[tile] : make_uint2(0u, 0u);
     const float cutm = cut_margin(cut);
     float acc = 0.f;
-    uint32_t vnext = r.x + t < r.y ? vals[r.x + t] : 0u;
-    for (uint32_t base = r.x; base < r.y; base += BATCH) {
+    uint32_t vnext[PER];  // next batch's list entries, loaded one batch ahead
+    unrolled<PER>([&](int u) { vnext[u] = r.x + t + 256 * u < r.y ? vals[r.x + t + 256 * u] : 0u; });
+    for (uint32_t base = r.x; base < r.y; base += NB) {
         __syncthreads();
-        if (base + t < r.y) {
-            const uint32_t vg = vnext;
-            float4 G, P;
-            float2 uv, Q;
-            float cn;
-            uint32_t m;
-            if (vg_ok(st, views[c.v], vg)) {
-                stage_img(img, vg, c, cutm, G, uv, cn, m);
-                poly_coeffs(uv.x, uv.y, G.x, G.y, G.z, P, Q);
-                sP[t] = P;
-                sQ[t] = make_float4(Q.x, Q.y, cn * comp[vg].P * A[vg], 0.f);
-                sM[t] = m;
-            } else {
-                sM[t] = 0;  // checked build: an entry of another view stays inert
+        unrolled<PER>([&](int u) {
+            const int k = t + 256 * u;
+            if (base + k < r.y) {
+                const uint32_t vg = vnext[u];
+                float4 G, P;
+                float2 uv, Q;
+                float cn;
+                uint32_t m;
+                if (vg_ok(st, views[c.v], vg)) {
+                    stage_img(img, vg, c, cutm, G, uv, cn, m);
+                    poly_coeffs(uv.x, uv.y, G.x, G.y, G.z, P, Q);
+                    sP[k] = P;
+                    sQ[k] = make_float4(Q.x, Q.y, cn * comp[vg].P * A[vg], 0.f);
+                    sM[k] = m;
+                } else {
+                    sM[k] = 0;  // checked build: an entry of another view stays inert
+                }
             }
-        }
-        if (base + BATCH + t < r.y) vnext = vals[base + BATCH + t];
+            if (base + NB + k < r.y) vnext[u] = vals[base + NB + k];
+        });
         __syncthreads();
-        const int nb = min(BATCH, (int)(r.y - base));
+        const int nb = min(NB, (int)(r.y - base));
         for (int k0 = 0; k0 < nb; k0 += 32) {
             uint32_t hm = warp_hits(sM, k0, min(32, nb - k0));
             while (hm) {
@@ -483,21 +519,28 @@ splat_fwd_tile(const int tile, const StatusDev *st, const uint2 *__restrict__ ra
 
 // Every pixel is written: with a work list (non-empty tiles only) the caller
 // zeroes the images first.
+template <int NB>
 __global__ void __launch_bounds__(256)
 k_splat_fwd(const uint2 *__restrict__ rangesI, const uint32_t *__restrict__ vals, const ImgRec *__restrict__ img,
             const CompRec *__restrict__ comp, const float *__restrict__ A, const ViewDev *__restrict__ views, int V,
             float cut, const StatusDev *st, float *__restrict__ images, const TileSched sc) {
     const bool ok = st->code == SDGR_OK;
     if (!ok && sc.order) return;
-    for_tiles(sc, st, [&](int tile) { splat_fwd_tile(tile, st, rangesI, vals, img, comp, A, views, V, cut, ok, images); });
+    for_tiles(sc, st,
+              [&](int tile) { splat_fwd_tile<NB>(tile, st, rangesI, vals, img, comp, A, views, V, cut, ok, images); });
 }
 
 cudaError_t launch_splat_fwd(const uint2 *rangesI, const uint32_t *vals, const ImgRec *img, const CompRec *comp,
                              const float *A, const ViewDev *views, int V, int tiles, float cut, const StatusDev *st,
                              float *images, const TileSched &sched, cudaStream_t s) {
     if (tiles <= 0) return cudaSuccess;
-    k_splat_fwd<<<raster_grid(tiles, sched), TILE_PIX, 0, s>>>(rangesI, vals, img, comp, A, views, V, cut, st, images,
-                                                               sched);
+    const unsigned grid = raster_grid(tiles, sched);
+    if (sched.nb == 1024)
+        k_splat_fwd<1024><<<grid, TILE_PIX, 0, s>>>(rangesI, vals, img, comp, A, views, V, cut, st, images, sched);
+    else if (sched.nb == 512)
+        k_splat_fwd<512><<<grid, TILE_PIX, 0, s>>>(rangesI, vals, img, comp, A, views, V, cut, st, images, sched);
+    else
+        k_splat_fwd<256><<<grid, TILE_PIX, 0, s>>>(rangesI, vals, img, comp, A, views, V, cut, st, images, sched);
     note_launch();
     return cudaGetLastError();
 }
@@ -511,15 +554,17 @@ cudaError_t launch_splat_fwd(const uint2 *rangesI, const uint32_t *vals, const I
 // with dL/dS read from shared memory as one float4; the eight partial
 // moments meet in shared memory, one thread per moment adds them.
 // ---------------------------------------------------------------------------
+template <int NB>
 __device__ __forceinline__ void
 splat_bwd_tile(const int tile, const StatusDev *st, const uint2 *__restrict__ rangesI, const uint32_t *__restrict__ vals,
                const ImgRec *__restrict__ img, const float *__restrict__ dLdS, const ViewDev *__restrict__ views, int V,
                float cut, float4 *__restrict__ accI) {
-    __shared__ float4 sG[SBATCH];  // (qa, qb, qc, -)
-    __shared__ float2 sU[SBATCH];  // tile-local centre
-    __shared__ uint32_t sM[SBATCH];
-    __shared__ uint32_t sid[SBATCH];
-    __shared__ uint8_t sperm[SBATCH];
+    constexpr int PER = NB / 256;  // records staged per thread
+    __shared__ float4 sG[NB];  // (qa, qb, qc, -)
+    __shared__ float2 sU[NB];  // tile-local centre
+    __shared__ uint32_t sM[NB];
+    __shared__ uint32_t sid[NB];
+    __shared__ uint8_t sperm[NB];
     __shared__ __align__(16) float sg[TILE_PIX];  // dL/dS of the tile's pixels, in table layout
     __shared__ __align__(16) float zero4[4];
     __shared__ __align__(16) float sred[32 * RSTRIDE];  // moment reduction scratch, one slot per group of 8
@@ -532,13 +577,11 @@ splat_bwd_tile(const int tile, const StatusDev *st, const uint2 *__restrict__ ra
     if (__syncthreads_count(g != 0.f) == 0) return;
     const float cutm = cut_margin(cut);
     const int cc = t & 7;
-    uint32_t vnext[SPER];  // next batch's list entries, loaded one batch ahead
-#pragma unroll
-    for (int u = 0; u < SPER; ++u) vnext[u] = r.x + t + 256 * u < r.y ? vals[r.x + t + 256 * u] : 0u;
-    for (uint32_t base = r.x; base < r.y; base += SBATCH) {
+    uint32_t vnext[PER];  // next batch's list entries, loaded one batch ahead
+    unrolled<PER>([&](int u) { vnext[u] = r.x + t + 256 * u < r.y ? vals[r.x + t + 256 * u] : 0u; });
+    for (uint32_t base = r.x; base < r.y; base += NB) {
         __syncthreads();
-#pragma unroll
-        for (int u = 0; u < SPER; ++u) {
+        unrolled<PER>([&](int u) {
             const int k = t + 256 * u;
             if (base + k < r.y) {
                 const uint32_t vg = vnext[u];
@@ -552,10 +595,10 @@ splat_bwd_tile(const int tile, const StatusDev *st, const uint2 *__restrict__ ra
                 sM[k] = m;
                 sid[k] = vg;
             }
-            if (base + SBATCH + k < r.y) vnext[u] = vals[base + SBATCH + k];
-        }
+            if (base + NB + k < r.y) vnext[u] = vals[base + NB + k];
+        });
         __syncthreads();
-        const int nb = min(SBATCH, (int)(r.y - base));
+        const int nb = min(NB, (int)(r.y - base));
         for (int j0 = warp * 32; j0 < nb; j0 += 256) order_by_blocks(sM, j0, min(32, nb - j0), sperm + j0);
         __syncthreads();
         for (int j0 = 0; j0 < nb; j0 += 32) {
@@ -599,20 +642,26 @@ splat_bwd_tile(const int tile, const StatusDev *st, const uint2 *__restrict__ ra
     }
 }
 
+template <int NB>
 __global__ void __launch_bounds__(256)
 k_splat_bwd(const uint2 *__restrict__ rangesI, const uint32_t *__restrict__ vals, const ImgRec *__restrict__ img,
             const float *__restrict__ dLdS, const ViewDev *__restrict__ views, int V, float cut, const StatusDev *st,
             float4 *__restrict__ accI, const TileSched sc) {
     if (st->code != SDGR_OK) return;
-    for_tiles(sc, st, [&](int tile) { splat_bwd_tile(tile, st, rangesI, vals, img, dLdS, views, V, cut, accI); });
+    for_tiles(sc, st, [&](int tile) { splat_bwd_tile<NB>(tile, st, rangesI, vals, img, dLdS, views, V, cut, accI); });
 }
 
 cudaError_t launch_splat_bwd(const uint2 *rangesI, const uint32_t *vals, const ImgRec *img, const float *dLdS,
                              const ViewDev *views, int V, int tiles, float cut, const StatusDev *st, float4 *accI,
                              const TileSched &sched, cudaStream_t s) {
     if (tiles <= 0) return cudaSuccess;
-    k_splat_bwd<<<raster_grid(tiles, sched), TILE_PIX, 0, s>>>(rangesI, vals, img, dLdS, views, V, cut, st, accI,
-                                                               sched);
+    const unsigned grid = raster_grid(tiles, sched);
+    if (sched.nb == 256)
+        k_splat_bwd<256><<<grid, TILE_PIX, 0, s>>>(rangesI, vals, img, dLdS, views, V, cut, st, accI, sched);
+    else if (sched.nb == 512)
+        k_splat_bwd<512><<<grid, TILE_PIX, 0, s>>>(rangesI, vals, img, dLdS, views, V, cut, st, accI, sched);
+    else
+        k_splat_bwd<1024><<<grid, TILE_PIX, 0, s>>>(rangesI, vals, img, dLdS, views, V, cut, st, accI, sched);
     note_launch();
     return cudaGetLastError();
 }
@@ -834,23 +883,42 @@ cudaError_t launch_intensity_bwd(const uint2 *ranges, const uint32_t *vals, cons
     return cudaGetLastError();
 }
 
-int raster_blocks_per_sm(int kernel) {
-    static int cache[4] = {0, 0, 0, 0};
+int stage_batch_options(int kernel, const int **sizes) {
+    switch (kernel) {
+        case 0: *sizes = kStageK3; return (int)(sizeof(kStageK3) / sizeof(int));
+        case 1: *sizes = kStageK4; return (int)(sizeof(kStageK4) / sizeof(int));
+        case 2: *sizes = kStageK5; return (int)(sizeof(kStageK5) / sizeof(int));
+        case 3: *sizes = kStageK6; return (int)(sizeof(kStageK6) / sizeof(int));
+        default: *sizes = nullptr; return 0;
+    }
+}
+
+// Resident CTAs per SM of raster kernel `kernel` built for staging batch nb
+// (a size stage_batch_options lists); the persistent grid is SMs times this.
+int raster_blocks_per_sm(int kernel, int nb) {
+    static int cache[4][3] = {};
     if (kernel < 0 || kernel > 3) return 1;
-    if (cache[kernel] > 0) return cache[kernel];
+    const int vi = nb == 1024 ? 2 : (nb == 512 ? 1 : 0);
+    if (cache[kernel][vi] > 0) return cache[kernel][vi];
     int n = 0;
     cudaError_t e = cudaErrorInvalidValue;
-    switch (kernel) {
-        case 0: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_intensity_fwd<0>, TILE_PIX, 0); break;
-        case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_splat_fwd, TILE_PIX, 0); break;
-        case 2: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_splat_bwd, TILE_PIX, 0); break;
-        default: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_intensity_bwd<0>, TILE_PIX, 0); break;
+    switch (kernel * 3 + vi) {
+        case 0: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_intensity_fwd<0, 256>, TILE_PIX, 0); break;
+        case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_intensity_fwd<0, 512>, TILE_PIX, 0); break;
+        case 3: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_splat_fwd<256>, TILE_PIX, 0); break;
+        case 4: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_splat_fwd<512>, TILE_PIX, 0); break;
+        case 5: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_splat_fwd<1024>, TILE_PIX, 0); break;
+        case 6: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_splat_bwd<256>, TILE_PIX, 0); break;
+        case 7: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_splat_bwd<512>, TILE_PIX, 0); break;
+        case 8: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_splat_bwd<1024>, TILE_PIX, 0); break;
+        case 9: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_intensity_bwd<0>, TILE_PIX, 0); break;
+        default: break;
     }
     if (e != cudaSuccess || n < 1) {
         (void)cudaGetLastError();
         n = 1;
     }
-    cache[kernel] = n;
+    cache[kernel][vi] = n;
     return n;
 }
 

@@ -94,7 +94,13 @@ struct TileSched {
     int slot;               // item counter used by this launch
     int persistent_grid;    // > 0: persistent launch with this many CTAs
     int ntiles;             // tiles of the plane (bound of every work-list entry)
+    int nb;                 // Gaussian records staged per batch (a supported size of the kernel)
 };
+
+// Staging batch sizes each raster kernel is built for (records per CTA
+// batch): 0 intensity pass, 1 splat, 2 splat adjoint, 3 intensity adjoint.
+// The first entry of each list is the kernel's default.
+int stage_batch_options(int kernel, const int **sizes);
 
 // One segment of a segmented radix sort: items [start, start + len), digits
 // taken from (key - key_base); blk_start = first block of the segment.
@@ -235,7 +241,7 @@ cudaError_t launch_intensity_bwd(const uint2 *ranges, const uint32_t *vals, cons
                                  int V, int tiles, float cut, int alpha_mode, const StatusDev *st, float4 *accC,
                                  const TileSched &sched, cudaStream_t s);
 // CTAs per SM of a raster kernel at 256 threads (occupancy query, cached).
-int raster_blocks_per_sm(int kernel);
+int raster_blocks_per_sm(int kernel, int nb);
 cudaError_t launch_count_pairs(const uint2 *ranges, const uint32_t *vals, const CompRec *comp, const ImgRec *img,
                                const ViewDev *views, int V, int tiles, float cut, StatusDev *st, cudaStream_t s);
 cudaError_t launch_intensity_out(const CompRec *comp, const float *A, int64_t VG, float *I, int sms, cudaStream_t s);

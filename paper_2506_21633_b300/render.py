@@ -53,6 +53,7 @@ class Renderer:
         self.params = None
         self.n_inst = None
         self.schedule = "persistent"
+        self.stage_batch = {}  # raster kernel name -> staging batch (absent: the kernel's default)
 
     def __del__(self):
         try:
@@ -85,6 +86,8 @@ class Renderer:
         if dens is not None:
             L.sdgr_set_densify_stats(self.ws, *dens)
         L.sdgr_set_schedule(self.ws, L.SCHEDULES[self.schedule])
+        for k, nb in self.stage_batch.items():
+            L.sdgr_set_stage_batch(self.ws, k, nb)
 
     def workspace_bytes(self):
         return 0 if self.buf is None else self.buf.numel()
@@ -171,6 +174,24 @@ class Renderer:
         self.schedule = name
         if self.ws is not None:
             L.sdgr_set_schedule(self.ws, L.SCHEDULES[name])
+
+    def set_stage_batch(self, kernel, records):
+        """Gaussian records a CTA of raster kernel `kernel` ('intensity_fwd',
+        'splat_fwd', 'splat_bwd' or 'intensity_bwd') stages per batch; one of
+        L.sdgr_stage_batch_options(kernel), or 0 / None for the default.
+        Applies to the following forward / backward calls; the results do not
+        depend on it."""
+        if kernel not in L.RASTER_KERNELS:
+            raise ValueError(f"unknown raster kernel {kernel!r}")
+        records = int(records or 0)
+        if records and records not in L.sdgr_stage_batch_options(kernel):
+            raise ValueError(f"{kernel} has no staging batch of {records} records")
+        if records:
+            self.stage_batch[kernel] = records
+        else:
+            self.stage_batch.pop(kernel, None)
+        if self.ws is not None:
+            L.sdgr_set_stage_batch(self.ws, kernel, records)
 
     def count_pairs(self, stream=None):
         """In-cutoff (pixel, Gaussian) pairs (computation plane, imaging plane)

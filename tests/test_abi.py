@@ -13,7 +13,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 def _declared():
     src = open(os.path.join(ROOT, "include", "sdgr.h")).read()
-    return sorted(set(re.findall(r"^(?:sdgr_status|const char \*|int64_t|size_t)\s*(sdgr_\w+)\s*\(", src, re.M)))
+    return sorted(set(re.findall(r"^(?:sdgr_status|const char \*|int64_t|int32_t|size_t)\s*(sdgr_\w+)\s*\(", src, re.M)))
 
 
 @pytest.fixture(scope="module")
@@ -82,6 +82,21 @@ def test_host_validation(L):
     assert lib.sdgr_adam_step(ctypes.c_void_p(8), ctypes.c_void_p(16), ctypes.c_void_p(32), ctypes.c_void_p(48), 10,
                               lr, 0.9, 0.999, 1e-8, 1, None) == L.SDGR_ERR_INVALID
     assert lib.sdgr_l1_loss(None, None, 10, None, None, None) == L.SDGR_ERR_INVALID
+    assert lib.sdgr_set_stage_batch(None, 0, 256) == L.SDGR_ERR_INVALID
+
+
+def test_stage_batch_options(L):
+    """Every raster kernel lists its staging batch sizes, the default first:
+    multiples of the 256 threads of a CTA (each thread stages whole records);
+    an unknown kernel has none."""
+    for k, name in enumerate(L.RASTER_KERNELS):
+        opts = L.sdgr_stage_batch_options(name)
+        assert opts and opts == L.sdgr_stage_batch_options(k)
+        assert len(set(opts)) == len(opts)
+        assert all(nb % 256 == 0 and 256 <= nb <= 1024 for nb in opts)
+    assert L.sdgr_stage_batch_options(1) == (256, 512, 1024)
+    assert L.lib().sdgr_stage_batch_options(4, None, 0) == 0
+    assert L.lib().sdgr_stage_batch_options(-1, None, 0) == 0
 
 
 def test_product_does_not_import_oracle():
