@@ -23,7 +23,7 @@
 //
 // Sums over the tile's pixels per Gaussian.  The intensity pass needs only
 // sum_rays alpha T (non-negative, each term <= 1): one redux.sync per hit on
-// 2^-26 fixed point into a 64-bit shared slot.  The intensity adjoint needs
+// 2^-23 fixed point into a 32-bit shared slot.  The intensity adjoint needs
 // six signed moments and uses a two-phase transpose: in phase 1 every pixel
 // writes its weight for each of its hit Gaussians into a 32 x 256 shared-
 // memory table; in phase 2 eight threads per Gaussian read the table's entries
@@ -331,34 +331,47 @@ __device__ __forceinline__ void stage_comp(const CompRec *__restrict__ comp, uin
 // (negated if the ray stopped at the floor) and the transmittance in front of
 // that Gaussian.  The pair update is branch-free: a pair outside the cutoff
 // (or on a stopped ray) gets weight 0, which leaves T unchanged.
+//
+// The ray carries Ts = 2^23 T.  Scaling by a power of two commutes with every
+// rounding here (all values stay normal: T >= 2^-100 before a factor, and a
+// factor 1 - alpha is 0 or >= 2^-24), so Ts / 2^23 has exactly the bits of
+// the unscaled recursion that the adjoint repeats.  With it one FMA gives the
+// pair's fixed-point weight: fma(alpha, Ts, 2^23) lies in [2^23, 2^24], where
+// floats are the integers, so its bit pattern is 0x4B000000 + round(2^23
+// alpha T); the 32 lanes' patterns add up (mod 2^32) to 32 x 0x4B000000 =
+// 0x60000000 (mod 2^32) plus the warp's sum, at most 2^28.
 // ---------------------------------------------------------------------------
+constexpr float S23 = 8388608.f;  // 2^23: scale of the intensity pass's transmittance
+
+// TfloorS: the transmittance floor times 2^23.
 template <int AM, int NB>
 __device__ __forceinline__ void
 intensity_fwd_tile(const int tile, const StatusDev *st, const uint2 *__restrict__ ranges, const uint32_t *__restrict__ vals,
-                   const CompRec *__restrict__ comp, const ViewDev *__restrict__ views, int V, float cut, float Tfloor,
+                   const CompRec *__restrict__ comp, const ViewDev *__restrict__ views, int V, float cut, float TfloorS,
                    float *__restrict__ A, float *__restrict__ Tstop, int32_t *__restrict__ last) {
     constexpr int PER = NB / 256;  // records staged per thread
     __shared__ float4 sP[NB];  // (qa, qb, qc, l1)
     __shared__ float4 sQ[NB];  // (l2, c0, o, -)
     __shared__ uint32_t sM[NB];
     __shared__ uint32_t sid[NB];
-    __shared__ unsigned long long sAcc[NB];  // sum of alpha T over the tile's rays, in units of 2^-26
+    __shared__ uint32_t sAcc[NB];  // sum of alpha T over the tile's 256 rays, in units of 2^-23 (< 2^31)
     const int t = threadIdx.x, lane = t & 31;
     const TileCtx c = tile_ctx(views, V, tile);
     const LaneXY L = lane_xy();
     const uint2 r = ranges[tile];
     const float cutm = cut_margin(cut);
-    float T = c.inside ? 1.f : 0.f, Tprev = 1.f;  // a ray outside the image takes no pair
+    constexpr uint32_t WARP_BIAS = 0x60000000u;  // 32 x bits(2^23), mod 2^32
+    float T = c.inside ? S23 : 0.f, Tprev = S23;  // Ts; a ray outside the image takes no pair
     int32_t lastj = 0;
     int nb = 0;  // Gaussians staged in the current batch
     uint32_t vnext[PER];  // next batch's list entries, loaded one batch ahead
     unrolled<PER>([&](int u) { vnext[u] = r.x + t + 256 * u < r.y ? vals[r.x + t + 256 * u] : 0u; });
     for (uint32_t base = r.x; base < r.y; base += NB) {
-        if (__syncthreads_count(T < Tfloor) == (int)blockDim.x) break;
+        if (__syncthreads_count(T < TfloorS) == (int)blockDim.x) break;
         unrolled<PER>([&](int u) {
             const int k = t + 256 * u;
             // the previous batch's sums: one global atomic per (tile, Gaussian)
-            if (k < nb && sAcc[k] != 0ull) atomicAdd(&A[sid[k]], __ull2float_rn(sAcc[k]) * (1.f / 67108864.f));
+            if (k < nb && sAcc[k] != 0u) atomicAdd(&A[sid[k]], __uint2float_rn(sAcc[k]) * (1.f / S23));
             if (base + k < r.y) {
                 const uint32_t vg = vnext[u];
                 float4 P;
@@ -370,7 +383,7 @@ intensity_fwd_tile(const int tile, const StatusDev *st, const uint2 *__restrict_
                 sM[k] = m;
                 sid[k] = vg;
             }
-            sAcc[k] = 0ull;
+            sAcc[k] = 0u;
             if (base + NB + k < r.y) vnext[u] = vals[base + NB + k];
         });
         __syncthreads();
@@ -384,13 +397,11 @@ intensity_fwd_tile(const int tile, const StatusDev *st, const uint2 *__restrict_
                 const float4 P = sP[sub + jj];
                 const float4 Q = sQ[sub + jj];
                 const float q = poly_q(P, Q.x, Q.y, L);
-                const bool in = (q >= cut) & (T >= Tfloor);
+                const bool in = (q >= cut) & (T >= TfloorS);
                 const float alpha = alpha_of<AM>(Q.z, in ? ex2_approx(q) : 0.f);
-                // the warp's 32 rays summed in fixed point (0 <= alpha T <= 1, so
-                // 32 lanes of 2^26 fit 32 bits): one redux instead of a table
-                const uint32_t fx = __float2uint_rn(__fmul_rn(alpha, T) * 67108864.f);
-                const uint32_t ws = __reduce_add_sync(0xffffffffu, fx);
-                if (lane == 0 && ws != 0u) atomicAdd(&sAcc[sub + jj], (unsigned long long)ws);
+                // the warp's 32 rays summed in fixed point: one redux instead of a table
+                const uint32_t ws = __reduce_add_sync(0xffffffffu, __float_as_uint(__fmaf_rn(alpha, T, S23)));
+                if (lane == 0 && ws != WARP_BIAS) atomicAdd(&sAcc[sub + jj], ws - WARP_BIAS);
                 Tprev = in ? T : Tprev;
                 lastj = in ? kb + jj : lastj;
                 T = __fmul_rn(T, __fsub_rn(1.f, alpha));
@@ -400,22 +411,22 @@ intensity_fwd_tile(const int tile, const StatusDev *st, const uint2 *__restrict_
     __syncthreads();
     unrolled<PER>([&](int u) {
         const int k = t + 256 * u;
-        if (k < nb && sAcc[k] != 0ull) atomicAdd(&A[sid[k]], __ull2float_rn(sAcc[k]) * (1.f / 67108864.f));
+        if (k < nb && sAcc[k] != 0u) atomicAdd(&A[sid[k]], __uint2float_rn(sAcc[k]) * (1.f / S23));
     });
     if (c.inside) {
-        Tstop[c.pix] = Tprev;
-        last[c.pix] = T < Tfloor ? -lastj : lastj;  // negative: the ray stopped at the floor
+        Tstop[c.pix] = Tprev * (1.f / S23);
+        last[c.pix] = T < TfloorS ? -lastj : lastj;  // negative: the ray stopped at the floor
     }
 }
 
 template <int AM, int NB>
 __global__ void __launch_bounds__(256)
 k_intensity_fwd(const uint2 *__restrict__ ranges, const uint32_t *__restrict__ vals, const CompRec *__restrict__ comp,
-                const ViewDev *__restrict__ views, int V, float cut, float Tfloor, const StatusDev *st,
+                const ViewDev *__restrict__ views, int V, float cut, float TfloorS, const StatusDev *st,
                 float *__restrict__ A, float *__restrict__ Tstop, int32_t *__restrict__ last, const TileSched sc) {
     if (st->code != SDGR_OK) return;
     for_tiles(sc, st, [&](int tile) {
-        intensity_fwd_tile<AM, NB>(tile, st, ranges, vals, comp, views, V, cut, Tfloor, A, Tstop, last);
+        intensity_fwd_tile<AM, NB>(tile, st, ranges, vals, comp, views, V, cut, TfloorS, A, Tstop, last);
     });
 }
 
@@ -430,11 +441,12 @@ cudaError_t launch_intensity_fwd(const uint2 *ranges, const uint32_t *vals, cons
     if (tiles <= 0) return cudaSuccess;
     const unsigned grid = raster_grid(tiles, sched);
     const int v = (alpha_mode ? 2 : 0) + (sched.nb == 512 ? 1 : 0);
+    const float TfloorS = Tfloor * S23;  // exact: a power-of-two scale of a normal float
     switch (v) {
-        case 0: k_intensity_fwd<0, 256><<<grid, TILE_PIX, 0, s>>>(ranges, vals, comp, views, V, cut, Tfloor, st, A, Tstop, last, sched); break;
-        case 1: k_intensity_fwd<0, 512><<<grid, TILE_PIX, 0, s>>>(ranges, vals, comp, views, V, cut, Tfloor, st, A, Tstop, last, sched); break;
-        case 2: k_intensity_fwd<1, 256><<<grid, TILE_PIX, 0, s>>>(ranges, vals, comp, views, V, cut, Tfloor, st, A, Tstop, last, sched); break;
-        default: k_intensity_fwd<1, 512><<<grid, TILE_PIX, 0, s>>>(ranges, vals, comp, views, V, cut, Tfloor, st, A, Tstop, last, sched); break;
+        case 0: k_intensity_fwd<0, 256><<<grid, TILE_PIX, 0, s>>>(ranges, vals, comp, views, V, cut, TfloorS, st, A, Tstop, last, sched); break;
+        case 1: k_intensity_fwd<0, 512><<<grid, TILE_PIX, 0, s>>>(ranges, vals, comp, views, V, cut, TfloorS, st, A, Tstop, last, sched); break;
+        case 2: k_intensity_fwd<1, 256><<<grid, TILE_PIX, 0, s>>>(ranges, vals, comp, views, V, cut, TfloorS, st, A, Tstop, last, sched); break;
+        default: k_intensity_fwd<1, 512><<<grid, TILE_PIX, 0, s>>>(ranges, vals, comp, views, V, cut, TfloorS, st, A, Tstop, last, sched); break;
     }
     note_launch();
     return cudaGetLastError();
@@ -699,8 +711,7 @@ intensity_bwd_tile(const int tile, const StatusDev *st, const uint2 *__restrict_
     const LaneXY L = lane_xy();
     const uint2 r = ranges[tile];
     const int32_t rec = c.inside ? last[c.pix] : 0;
-    const int32_t mylast = rec < 0 ? -rec : rec;
-    const bool stopped = rec < 0;
+    const int32_t mylast = rec < 0 ? -rec : rec;  // negative: the ray stopped at the floor there
     float T = c.inside ? Tstop[c.pix] : 0.f;  // 0 outside the image: such a lane adds nothing
     bool first = mylast > 0;  // a ray without in-cutoff pairs never meets one here either
     if (t == 0) smax = 0;
@@ -748,10 +759,12 @@ intensity_bwd_tile(const int tile, const StatusDev *st, const uint2 *__restrict_
             const int ns = send - sub;
             uint32_t hm = warp_hits(sM, sub, ns);
             // fast path: every ray of the warp is past its first in-cutoff
-            // Gaussian and none stopped at the floor -- then every later pair
-            // of the list that is in the cutoff was taken by the forward pass
-            // (no index bound) and T is always rebuilt by division
-            if (__all_sync(0xffffffffu, !first && !stopped)) {
+            // Gaussian (walking back to front: the last pair the forward pass
+            // took, the stopping one on a ray that stopped at the floor) --
+            // then every in-cutoff pair still ahead has a lower list index, so
+            // the forward pass took it (no index bound), and T is always
+            // rebuilt by division
+            if (__all_sync(0xffffffffu, !first)) {
                 while (hm) {
                     // two hits per iteration, back to front (the second may be absent)
                     const int j0 = 31 - __clz(hm);
