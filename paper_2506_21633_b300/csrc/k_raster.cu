@@ -48,12 +48,13 @@ constexpr int WSTRIDE = 264;  // row stride of the weight table (floats)
 // table and phase-2 mapping are built around one record per thread.
 static const int kStageK3[] = {256, 512};
 static const int kStageK4[] = {256, 512, 1024};
-static const int kStageK5[] = {1024, 512, 256};
+static const int kStageK5[] = {512, 1024, 256};
 static const int kStageK6[] = {256};
 
 struct TileCtx {
     int v;
     int x0, y0;  // pixel coordinates of the tile's first pixel
+    float x0f, y0f;  // the same as floats (converted once per tile)
     int px, py;  // this thread's pixel
     bool inside;
     int64_t pix;
@@ -68,6 +69,8 @@ __device__ __forceinline__ TileCtx tile_ctx(const ViewDev *views, int V, int til
     const int lt = tile - vd.tile_off;
     c.x0 = (lt % vd.tiles_x) * TILE;
     c.y0 = (lt / vd.tiles_x) * TILE;
+    c.x0f = (float)c.x0;
+    c.y0f = (float)c.y0;
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
     c.px = c.x0 + 8 * (w & 1) + (l & 7);
     c.py = c.y0 + 4 * (w >> 1) + (l >> 3);
@@ -82,6 +85,11 @@ __device__ __forceinline__ TileCtx tile_ctx(const ViewDev *views, int V, int til
         if (c.x0 + 8 * (b & 1) < vd.NA && c.y0 + 4 * (b >> 1) < vd.NR) c.valid |= 1u << b;
     return c;
 }
+
+// n as a float for 0 <= n < 2^23, exactly: the float with bit pattern
+// 0x4B000000 | n is 2^23 + n.  A logic op and an add in place of a
+// conversion instruction.
+__device__ __forceinline__ float small_u2f(uint32_t n) { return __fsub_rn(__uint_as_float(0x4B000000u | n), 8388608.f); }
 
 // Tile-local pixel coordinates of the thread and their products.
 struct LaneXY {
@@ -123,8 +131,8 @@ __device__ __forceinline__ float poly_q(const float4 &P, float l2, float c0, con
 
 // Tile-local rows [x, y] that the K-ellipse of a Gaussian centred at row uy
 // with bounding-box half-height ry can reach (empty when x > y).
-__device__ __forceinline__ int2 tile_rows(float uy, float ry, int y0) {
-    float lo = ceilf(uy - ry) - (float)y0, hi = floorf(uy + ry) - (float)y0;
+__device__ __forceinline__ int2 tile_rows(float uy, float ry, float y0) {
+    float lo = ceilf(uy - ry) - y0, hi = floorf(uy + ry) - y0;
     lo = fminf(fmaxf(lo, 0.f), 16.f);
     hi = fminf(fmaxf(hi, -1.f), 15.f);
     if (!(lo <= 16.f)) lo = 0.f;  // NaN centre: keep every row, the mask test decides
@@ -317,9 +325,9 @@ __device__ __forceinline__ void stage_comp(const CompRec *__restrict__ comp, uin
     const float4 *cp = reinterpret_cast<const float4 *>(comp + vg);
     const float4 c0 = cp[0], c1 = cp[1];  // (ux, uy, qa, qb), (qc, o, P, ry)
     oP = make_float2(c1.y, c1.z);
-    const float u = __fsub_rn(c0.x, (float)c.x0), v = __fsub_rn(c0.y, (float)c.y0);
+    const float u = __fsub_rn(c0.x, c.x0f), v = __fsub_rn(c0.y, c.y0f);
     poly_coeffs(u, v, c0.z, c0.w, c1.x, P, Q);
-    mask = block_mask(u, v, c0.z, c0.w, c1.x, cutm, tile_rows(c0.y, c1.w, c.y0)) & c.valid;
+    mask = block_mask(u, v, c0.z, c0.w, c1.x, cutm, tile_rows(c0.y, c1.w, c.y0f)) & c.valid;
     uv = make_float2(u, v);
 }
 
@@ -457,11 +465,11 @@ __device__ __forceinline__ void stage_img(const ImgRec *__restrict__ img, uint32
                                           float4 &G, float2 &uv, float &cn, uint32_t &mask) {
     const float4 *ip = reinterpret_cast<const float4 *>(img + vg);
     const float4 i0 = ip[0], i1 = ip[1];  // (ux, uy, qa, qb), (qc, cn, ry, -)
-    const float u = __fsub_rn(i0.x, (float)c.x0), v = __fsub_rn(i0.y, (float)c.y0);
+    const float u = __fsub_rn(i0.x, c.x0f), v = __fsub_rn(i0.y, c.y0f);
     G = make_float4(i0.z, i0.w, i1.x, 0.f);
     uv = make_float2(u, v);
     cn = i1.y;
-    mask = block_mask(u, v, i0.z, i0.w, i1.x, cutm, tile_rows(i0.y, i1.z, c.y0)) & c.valid;
+    mask = block_mask(u, v, i0.z, i0.w, i1.x, cutm, tile_rows(i0.y, i1.z, c.y0f)) & c.valid;
 }
 
 // ---------------------------------------------------------------------------
@@ -629,7 +637,7 @@ splat_bwd_tile(const int tile, const StatusDev *st, const uint2 *__restrict__ ra
                     const float *src = mb ? sg + 32 * b + 4 * cc : zero4;  // no block left: dL/dS = 0
                     mb &= mb - 1;
                     const float dx = (b & 1) ? dx1 : dx0;
-                    const float dy0 = fmaf(4.f, (float)(b >> 1), dy00);
+                    const float dy0 = fmaf(4.f, small_u2f((uint32_t)b >> 1), dy00);
                     const float4 g4 = *reinterpret_cast<const float4 *>(src);
                     // exponent along the column: qa dx^2 + (qb dx) dy + qc dy^2
                     const float Aq = G.x * dx * dx, Bq = G.y * dx;
@@ -857,7 +865,7 @@ intensity_bwd_tile(const int tile, const StatusDev *st, const uint2 *__restrict_
                 const float *src = mb ? wr + 32 * b : zero4;
                 mb &= mb - 1;
                 const float4 w4 = *reinterpret_cast<const float4 *>(src);
-                block_moments(w4, (b & 1) ? dx1 : dx0, fmaf(4.f, (float)(b >> 1), dy00), m);
+                block_moments(w4, (b & 1) ? dx1 : dx0, fmaf(4.f, small_u2f((uint32_t)b >> 1), dy00), m);
             }
             // the group's table row is free after the reads above: scratch, at
             // an offset that puts the four groups of the warp on disjoint banks
