@@ -399,6 +399,11 @@ intensity_fwd_tile(const int tile, const StatusDev *st, const uint2 *__restrict_
         for (int sub = 0; sub < nb; sub += 32) {
             uint32_t hm = warp_hits(sM, sub, min(32, nb - sub));
             const int32_t kb = (int32_t)(base + sub + 1);
+            // the warp's 32 rays are summed in fixed point by one redux per hit;
+            // lane j keeps the warp's sum for staged Gaussian sub + j, which goes
+            // to shared memory once per 32 staged Gaussians (no branch and no
+            // atomic in the hit loop: 10 % of the pass's time)
+            uint32_t mine = 0u;
             while (hm) {
                 const int jj = __ffs(hm) - 1;
                 hm &= hm - 1;
@@ -407,13 +412,13 @@ intensity_fwd_tile(const int tile, const StatusDev *st, const uint2 *__restrict_
                 const float q = poly_q(P, Q.x, Q.y, L);
                 const bool in = (q >= cut) & (T >= TfloorS);
                 const float alpha = alpha_of<AM>(Q.z, in ? ex2_approx(q) : 0.f);
-                // the warp's 32 rays summed in fixed point: one redux instead of a table
                 const uint32_t ws = __reduce_add_sync(0xffffffffu, __float_as_uint(__fmaf_rn(alpha, T, S23)));
-                if (lane == 0 && ws != WARP_BIAS) atomicAdd(&sAcc[sub + jj], ws - WARP_BIAS);
+                mine = lane == jj ? ws - WARP_BIAS : mine;
                 Tprev = in ? T : Tprev;
                 lastj = in ? kb + jj : lastj;
                 T = __fmul_rn(T, __fsub_rn(1.f, alpha));
             }
+            if (mine != 0u) atomicAdd(&sAcc[sub + lane], mine);
         }
     }
     __syncthreads();
