@@ -46,7 +46,7 @@ constexpr int WSTRIDE = 264;  // row stride of the weight table (floats)
 // less shared memory (more resident CTAs) and less staging past the point
 // where every ray of a tile has stopped.  The intensity adjoint's weight
 // table and phase-2 mapping are built around one record per thread.
-static const int kStageK3[] = {256, 512};
+static const int kStageK3[] = {512, 256};
 static const int kStageK4[] = {256, 512, 1024};
 static const int kStageK5[] = {512, 1024, 256};
 static const int kStageK6[] = {256};
@@ -432,8 +432,11 @@ intensity_fwd_tile(const int tile, const StatusDev *st, const uint2 *__restrict_
     }
 }
 
+// The 512-record build is held to five resident CTAs per SM (48 registers;
+// unbounded it takes 59 and loses a CTA), where it is 1 % faster than the
+// 256-record build; that one is left unbounded (minimum 0).
 template <int AM, int NB>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, NB == 512 ? 5 : 0)
 k_intensity_fwd(const uint2 *__restrict__ ranges, const uint32_t *__restrict__ vals, const CompRec *__restrict__ comp,
                 const ViewDev *__restrict__ views, int V, float cut, float TfloorS, const StatusDev *st,
                 float *__restrict__ A, float *__restrict__ Tstop, int32_t *__restrict__ last, const TileSched sc) {
