@@ -203,6 +203,22 @@ __device__ __forceinline__ void block_moments(const float4 &w, float dx, float d
     m[5] += pyy;
 }
 
+// Block list of an 8-bit block set m: the indices of its set bits in
+// increasing order, four bits each (the i-th in bits 4i .. 4i + 3).  Built
+// once per CTA into a 256-entry shared table, so that a phase-2 loop walks a
+// Gaussian's blocks with a shift and a mask per block.
+__device__ __forceinline__ uint32_t block_list(uint32_t m) {
+    uint32_t l = 0u;
+    int n = 0;
+#pragma unroll
+    for (int b = 0; b < 8; ++b)
+        if ((m >> b) & 1u) {
+            l |= (uint32_t)b << (4 * n);
+            ++n;
+        }
+    return l;
+}
+
 // Sum of the six moments over a group of eight threads (cc = 0..7) and one
 // atomic per moment: each thread stores its partial moments into `scr` (48
 // floats owned by the group, moment-major), then thread cc < 6 adds the eight
@@ -586,7 +602,7 @@ template <int NB>
 __device__ __forceinline__ void
 splat_bwd_tile(const int tile, const StatusDev *st, const uint2 *__restrict__ rangesI, const uint32_t *__restrict__ vals,
                const ImgRec *__restrict__ img, const float *__restrict__ dLdS, const ViewDev *__restrict__ views, int V,
-               float cut, float4 *__restrict__ accI) {
+               float cut, float4 *__restrict__ accI, const uint32_t *sBL) {
     constexpr int PER = NB / 256;  // records staged per thread
     __shared__ float4 sG[NB];  // (qa, qb, qc, -)
     __shared__ float2 sU[NB];  // tile-local centre
@@ -632,18 +648,20 @@ splat_bwd_tile(const int tile, const StatusDev *st, const uint2 *__restrict__ ra
         for (int j0 = 0; j0 < nb; j0 += 32) {
             const int k = j0 + sperm[j0 + (t >> 3)];
             const int ks = k < nb ? k : j0;
-            uint32_t mb = k < nb ? sM[k] : 0u;
+            const uint32_t mb = k < nb ? sM[k] : 0u;
+            uint32_t bl = sBL[mb];
+            const int cnt = __popc(mb);
             const float4 G = sG[ks];
             const float2 uv = sU[ks];
             const float dx0 = (float)cc - uv.x, dy00 = -uv.y;
             float m[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
             const float dx1 = dx0 + 8.f;
-            const int rounds = __reduce_max_sync(0xffffffffu, __popc(mb));
+            const int rounds = __reduce_max_sync(0xffffffffu, cnt);
             for (int i = 0; i < rounds; ++i) {
                 {
-                    const int b = mb ? __ffs(mb) - 1 : 0;
-                    const float *src = mb ? sg + 32 * b + 4 * cc : zero4;  // no block left: dL/dS = 0
-                    mb &= mb - 1;
+                    const int b = (int)(bl & 7u);
+                    bl >>= 4;
+                    const float *src = i < cnt ? sg + 32 * b + 4 * cc : zero4;  // no block left: dL/dS = 0
                     const float dx = (b & 1) ? dx1 : dx0;
                     const float dy0 = fmaf(4.f, small_u2f((uint32_t)b >> 1), dy00);
                     const float4 g4 = *reinterpret_cast<const float4 *>(src);
@@ -676,7 +694,11 @@ k_splat_bwd(const uint2 *__restrict__ rangesI, const uint32_t *__restrict__ vals
             const float *__restrict__ dLdS, const ViewDev *__restrict__ views, int V, float cut, const StatusDev *st,
             float4 *__restrict__ accI, const TileSched sc) {
     if (st->code != SDGR_OK) return;
-    for_tiles(sc, st, [&](int tile) { splat_bwd_tile<NB>(tile, st, rangesI, vals, img, dLdS, views, V, cut, accI); });
+    __shared__ uint32_t sBL[256];
+    sBL[threadIdx.x] = block_list(threadIdx.x);
+    __syncthreads();
+    for_tiles(sc, st,
+              [&](int tile) { splat_bwd_tile<NB>(tile, st, rangesI, vals, img, dLdS, views, V, cut, accI, sBL); });
 }
 
 cudaError_t launch_splat_bwd(const uint2 *rangesI, const uint32_t *vals, const ImgRec *img, const float *dLdS,
@@ -711,7 +733,7 @@ __device__ __forceinline__ void
 intensity_bwd_tile(const int tile, const StatusDev *st, const uint2 *__restrict__ ranges, const uint32_t *__restrict__ vals,
                    const CompRec *__restrict__ comp, const ImgRec *__restrict__ img, const float4 *__restrict__ accI,
                    const float *__restrict__ Tstop, const int32_t *__restrict__ last,
-                   const ViewDev *__restrict__ views, int V, float cut, float4 *__restrict__ accC) {
+                   const ViewDev *__restrict__ views, int V, float cut, float4 *__restrict__ accC, const uint32_t *sBL) {
     __shared__ float4 sP[BATCH];  // (qa, qb, qc, l1)
     __shared__ float4 sQ[BATCH];  // (l2, c0, o, chat)
     __shared__ float2 sU[BATCH];  // tile-local centre
@@ -861,17 +883,19 @@ intensity_bwd_tile(const int tile, const StatusDev *st, const uint2 *__restrict_
             }
             __syncthreads();
             const int j = sperm[sl * SUB + (t >> 3)], cc = t & 7;
-            uint32_t mb = j < ns ? sM[sub + j] : 0u;
+            const uint32_t mb = j < ns ? sM[sub + j] : 0u;
+            uint32_t bl = sBL[mb];
+            const int cnt = __popc(mb);
             const float2 uv = sU[sub + (j < ns ? j : 0)];
             const float dx0 = (float)cc - uv.x, dy00 = -uv.y;
             const float *wr = W + j * WSTRIDE + 4 * cc;
             float m[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
             const float dx1 = dx0 + 8.f;
-            const int rounds = __reduce_max_sync(0xffffffffu, __popc(mb));
+            const int rounds = __reduce_max_sync(0xffffffffu, cnt);
             for (int i = 0; i < rounds; ++i) {
-                const int b = mb ? __ffs(mb) - 1 : 0;
-                const float *src = mb ? wr + 32 * b : zero4;
-                mb &= mb - 1;
+                const int b = (int)(bl & 7u);
+                bl >>= 4;
+                const float *src = i < cnt ? wr + 32 * b : zero4;
                 const float4 w4 = *reinterpret_cast<const float4 *>(src);
                 block_moments(w4, (b & 1) ? dx1 : dx0, fmaf(4.f, small_u2f((uint32_t)b >> 1), dy00), m);
             }
@@ -892,8 +916,11 @@ k_intensity_bwd(const uint2 *__restrict__ ranges, const uint32_t *__restrict__ v
                 const int32_t *__restrict__ last, const ViewDev *__restrict__ views, int V, float cut,
                 const StatusDev *st, float4 *__restrict__ accC, const TileSched sc) {
     if (st->code != SDGR_OK) return;
+    __shared__ uint32_t sBL[256];
+    sBL[threadIdx.x] = block_list(threadIdx.x);
+    __syncthreads();
     for_tiles(sc, st, [&](int tile) {
-        intensity_bwd_tile<AM>(tile, st, ranges, vals, comp, img, accI, Tstop, last, views, V, cut, accC);
+        intensity_bwd_tile<AM>(tile, st, ranges, vals, comp, img, accI, Tstop, last, views, V, cut, accC, sBL);
     });
 }
 

@@ -141,16 +141,19 @@ cudaError_t launch_scan_u64(const unsigned long long *in, unsigned long long *ou
 // exclusive scan yields every output position.  The digit of an item is
 // taken from (key - key_base of its segment).
 //
-// Block-local ranking is stable and warp-private: warp w ranks items
-// [512 w, 512 w + 512) of the block with __match_any_sync against its own
-// per-digit counters, then one block-wide pass turns the per-(warp, digit)
-// counts into offsets.  Items are reordered in shared memory and written out
-// coalesced.
+// Block-local ranking is stable and warp-private: warp w loads items
+// [256 w, 256 w + 256) of the block into registers (eight coalesced rounds of
+// 32) and ranks them with __match_any_sync against its own per-digit
+// counters, then one block-wide pass turns the per-(warp, digit) counts into
+// offsets.  Items are reordered in shared memory (16 KB a block) and written
+// out coalesced.  The scatter is held to five resident blocks per SM: with
+// more warps in flight it moves its bytes faster than the unbounded build
+// (64 registers, four blocks), although the bound costs a few spilled words.
 // ---------------------------------------------------------------------------
 constexpr int SORT_WARPS = SORT_THREADS / 32;
-constexpr int SORT_PER_WARP = SORT_IPB / SORT_WARPS;       // 512
-constexpr int SORT_ROUNDS = SORT_PER_WARP / 32;            // 16
-constexpr size_t SORT_SMEM = 4 * SORT_IPB * sizeof(uint32_t);
+constexpr int SORT_PER_WARP = SORT_IPB / SORT_WARPS;
+constexpr int SORT_ROUNDS = SORT_PER_WARP / 32;
+constexpr size_t SORT_SMEM = 2 * SORT_IPB * sizeof(uint32_t);
 
 __device__ __forceinline__ int seg_of_block(const SegDev *segs, int nseg, int b) {
     return upper_index(nseg + 1, b, [&](int k) { return (int64_t)segs[k].blk_start; });
@@ -197,22 +200,26 @@ k_radix_hist(const uint32_t *__restrict__ keys, int shift, const SegDev *__restr
 }
 
 template <int BITS>
-__global__ void __launch_bounds__(SORT_THREADS)
+__global__ void __launch_bounds__(SORT_THREADS, 5)
 k_radix_scatter(const uint32_t *__restrict__ kin, const uint32_t *__restrict__ vin, uint32_t *__restrict__ kout,
                 uint32_t *__restrict__ vout, int shift, const SegDev *__restrict__ segs, int nseg,
                 const uint32_t *__restrict__ hscan) {
     constexpr int RADIX = 1 << BITS;  // digit values of this pass
     extern __shared__ uint32_t sm[];
-    uint32_t *sk = sm, *sv = sm + SORT_IPB, *ok = sm + 2 * SORT_IPB, *ov = sm + 3 * SORT_IPB;
+    uint32_t *ok = sm, *ov = sm + SORT_IPB;
     __shared__ uint32_t wcnt[SORT_WARPS][RADIX];
     __shared__ uint32_t dstart[RADIX], gbase[RADIX];
     BlockSeg bs;
     if (!block_seg(segs, nseg, blockIdx.x, bs, RADIX)) return;
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const uint32_t n = bs.count;
-    for (uint32_t i = t; i < n; i += SORT_THREADS) {
-        sk[i] = kin[bs.start + i];
-        sv[i] = vin[bs.start + i];
+    // this warp's items in registers (round r, lane l: item SORT_PER_WARP w + 32 r + l)
+    uint32_t rk[SORT_ROUNDS], rv[SORT_ROUNDS];
+#pragma unroll
+    for (int r = 0; r < SORT_ROUNDS; ++r) {
+        const uint32_t i = (uint32_t)(warp * SORT_PER_WARP + r * 32 + lane);
+        rk[r] = i < n ? kin[bs.start + i] : 0u;
+        rv[r] = i < n ? vin[bs.start + i] : 0u;
     }
     for (int d = t; d < RADIX; d += SORT_THREADS) {
 #pragma unroll
@@ -226,7 +233,7 @@ k_radix_scatter(const uint32_t *__restrict__ kin, const uint32_t *__restrict__ v
     for (int r = 0; r < SORT_ROUNDS; ++r) {
         const uint32_t i = (uint32_t)(warp * SORT_PER_WARP + r * 32 + lane);
         const bool valid = i < n;
-        const uint32_t d = valid ? (((sk[i] - bs.key_base) >> shift) & (RADIX - 1)) : (uint32_t)RADIX;
+        const uint32_t d = valid ? (((rk[r] - bs.key_base) >> shift) & (RADIX - 1)) : (uint32_t)RADIX;
         const unsigned peers = __match_any_sync(0xffffffffu, d);
         const bool leader = (__ffs(peers) - 1) == lane;
         lr[r] = (valid ? wcnt[warp][d] : 0u) + (uint32_t)__popc(peers & lt_mask);
@@ -257,11 +264,11 @@ k_radix_scatter(const uint32_t *__restrict__ kin, const uint32_t *__restrict__ v
     for (int r = 0; r < SORT_ROUNDS; ++r) {
         const uint32_t i = (uint32_t)(warp * SORT_PER_WARP + r * 32 + lane);
         if (i < n) {
-            const uint32_t k = sk[i];
+            const uint32_t k = rk[r];
             const uint32_t d = ((k - bs.key_base) >> shift) & (RADIX - 1);
             const uint32_t pos = dstart[d] + wcnt[warp][d] + lr[r];
             ok[pos] = k;
-            ov[pos] = sv[i];
+            ov[pos] = rv[r];
         }
     }
     __syncthreads();

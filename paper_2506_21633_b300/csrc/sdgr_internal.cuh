@@ -13,7 +13,7 @@ constexpr int TILE = 16;         // tile edge (pixels); one CTA per tile
 constexpr int TILE_PIX = TILE * TILE;
 constexpr int RADIX_BITS = 8;
 constexpr int RADIX = 1 << RADIX_BITS;
-constexpr int SORT_IPB = 4096;   // items per radix-sort block
+constexpr int SORT_IPB = 2048;   // items per radix-sort block
 constexpr int SORT_THREADS = 256;
 constexpr int SCAN_IPB = 4096;   // items per scan block
 constexpr int SCAN_THREADS = 256;
