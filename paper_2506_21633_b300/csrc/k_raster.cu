@@ -15,7 +15,10 @@
 // exact horizontal extent over each band of four rows).  A warp walks only
 // the Gaussians whose set holds its block: per 32 staged Gaussians one ballot
 // gives the warp its hit list, which it visits in list order (front to back
-// for the intensity pass, back to front for its adjoint).
+// for the intensity pass, back to front for its adjoint).  The intensity pass
+// and its adjoint first write the list out as byte indices (one popc per lane)
+// and walk that: a shared load per hit instead of a bit scan and a mask
+// update (-7 % and -5 % of their time).
 //
 // Exponent: in a tile, a pixel's exponent of Gaussian i is a quadratic in the
 // pixel's tile-local coordinates (X, Y); the six coefficients are formed when
@@ -46,7 +49,7 @@ constexpr int WSTRIDE = 264;  // row stride of the weight table (floats)
 // less shared memory (more resident CTAs) and less staging past the point
 // where every ray of a tile has stopped.  The intensity adjoint's weight
 // table and phase-2 mapping are built around one record per thread.
-static const int kStageK3[] = {512, 256};
+static const int kStageK3[] = {256, 512};
 static const int kStageK4[] = {256, 512, 1024};
 static const int kStageK5[] = {512, 1024, 256};
 static const int kStageK6[] = {256};
@@ -379,7 +382,10 @@ intensity_fwd_tile(const int tile, const StatusDev *st, const uint2 *__restrict_
     __shared__ uint32_t sM[NB];
     __shared__ uint32_t sid[NB];
     __shared__ uint32_t sAcc[NB];  // sum of alpha T over the tile's 256 rays, in units of 2^-23 (< 2^31)
+    __shared__ uint8_t sHL[8 * 32];  // per warp: its hit list of the current slice
     const int t = threadIdx.x, lane = t & 31;
+    uint8_t *const wl = sHL + 32 * (t >> 5);
+    int nh = 0;
     const TileCtx c = tile_ctx(views, V, tile);
     const LaneXY L = lane_xy();
     const uint2 r = ranges[tile];
@@ -413,16 +419,22 @@ intensity_fwd_tile(const int tile, const StatusDev *st, const uint2 *__restrict_
         __syncthreads();
         nb = min(NB, (int)(r.y - base));
         for (int sub = 0; sub < nb; sub += 32) {
-            uint32_t hm = warp_hits(sM, sub, min(32, nb - sub));
+            // this warp's hits as staged indices, in list order
+            {
+                const uint32_t hm = warp_hits(sM, sub, min(32, nb - sub));
+                __syncwarp();  // every lane has read the previous slice's list
+                if ((hm >> lane) & 1u) wl[__popc(hm & ((1u << lane) - 1u))] = (uint8_t)lane;
+                nh = __popc(hm);
+                __syncwarp();
+            }
             const int32_t kb = (int32_t)(base + sub + 1);
             // the warp's 32 rays are summed in fixed point by one redux per hit;
             // lane j keeps the warp's sum for staged Gaussian sub + j, which goes
             // to shared memory once per 32 staged Gaussians (no branch and no
             // atomic in the hit loop: 10 % of the pass's time)
             uint32_t mine = 0u;
-            while (hm) {
-                const int jj = __ffs(hm) - 1;
-                hm &= hm - 1;
+            for (int i = 0; i < nh; ++i) {
+                const int jj = wl[i];
                 const float4 P = sP[sub + jj];
                 const float4 Q = sQ[sub + jj];
                 const float q = poly_q(P, Q.x, Q.y, L);
@@ -449,8 +461,9 @@ intensity_fwd_tile(const int tile, const StatusDev *st, const uint2 *__restrict_
 }
 
 // The 512-record build is held to five resident CTAs per SM (48 registers;
-// unbounded it takes 59 and loses a CTA), where it is 1 % faster than the
-// 256-record build; that one is left unbounded (minimum 0).
+// unbounded it takes 59 and loses a CTA); the 256-record build is left
+// unbounded (minimum 0).  Which one is faster depends on the hit loop: the
+// tuner decides.
 template <int AM, int NB>
 __global__ void __launch_bounds__(256, NB == 512 ? 5 : 0)
 k_intensity_fwd(const uint2 *__restrict__ ranges, const uint32_t *__restrict__ vals, const CompRec *__restrict__ comp,
@@ -742,8 +755,11 @@ intensity_bwd_tile(const int tile, const StatusDev *st, const uint2 *__restrict_
     __shared__ uint8_t sperm[BATCH];
     __shared__ __align__(16) float W[SUB * WSTRIDE];
     __shared__ __align__(16) float zero4[4];
+    __shared__ __align__(4) uint8_t sHL[8 * 32];  // per warp: its hit list of the current slice
     __shared__ int smax;
-    const int t = threadIdx.x, warp = t >> 5;
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    uint8_t *const wl = sHL + 32 * warp;
+    int nh = 0;
     if (t < 4) zero4[t] = 0.f;
     const TileCtx c = tile_ctx(views, V, tile);
     const LaneXY L = lane_xy();
@@ -795,7 +811,13 @@ intensity_bwd_tile(const int tile, const StatusDev *st, const uint2 *__restrict_
         for (int sl = 0; sl * SUB < nb; ++sl) {
             const int send = nb - sl * SUB, sub = max(0, send - SUB);
             const int ns = send - sub;
-            uint32_t hm = warp_hits(sM, sub, ns);
+            // this warp's hits as staged indices, back to front (descending)
+            {
+                const uint32_t hm = warp_hits(sM, sub, ns);
+                if ((hm >> lane) & 1u) wl[__popc(hm >> lane) - 1] = (uint8_t)lane;
+                nh = __popc(hm);
+                __syncwarp();
+            }
             // fast path: every ray of the warp is past its first in-cutoff
             // Gaussian (walking back to front: the last pair the forward pass
             // took, the stopping one on a ray that stopped at the floor) --
@@ -803,13 +825,12 @@ intensity_bwd_tile(const int tile, const StatusDev *st, const uint2 *__restrict_
             // the forward pass took it (no index bound), and T is always
             // rebuilt by division
             if (__all_sync(0xffffffffu, !first)) {
-                while (hm) {
+                for (int i = 0; i < nh; i += 2) {
                     // two hits per iteration, back to front (the second may be absent)
-                    const int j0 = 31 - __clz(hm);
-                    hm ^= 1u << j0;
-                    const bool two = hm != 0u;
-                    const int j1 = two ? 31 - __clz(hm) : j0;
-                    if (two) hm ^= 1u << j1;
+                    const uint32_t pr = *reinterpret_cast<const uint16_t *>(wl + i);
+                    const int j0 = (int)(pr & 0xffu);
+                    const bool two = i + 1 < nh;
+                    const int j1 = two ? (int)(pr >> 8) : j0;
                     const float4 P0 = sP[sub + j0], Q0 = sQ[sub + j0];
                     const float4 P1 = sP[sub + j1], Q1 = sQ[sub + j1];
                     const float q0 = poly_q(P0, Q0.x, Q0.y, L);
@@ -841,13 +862,12 @@ intensity_bwd_tile(const int tile, const StatusDev *st, const uint2 *__restrict_
                     }
                 }
             } else {
-                while (hm) {
+                for (int i = 0; i < nh; i += 2) {
                     // two hits per iteration, back to front (the second may be absent)
-                    const int j0 = 31 - __clz(hm);
-                    hm ^= 1u << j0;
-                    const bool two = hm != 0u;
-                    const int j1 = two ? 31 - __clz(hm) : j0;
-                    if (two) hm ^= 1u << j1;
+                    const uint32_t pr = *reinterpret_cast<const uint16_t *>(wl + i);
+                    const int j0 = (int)(pr & 0xffu);
+                    const bool two = i + 1 < nh;
+                    const int j1 = two ? (int)(pr >> 8) : j0;
                     const float4 P0 = sP[sub + j0], Q0 = sQ[sub + j0];
                     const float4 P1 = sP[sub + j1], Q1 = sQ[sub + j1];
                     const float q0 = poly_q(P0, Q0.x, Q0.y, L);
