@@ -665,6 +665,7 @@ splat_bwd_tile(const int tile, const StatusDev *st, const uint2 *__restrict__ ra
             uint32_t bl = sBL[mb];
             const int cnt = __popc(mb);
             const float4 G = sG[ks];
+            const float qc2 = 2.f * G.z;
             const float2 uv = sU[ks];
             const float dx0 = (float)cc - uv.x, dy00 = -uv.y;
             float m[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
@@ -678,20 +679,21 @@ splat_bwd_tile(const int tile, const StatusDev *st, const uint2 *__restrict__ ra
                     const float dx = (b & 1) ? dx1 : dx0;
                     const float dy0 = fmaf(4.f, small_u2f((uint32_t)b >> 1), dy00);
                     const float4 g4 = *reinterpret_cast<const float4 *>(src);
-                    // exponent along the column: qa dx^2 + (qb dx) dy + qc dy^2
+                    // exponent along the column: qa dx^2 + (qb dx) dy + qc dy^2 at the
+                    // first row, then by differences: from row dy to dy + 1 it grows
+                    // by qb dx + qc (2 dy + 1), which grows by 2 qc per row
                     const float Aq = G.x * dx * dx, Bq = G.y * dx;
                     float4 w;
-                    float dy = dy0, q;
-                    q = fmaf(fmaf(G.z, dy, Bq), dy, Aq);
+                    float q = fmaf(fmaf(G.z, dy0, Bq), dy0, Aq);
+                    float dq = fmaf(qc2, dy0, G.z + Bq);
                     w.x = q >= cut ? g4.x * ex2_approx(q) : 0.f;
-                    dy += 1.f;
-                    q = fmaf(fmaf(G.z, dy, Bq), dy, Aq);
+                    q += dq;
+                    dq += qc2;
                     w.y = q >= cut ? g4.y * ex2_approx(q) : 0.f;
-                    dy += 1.f;
-                    q = fmaf(fmaf(G.z, dy, Bq), dy, Aq);
+                    q += dq;
+                    dq += qc2;
                     w.z = q >= cut ? g4.z * ex2_approx(q) : 0.f;
-                    dy += 1.f;
-                    q = fmaf(fmaf(G.z, dy, Bq), dy, Aq);
+                    q += dq;
                     w.w = q >= cut ? g4.w * ex2_approx(q) : 0.f;
                     block_moments(w, dx, dy0, m);
                 }
