@@ -240,6 +240,16 @@ sdgr_status sdgr_set_schedule(sdgr_ws *ws, int32_t mode);
  * restores the default.  Errors: SDGR_ERR_INVALID (NULL ws, unknown kernel,
  * unsupported size). */
 int32_t sdgr_stage_batch_options(int32_t kernel, int32_t *sizes, int32_t max_sizes);
+
+/* Device self-check of the approximate instructions whose exact values the
+ * kernels rely on.  Writes (asynchronously, on `stream`) a bit mask to the
+ * caller's device word *flags: bit 0 set when rcp.approx(1.0f) is exactly
+ * 1.0f (the intensity adjoint divides the transmittance by 1 - alpha = 1 for
+ * the pairs outside the cutoff, and must leave its bits unchanged).  Every
+ * defined bit is set on a correct device (SDGR_SELFCHECK_ALL).  Errors:
+ * SDGR_ERR_INVALID (NULL or misaligned flags), SDGR_ERR_CUDA (launch). */
+#define SDGR_SELFCHECK_ALL 1u
+sdgr_status sdgr_device_selfcheck(uint32_t *flags, void *stream);
 sdgr_status sdgr_set_stage_batch(sdgr_ws *ws, int32_t kernel, int32_t records);
 
 /* Densification and pruning (the "Densification and Pruning Operation" of

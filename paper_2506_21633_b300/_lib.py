@@ -25,8 +25,10 @@ EXPORTS = (
     "sdgr_count_pairs", "sdgr_launch_count", "sdgr_render_fwd_noalloc", "sdgr_adam_step_device",
     "sdgr_copy_status_async", "sdgr_set_sh", "sdgr_set_densify_stats", "sdgr_densify_scratch_bytes",
     "sdgr_densify", "sdgr_set_schedule", "sdgr_adam_step_flat", "sdgr_stage_batch_options",
-    "sdgr_set_stage_batch",
+    "sdgr_set_stage_batch", "sdgr_device_selfcheck",
 )
+
+SELFCHECK_ALL = 1  # every bit sdgr_device_selfcheck defines
 
 SCHED_ORDERED = 1
 SCHED_PERSISTENT = 2
@@ -112,6 +114,7 @@ def lib():
         L.sdgr_stage_batch_options.argtypes = [i32, P(ctypes.c_int32), i32]
         L.sdgr_stage_batch_options.restype = i32
         L.sdgr_set_stage_batch.argtypes = [vp, i32, i32]
+        L.sdgr_device_selfcheck.argtypes = [vp, vp]
         L.sdgr_densify_scratch_bytes.argtypes = [i64]
         L.sdgr_densify.argtypes = [vp, vp, vp, vp, vp, vp, vp, i64, P(SdgrDensifyCfg), vp, vp, vp, vp, i64, vp,
                                    P(ctypes.c_int64), vp]
@@ -263,6 +266,12 @@ def sdgr_stage_batch_options(kernel):
 def sdgr_set_stage_batch(ws, kernel, records):
     k = RASTER_KERNELS.index(kernel) if isinstance(kernel, str) else int(kernel)
     _check("sdgr_set_stage_batch", lib().sdgr_set_stage_batch(ws, k, int(records)))
+
+
+def sdgr_device_selfcheck(flags_ptr, stream=None):
+    """Enqueue the device self-check; it writes its bit mask to the device
+    word at flags_ptr (uint32)."""
+    _check("sdgr_device_selfcheck", lib().sdgr_device_selfcheck(ctypes.c_void_p(flags_ptr), stream))
 
 
 def sdgr_densify_scratch_bytes(N):

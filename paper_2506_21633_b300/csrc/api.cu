@@ -545,6 +545,11 @@ sdgr_status sdgr_set_schedule(sdgr_ws *ws, int32_t mode) {
     return SDGR_OK;
 }
 
+sdgr_status sdgr_device_selfcheck(uint32_t *flags, void *stream) {
+    if (!flags || ((uintptr_t)flags) % 4 != 0) return SDGR_ERR_INVALID;
+    return launch_selfcheck(flags, static_cast<cudaStream_t>(stream)) == cudaSuccess ? SDGR_OK : SDGR_ERR_CUDA;
+}
+
 int32_t sdgr_stage_batch_options(int32_t kernel, int32_t *sizes, int32_t max_sizes) {
     const int *opt = nullptr;
     const int n = stage_batch_options(kernel, &opt);

@@ -842,10 +842,11 @@ intensity_bwd_tile(const int tile, const StatusDev *st, const uint2 *__restrict_
                         const float e = in ? ex2_approx(q0) : 0.f;
                         const float alpha = alpha_of<AM>(Q0.z, e);
                         // relative error of a few ulp per step; the factor 1 - alpha is
-                        // the forward's (same alpha bits, same rounding)
+                        // the forward's (same alpha bits, same rounding).  Outside the
+                        // cutoff alpha = 0, and rcp.approx(1) is exactly 1 (the
+                        // library's device self-check), so T stays as it is.
                         const float om = __fsub_rn(1.f, alpha);
-                        const float Td = T * rcp_approx(om);
-                        T = in ? Td : T;
+                        T = T * rcp_approx(om);
                         const float d = Q0.w - B;
                         B = fmaf(alpha, d, B);
                         // weight of the profile: d alpha / d G = o, or tau (1 - alpha)
@@ -856,8 +857,7 @@ intensity_bwd_tile(const int tile, const StatusDev *st, const uint2 *__restrict_
                         const float e = in ? ex2_approx(q1) : 0.f;
                         const float alpha = alpha_of<AM>(Q1.z, e);
                         const float om = __fsub_rn(1.f, alpha);
-                        const float Td = T * rcp_approx(om);
-                        T = in ? Td : T;
+                        T = T * rcp_approx(om);
                         const float d = Q1.w - B;
                         B = fmaf(alpha, d, B);
                         if (two) W[j1 * WSTRIDE + c.toff] = T * d * (AM ? e * om : e);
@@ -998,6 +998,23 @@ int raster_blocks_per_sm(int kernel, int nb) {
     }
     cache[kernel][vi] = n;
     return n;
+}
+
+// Device self-check of the approximate instructions whose exact values the
+// kernels rely on: bit 0 -- rcp.approx of 1 is 1 (the intensity adjoint's
+// fast path divides T by 1 - alpha = 1 for pairs outside the cutoff).
+__global__ void k_selfcheck(uint32_t *flags) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    volatile float one = 1.f;
+    uint32_t f = 0u;
+    if (rcp_approx(one) == 1.f) f |= 1u;
+    *flags = f;
+}
+
+cudaError_t launch_selfcheck(uint32_t *flags, cudaStream_t s) {
+    k_selfcheck<<<1, 32, 0, s>>>(flags);
+    note_launch();
+    return cudaGetLastError();
 }
 
 // Diagnostic: in-cutoff (pixel, Gaussian) pairs of every tile of one plane.

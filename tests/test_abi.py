@@ -83,6 +83,8 @@ def test_host_validation(L):
                               lr, 0.9, 0.999, 1e-8, 1, None) == L.SDGR_ERR_INVALID
     assert lib.sdgr_l1_loss(None, None, 10, None, None, None) == L.SDGR_ERR_INVALID
     assert lib.sdgr_set_stage_batch(None, 0, 256) == L.SDGR_ERR_INVALID
+    assert lib.sdgr_device_selfcheck(None, None) == L.SDGR_ERR_INVALID
+    assert lib.sdgr_device_selfcheck(ctypes.c_void_p(4096 + 2), None) == L.SDGR_ERR_INVALID
 
 
 def test_stage_batch_options(L):
