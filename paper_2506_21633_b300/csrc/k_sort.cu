@@ -544,23 +544,46 @@ cudaError_t launch_emit(const uint32_t *sorted_vg, const unsigned long long *sof
     return cudaGetLastError();
 }
 
+// Each thread reads four consecutive keys as one 16-byte load (the key array
+// starts 16-byte aligned) and the key on either side; a key that differs from
+// its left (right) neighbour starts (ends) its range.
 __global__ void k_ranges(const uint32_t *__restrict__ keys, StatusDev *st, int64_t cap, int64_t nranges,
                          uint2 *ranges) {
     int64_t n = st->code == SDGR_OK ? st->n_inst : 0;
     if (n > cap) n = cap;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        const uint32_t k = keys[i];
-        if (!SDGR_IN_BOUNDS(st, (int64_t)k < nranges)) continue;
-        (void)nranges;
-        if (i == 0 || keys[i - 1] != k) ranges[k].x = (uint32_t)i;
-        if (i == n - 1 || keys[i + 1] != k) ranges[k].y = (uint32_t)(i + 1);
+    const int64_t n4 = (n + 3) / 4;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n4; q += stride) {
+        const int64_t i0 = 4 * q;
+        uint32_t k[4];
+        if (i0 + 3 < n) {
+            const uint4 kv = *reinterpret_cast<const uint4 *>(keys + i0);
+            k[0] = kv.x;
+            k[1] = kv.y;
+            k[2] = kv.z;
+            k[3] = kv.w;
+        } else {
+#pragma unroll
+            for (int e = 0; e < 4; ++e) k[e] = i0 + e < n ? keys[i0 + e] : 0u;
+        }
+        const uint32_t prev = i0 > 0 ? keys[i0 - 1] : 0u;
+        const uint32_t next = i0 + 4 < n ? keys[i0 + 4] : 0u;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int64_t i = i0 + e;
+            if (i >= n) break;
+            if (!SDGR_IN_BOUNDS(st, (int64_t)k[e] < nranges)) continue;
+            const uint32_t left = e == 0 ? prev : k[e - 1], right = e == 3 ? next : k[e + 1];
+            if (i == 0 || left != k[e]) ranges[k[e]].x = (uint32_t)i;
+            if (i == n - 1 || right != k[e]) ranges[k[e]].y = (uint32_t)(i + 1);
+        }
     }
+    (void)nranges;
 }
 
 cudaError_t launch_ranges(const uint32_t *keys, StatusDev *st, int64_t cap, int64_t nranges, uint2 *ranges, int sms,
                           cudaStream_t s) {
-    int64_t blocks = (cap + 255) / 256;
+    int64_t blocks = (cap / 4 + 255) / 256;
     if (blocks > (int64_t)sms * 16) blocks = (int64_t)sms * 16;
     if (blocks < 1) blocks = 1;
     k_ranges<<<(unsigned)blocks, 256, 0, s>>>(keys, st, cap, nranges, ranges);
