@@ -26,7 +26,8 @@
 //
 // Sums over the tile's pixels per Gaussian.  The intensity pass needs only
 // sum_rays alpha T (non-negative, each term <= 1): one redux.sync per hit on
-// 2^-23 fixed point into a 32-bit shared slot.  The intensity adjoint needs
+// 2^-23 fixed point, kept in a register of one lane of the warp and added to
+// a 32-bit shared slot once per 32 staged Gaussians.  The intensity adjoint needs
 // six signed moments and uses a two-phase transpose: in phase 1 every pixel
 // writes its weight for each of its hit Gaussians into a 32 x 256 shared-
 // memory table; in phase 2 eight threads per Gaussian read the table's entries
