@@ -446,6 +446,23 @@ cudaError_t launch_gather_counts(const uint32_t *sorted_vg, const uint32_t *cntC
     return cudaGetLastError();
 }
 
+
+// Position of the d-th (from 0) set bit of m; m has more than d set bits.
+// Binary search over the low half of the remaining window: five steps.
+__device__ __forceinline__ uint32_t nth_set_bit(uint32_t m, uint32_t d) {
+    uint32_t pos = 0u;
+#pragma unroll
+    for (int s = 16; s >= 1; s >>= 1) {
+        const uint32_t c = (uint32_t)__popc(m & ((1u << s) - 1u));
+        if (d >= c) {
+            d -= c;
+            m >>= s;
+            pos += (uint32_t)s;
+        }
+    }
+    return pos;
+}
+
 __global__ void k_check_capacity(const unsigned long long *scnt, const unsigned long long *soff, int64_t VG,
                                  int64_t cap, StatusDev *st) {
     unsigned long long total = 0;
@@ -474,7 +491,7 @@ cudaError_t launch_check_capacity(const unsigned long long *scnt, const unsigned
 __global__ void __launch_bounds__(256)
 k_emit(const uint32_t *__restrict__ sorted_vg, const unsigned long long *__restrict__ soff,
        const unsigned long long *__restrict__ scnt, const uint2 *__restrict__ rectC, const uint2 *__restrict__ rectI,
-       const ViewDev *__restrict__ views, int V, int64_t VG, int total_tiles, const StatusDev *st, int64_t cap,
+       const uint32_t *__restrict__ maskC, const uint32_t *__restrict__ maskI, const ViewDev *__restrict__ views, int V, int64_t VG, int total_tiles, const StatusDev *st, int64_t cap,
        uint32_t *__restrict__ keys, uint32_t *__restrict__ vals) {
     if (st->code != SDGR_OK) return;
     const unsigned full = 0xffffffffu;
@@ -494,6 +511,7 @@ k_emit(const uint32_t *__restrict__ sorted_vg, const unsigned long long *__restr
 #pragma unroll
         for (int p = 0; p < 2; ++p) {
             const uint2 rect = valid ? (p ? rectI[vg] : rectC[vg]) : make_uint2(0u, 0u);
+            const uint32_t tmask = valid ? (p ? maskI[vg] : maskC[vg]) : 0u;
             const unsigned long long off = valid ? soff[(int64_t)p * VG + k] : 0ull;
             const uint32_t cnt = valid ? (uint32_t)scnt[(int64_t)p * VG + k] : 0u;
             const unsigned long long off0 = __shfl_sync(full, off, 0);
@@ -512,11 +530,15 @@ k_emit(const uint32_t *__restrict__ sorted_vg, const unsigned long long *__restr
                 }
                 const uint32_t o_rel = __shfl_sync(full, rel, o);
                 const uint32_t o_rx = __shfl_sync(full, rect.x, o), o_ry = __shfl_sync(full, rect.y, o);
+                const uint32_t o_mask = __shfl_sync(full, tmask, o);
                 const uint32_t o_kb = __shfl_sync(full, key_base, o), o_vg = __shfl_sync(full, vg, o);
                 const int o_tx = __shfl_sync(full, tiles_x, o);
                 if (i < total) {
-                    const uint32_t d = i - o_rel;
                     const uint32_t tx0 = o_rx & 0xffffu, w = (o_rx >> 16) - tx0 + 1u, ty0 = o_ry & 0xffffu;
+                    const uint32_t h = (o_ry >> 16) - ty0 + 1u;
+                    // the d-th tile of the Gaussian's set: of its rectangle, or
+                    // the d-th set bit of its tile mask (rectangles of <= 32 tiles)
+                    const uint32_t d = w * h <= 32u ? nth_set_bit(o_mask, i - o_rel) : i - o_rel;
                     const uint32_t q = d / w;
                     const uint32_t tx = tx0 + (d - q * w);
                     const unsigned long long pos = off0 + i;
@@ -532,13 +554,14 @@ k_emit(const uint32_t *__restrict__ sorted_vg, const unsigned long long *__restr
 }
 
 cudaError_t launch_emit(const uint32_t *sorted_vg, const unsigned long long *soff, const unsigned long long *scnt,
-                        const uint2 *rectC, const uint2 *rectI, const ViewDev *views, int V, int64_t VG,
+                        const uint2 *rectC, const uint2 *rectI, const uint32_t *maskC, const uint32_t *maskI,
+                        const ViewDev *views, int V, int64_t VG,
                         int total_tiles, const StatusDev *st, int64_t cap, uint32_t *keys, uint32_t *vals, int sms,
                         cudaStream_t s) {
     if (VG <= 0) return cudaSuccess;
     int64_t blocks = (VG + 255) / 256;
     if (blocks > (int64_t)sms * 8) blocks = (int64_t)sms * 8;
-    k_emit<<<(unsigned)blocks, 256, 0, s>>>(sorted_vg, soff, scnt, rectC, rectI, views, V, VG, total_tiles, st, cap,
+    k_emit<<<(unsigned)blocks, 256, 0, s>>>(sorted_vg, soff, scnt, rectC, rectI, maskC, maskI, views, V, VG, total_tiles, st, cap,
                                             keys, vals);
     note_launch();
     return cudaGetLastError();

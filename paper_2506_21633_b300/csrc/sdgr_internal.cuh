@@ -194,7 +194,8 @@ void note_launch();
 cudaError_t launch_upload(const void *host_src, size_t bytes, void *dev_dst, cudaStream_t s);
 
 cudaError_t launch_preprocess(const float4 *params, const float4 *sh, int sh_count, const ViewDev *views, int V,
-                              int64_t VG, float K, float eps, int norm_mode, int alpha_mode, CompRec *comp, ImgRec *img, uint2 *rectC, uint2 *rectI, uint32_t *cntC,
+                              int64_t VG, float K, float eps, int norm_mode, int alpha_mode, CompRec *comp, ImgRec *img, uint2 *rectC, uint2 *rectI,
+                              uint32_t *maskC, uint32_t *maskI, uint32_t *cntC,
                               uint32_t *cntI, uint32_t *dkey, uint32_t *dval, int sms, cudaStream_t s);
 
 // exclusive scans (scratch: see scan_scratch_elems)
@@ -215,7 +216,8 @@ cudaError_t launch_gather_counts(const uint32_t *sorted_vg, const uint32_t *cntC
 cudaError_t launch_check_capacity(const unsigned long long *scnt, const unsigned long long *soff, int64_t VG,
                                   int64_t cap, StatusDev *st, cudaStream_t s);
 cudaError_t launch_emit(const uint32_t *sorted_vg, const unsigned long long *soff, const unsigned long long *scnt,
-                        const uint2 *rectC, const uint2 *rectI, const ViewDev *views, int V, int64_t VG,
+                        const uint2 *rectC, const uint2 *rectI, const uint32_t *maskC, const uint32_t *maskI,
+                        const ViewDev *views, int V, int64_t VG,
                         int total_tiles, const StatusDev *st, int64_t cap, uint32_t *keys, uint32_t *vals, int sms,
                         cudaStream_t s);
 // vhist, voff: 2 * V * 32 entries; vt, vbase: 2 * V; scratch:
