@@ -89,14 +89,14 @@ def test_host_validation(L):
 
 def test_stage_batch_options(L):
     """Every raster kernel lists its staging batch sizes, the default first:
-    multiples of the 256 threads of a CTA (each thread stages whole records);
+    multiples of the threads of a CTA (each thread stages whole records);
     an unknown kernel has none."""
     for k, name in enumerate(L.RASTER_KERNELS):
         opts = L.sdgr_stage_batch_options(name)
         assert opts and opts == L.sdgr_stage_batch_options(k)
         assert len(set(opts)) == len(opts)
         assert all(nb % 256 == 0 and 256 <= nb <= 1024 for nb in opts)
-    assert L.sdgr_stage_batch_options(1) == (256, 512, 1024)
+    assert L.sdgr_stage_batch_options(1) == (512, 256)
     assert L.lib().sdgr_stage_batch_options(4, None, 0) == 0
     assert L.lib().sdgr_stage_batch_options(-1, None, 0) == 0
 
