@@ -50,7 +50,7 @@ constexpr int WSTRIDE = 264;  // row stride of the weight table (floats)
 // less shared memory (more resident CTAs) and less staging past the point
 // where every ray of a tile has stopped.  The intensity adjoint's weight
 // table and phase-2 mapping are built around one record per thread.
-static const int kStageK3[] = {256, 512};
+static const int kStageK3[] = {512, 256};
 static const int kStageK4[] = {512, 256};
 static const int kStageK5[] = {512, 1024, 256};
 static const int kStageK6[] = {256};
@@ -371,36 +371,67 @@ __device__ __forceinline__ void stage_comp(const CompRec *__restrict__ comp, uin
 // ---------------------------------------------------------------------------
 constexpr float S23 = 8388608.f;  // 2^23: scale of the intensity pass's transmittance
 
-// TfloorS: the transmittance floor times 2^23.
+// TfloorS: the transmittance floor times 2^23.  Four warps per tile, each on
+// an 8 x 8 block of rays with two rays per lane (rows r and r + 4 of the
+// block); each ray's exponent is the same five-FMA quadratic, in the same
+// tile-local coordinates, as the adjoint evaluates for it.  A lane adds its
+// two rays' fixed-point weights before the warp's redux: 64 patterns of
+// 2^23 + k sum to 64 x 0x4B000000 = 0xC0000000 (mod 2^32) plus the warp's
+// sum, at most 2^29.
 template <int AM, int NB>
 __device__ __forceinline__ void
 intensity_fwd_tile(const int tile, const StatusDev *st, const uint2 *__restrict__ ranges, const uint32_t *__restrict__ vals,
                    const CompRec *__restrict__ comp, const ViewDev *__restrict__ views, int V, float cut, float TfloorS,
                    float *__restrict__ A, float *__restrict__ Tstop, int32_t *__restrict__ last) {
-    constexpr int PER = NB / 256;  // records staged per thread
+    constexpr int NT = 128;
+    constexpr int PER = NB / NT;  // records staged per thread
     __shared__ float4 sP[NB];  // (qa, qb, qc, l1)
     __shared__ float4 sQ[NB];  // (l2, c0, o, -)
     __shared__ uint32_t sM[NB];
     __shared__ uint32_t sid[NB];
     __shared__ uint32_t sAcc[NB];  // sum of alpha T over the tile's 256 rays, in units of 2^-23 (< 2^31)
-    __shared__ uint8_t sHL[8 * 32];  // per warp: its hit list of the current slice
-    const int t = threadIdx.x, lane = t & 31;
-    uint8_t *const wl = sHL + 32 * (t >> 5);
+    __shared__ uint8_t sHL[4 * 32];  // per warp: its hit list of the current slice
+    const int t = threadIdx.x, w = t >> 5, lane = t & 31;
+    uint8_t *const wl = sHL + 32 * w;
     int nh = 0;
-    const TileCtx c = tile_ctx(views, V, tile);
-    const LaneXY L = lane_xy();
+    TileCtx c;
+    c.v = view_of_tile(views, V, tile);
+    const ViewDev &vd = views[c.v];
+    {
+        const int lt = tile - vd.tile_off;
+        c.x0 = (lt % vd.tiles_x) * TILE;
+        c.y0 = (lt / vd.tiles_x) * TILE;
+        c.x0f = (float)c.x0;
+        c.y0f = (float)c.y0;
+        c.valid = 0;
+#pragma unroll
+        for (int b = 0; b < 8; ++b)
+            if (c.x0 + 8 * (b & 1) < vd.NA && c.y0 + 4 * (b >> 1) < vd.NR) c.valid |= 1u << b;
+    }
+    const int X = 8 * (w & 1) + (lane & 7), Y = 8 * (w >> 1) + (lane >> 3);
+    const int px = c.x0 + X, py0 = c.y0 + Y, py1 = py0 + 4;
+    const bool in0 = px < vd.NA && py0 < vd.NR, in1 = px < vd.NA && py1 < vd.NR;
+    LaneXY L0, L1;
+    L0.X = L1.X = (float)X;
+    L0.Y = (float)Y;
+    L1.Y = (float)(Y + 4);
+    L0.X2 = L1.X2 = L0.X * L0.X;
+    L0.XY = L0.X * L0.Y;
+    L1.XY = L1.X * L1.Y;
+    L0.Y2 = L0.Y * L0.Y;
+    L1.Y2 = L1.Y * L1.Y;
     const uint2 r = ranges[tile];
     const float cutm = cut_margin(cut);
-    constexpr uint32_t WARP_BIAS = 0x60000000u;  // 32 x bits(2^23), mod 2^32
-    float T = c.inside ? S23 : 0.f, Tprev = S23;  // Ts; a ray outside the image takes no pair
-    int32_t lastj = 0;
+    constexpr uint32_t WARP_BIAS = 0xC0000000u;  // 64 x bits(2^23), mod 2^32
+    float T0 = in0 ? S23 : 0.f, T1 = in1 ? S23 : 0.f, Tp0 = S23, Tp1 = S23;  // a ray outside the image takes no pair
+    int32_t lj0 = 0, lj1 = 0;
     int nb = 0;  // Gaussians staged in the current batch
     uint32_t vnext[PER];  // next batch's list entries, loaded one batch ahead
-    unrolled<PER>([&](int u) { vnext[u] = r.x + t + 256 * u < r.y ? vals[r.x + t + 256 * u] : 0u; });
+    unrolled<PER>([&](int u) { vnext[u] = r.x + t + NT * u < r.y ? vals[r.x + t + NT * u] : 0u; });
     for (uint32_t base = r.x; base < r.y; base += NB) {
-        if (__syncthreads_count(T < TfloorS) == (int)blockDim.x) break;
+        if (__syncthreads_count((T0 < TfloorS) & (T1 < TfloorS)) == (int)blockDim.x) break;
         unrolled<PER>([&](int u) {
-            const int k = t + 256 * u;
+            const int k = t + NT * u;
             // the previous batch's sums: one global atomic per (tile, Gaussian)
             if (k < nb && sAcc[k] != 0u) atomicAdd(&A[sid[k]], __uint2float_rn(sAcc[k]) * (1.f / S23));
             if (base + k < r.y) {
@@ -408,10 +439,11 @@ intensity_fwd_tile(const int tile, const StatusDev *st, const uint2 *__restrict_
                 float4 P;
                 float2 Q, uv, oP;
                 uint32_t m = 0;
-                if (vg_ok(st, views[c.v], vg)) stage_comp(comp, vg, c, cutm, P, Q, m, uv, oP);
+                if (vg_ok(st, vd, vg)) stage_comp(comp, vg, c, cutm, P, Q, m, uv, oP);
                 sP[k] = P;
                 sQ[k] = make_float4(Q.x, Q.y, oP.x, 0.f);
-                sM[k] = m;
+                const uint32_t h = m | (m >> 2);  // 8 x 8 block 2 RB + cb: 8 x 4 blocks 4 RB + cb, 4 RB + 2 + cb
+                sM[k] = (h & 3u) | ((h >> 2) & 0xcu);
                 sid[k] = vg;
             }
             sAcc[k] = 0u;
@@ -429,44 +461,52 @@ intensity_fwd_tile(const int tile, const StatusDev *st, const uint2 *__restrict_
                 __syncwarp();
             }
             const int32_t kb = (int32_t)(base + sub + 1);
-            // the warp's 32 rays are summed in fixed point by one redux per hit;
+            // the warp's 64 rays are summed in fixed point by one redux per hit;
             // lane j keeps the warp's sum for staged Gaussian sub + j, which goes
-            // to shared memory once per 32 staged Gaussians (no branch and no
-            // atomic in the hit loop: 10 % of the pass's time)
+            // to shared memory once per 32 staged Gaussians
             uint32_t mine = 0u;
             for (int i = 0; i < nh; ++i) {
                 const int jj = wl[i];
                 const float4 P = sP[sub + jj];
                 const float4 Q = sQ[sub + jj];
-                const float q = poly_q(P, Q.x, Q.y, L);
-                const bool in = (q >= cut) & (T >= TfloorS);
-                const float alpha = alpha_of<AM>(Q.z, in ? ex2_approx(q) : 0.f);
-                const uint32_t ws = __reduce_add_sync(0xffffffffu, __float_as_uint(__fmaf_rn(alpha, T, S23)));
+                const float q0 = poly_q(P, Q.x, Q.y, L0);
+                const float q1 = poly_q(P, Q.x, Q.y, L1);
+                const bool i0 = (q0 >= cut) & (T0 >= TfloorS);
+                const bool i1 = (q1 >= cut) & (T1 >= TfloorS);
+                const float a0 = alpha_of<AM>(Q.z, i0 ? ex2_approx(q0) : 0.f);
+                const float a1 = alpha_of<AM>(Q.z, i1 ? ex2_approx(q1) : 0.f);
+                const uint32_t f = __float_as_uint(__fmaf_rn(a0, T0, S23)) + __float_as_uint(__fmaf_rn(a1, T1, S23));
+                const uint32_t ws = __reduce_add_sync(0xffffffffu, f);
                 mine = lane == jj ? ws - WARP_BIAS : mine;
-                Tprev = in ? T : Tprev;
-                lastj = in ? kb + jj : lastj;
-                T = __fmul_rn(T, __fsub_rn(1.f, alpha));
+                Tp0 = i0 ? T0 : Tp0;
+                Tp1 = i1 ? T1 : Tp1;
+                lj0 = i0 ? kb + jj : lj0;
+                lj1 = i1 ? kb + jj : lj1;
+                T0 = __fmul_rn(T0, __fsub_rn(1.f, a0));
+                T1 = __fmul_rn(T1, __fsub_rn(1.f, a1));
             }
             if (mine != 0u) atomicAdd(&sAcc[sub + lane], mine);
         }
     }
     __syncthreads();
     unrolled<PER>([&](int u) {
-        const int k = t + 256 * u;
+        const int k = t + NT * u;
         if (k < nb && sAcc[k] != 0u) atomicAdd(&A[sid[k]], __uint2float_rn(sAcc[k]) * (1.f / S23));
     });
-    if (c.inside) {
-        Tstop[c.pix] = Tprev * (1.f / S23);
-        last[c.pix] = T < TfloorS ? -lastj : lastj;  // negative: the ray stopped at the floor
+    if (in0) {
+        const int64_t pix = vd.pix_off + (int64_t)py0 * vd.NA + px;
+        Tstop[pix] = Tp0 * (1.f / S23);
+        last[pix] = T0 < TfloorS ? -lj0 : lj0;  // negative: the ray stopped at the floor
+    }
+    if (in1) {
+        const int64_t pix = vd.pix_off + (int64_t)py1 * vd.NA + px;
+        Tstop[pix] = Tp1 * (1.f / S23);
+        last[pix] = T1 < TfloorS ? -lj1 : lj1;
     }
 }
 
-// The 512-record build is held to five resident CTAs per SM (48 registers;
-// unbounded it takes 59 and loses a CTA); the 256-record build is left
-// unbounded (minimum 0).  Which one is faster depends on the hit loop: the
-// tuner decides.
 template <int AM, int NB>
-__global__ void __launch_bounds__(256, NB == 512 ? 5 : 0)
+__global__ void __launch_bounds__(128)
 k_intensity_fwd(const uint2 *__restrict__ ranges, const uint32_t *__restrict__ vals, const CompRec *__restrict__ comp,
                 const ViewDev *__restrict__ views, int V, float cut, float TfloorS, const StatusDev *st,
                 float *__restrict__ A, float *__restrict__ Tstop, int32_t *__restrict__ last, const TileSched sc) {
@@ -489,10 +529,10 @@ cudaError_t launch_intensity_fwd(const uint2 *ranges, const uint32_t *vals, cons
     const int v = (alpha_mode ? 2 : 0) + (sched.nb == 512 ? 1 : 0);
     const float TfloorS = Tfloor * S23;  // exact: a power-of-two scale of a normal float
     switch (v) {
-        case 0: k_intensity_fwd<0, 256><<<grid, TILE_PIX, 0, s>>>(ranges, vals, comp, views, V, cut, TfloorS, st, A, Tstop, last, sched); break;
-        case 1: k_intensity_fwd<0, 512><<<grid, TILE_PIX, 0, s>>>(ranges, vals, comp, views, V, cut, TfloorS, st, A, Tstop, last, sched); break;
-        case 2: k_intensity_fwd<1, 256><<<grid, TILE_PIX, 0, s>>>(ranges, vals, comp, views, V, cut, TfloorS, st, A, Tstop, last, sched); break;
-        default: k_intensity_fwd<1, 512><<<grid, TILE_PIX, 0, s>>>(ranges, vals, comp, views, V, cut, TfloorS, st, A, Tstop, last, sched); break;
+        case 0: k_intensity_fwd<0, 256><<<grid, TILE_PIX / 2, 0, s>>>(ranges, vals, comp, views, V, cut, TfloorS, st, A, Tstop, last, sched); break;
+        case 1: k_intensity_fwd<0, 512><<<grid, TILE_PIX / 2, 0, s>>>(ranges, vals, comp, views, V, cut, TfloorS, st, A, Tstop, last, sched); break;
+        case 2: k_intensity_fwd<1, 256><<<grid, TILE_PIX / 2, 0, s>>>(ranges, vals, comp, views, V, cut, TfloorS, st, A, Tstop, last, sched); break;
+        default: k_intensity_fwd<1, 512><<<grid, TILE_PIX / 2, 0, s>>>(ranges, vals, comp, views, V, cut, TfloorS, st, A, Tstop, last, sched); break;
     }
     note_launch();
     return cudaGetLastError();
@@ -1008,8 +1048,8 @@ int raster_blocks_per_sm(int kernel, int nb) {
     int n = 0;
     cudaError_t e = cudaErrorInvalidValue;
     switch (kernel * 3 + vi) {
-        case 0: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_intensity_fwd<0, 256>, TILE_PIX, 0); break;
-        case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_intensity_fwd<0, 512>, TILE_PIX, 0); break;
+        case 0: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_intensity_fwd<0, 256>, TILE_PIX / 2, 0); break;
+        case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_intensity_fwd<0, 512>, TILE_PIX / 2, 0); break;
         case 3: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_splat_fwd<256>, TILE_PIX / 2, 0); break;
         case 4: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_splat_fwd<512>, TILE_PIX / 2, 0); break;
         case 6: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_splat_bwd<256>, TILE_PIX, 0); break;
