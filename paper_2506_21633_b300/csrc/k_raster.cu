@@ -3,16 +3,20 @@
 // Section II-A-2, eq. I_i) and the layover splat on the imaging plane
 // (Section II-A-3, eq. S_{n,m}), and their adjoints (Section II-B-1/2).
 //
-// A CTA works on one 16x16 tile at a time, one thread per pixel (ray); warp w
-// covers the 8x4 pixel block with columns 8 (w & 1) .. +7 and rows
-// 4 (w >> 1) .. +3.  Which tiles a CTA takes follows the launch's schedule
-// (for_tiles): one CTA per tile, one per item of the longest-first work list,
-// or resident CTAs pulling items.  The tile's instance list is staged through
-// shared memory in batches (256 records; 1024 in the splat adjoint).
+// A CTA works on one 16x16 tile at a time.  The adjoints run eight warps,
+// one thread per pixel (ray); warp w covers the 8x4 pixel block with columns
+// 8 (w & 1) .. +7 and rows 4 (w >> 1) .. +3.  The intensity pass and the
+// splat run four warps; warp w covers the 8x8 block with columns 8 (w & 1) ..
+// +7 and rows 8 (w >> 1) .. +7, two rays (pixels) per lane, rows r and r + 4.
+// Which tiles a CTA takes follows the launch's schedule (for_tiles): one CTA
+// per tile, one per item of the longest-first work list, or resident CTAs
+// pulling items.  The tile's instance list is staged through shared memory in
+// batches (the staging batch of each kernel, a tuning knob).
 //
 // Culling: when a batch is staged, each Gaussian gets the set of the tile's
-// eight pixel blocks that its K-ellipse reaches (found from the ellipse's
-// exact horizontal extent over each band of four rows).  A warp walks only
+// eight 8x4 pixel blocks that its K-ellipse reaches (found from the ellipse's
+// exact horizontal extent over each band of four rows; an 8x8 block is the
+// union of two).  A warp walks only
 // the Gaussians whose set holds its block: per 32 staged Gaussians one ballot
 // gives the warp its hit list, which it visits in list order (front to back
 // for the intensity pass, back to front for its adjoint).  The intensity pass
