@@ -56,7 +56,7 @@ constexpr int WSTRIDE = 264;  // row stride of the weight table (floats)
 // table and phase-2 mapping are built around one record per thread.
 static const int kStageK3[] = {512, 256};
 static const int kStageK4[] = {512, 256};
-static const int kStageK5[] = {512, 1024, 256};
+static const int kStageK5[] = {1024, 512, 256};
 static const int kStageK6[] = {256};
 
 struct TileCtx {
@@ -231,10 +231,7 @@ __device__ __forceinline__ uint32_t block_list(uint32_t m) {
 // atomic per moment: each thread stores its partial moments into `scr` (48
 // floats owned by the group, moment-major), then thread cc < 6 adds the eight
 // partials of moment cc (two float4 loads) and issues that moment's atomic.
-// `scr` must be 16-byte aligned; the whole warp calls this.  Groups sit
-// RSTRIDE floats apart: the four groups of a warp then store to disjoint
-// banks (offsets 0, 24, 16, 8 mod 32).
-constexpr int RSTRIDE = 56;
+// `scr` must be 16-byte aligned; the whole warp calls this.
 __device__ __forceinline__ void moments_out(float *scr, int cc, const float m[6], bool valid, float4 *acc,
                                             uint32_t vg) {
     __syncwarp();
@@ -246,30 +243,6 @@ __device__ __forceinline__ void moments_out(float *scr, int cc, const float m[6]
         const float4 b = *reinterpret_cast<const float4 *>(scr + cc * 8 + 4);
         const float v = ((a.x + a.y) + (a.z + a.w)) + ((b.x + b.y) + (b.z + b.w));
         if (valid && v != 0.f) atomicAdd(reinterpret_cast<float *>(acc + 2 * (size_t)vg) + cc, v);
-    }
-}
-
-// The same over a group of four threads (c4 = 0..3): 24 floats of scratch
-// (moment q at q * 4 .. q * 4 + 3); thread c4 adds moments c4 and, for c4 < 2,
-// c4 + 4.  Groups sit RSTRIDE4 floats apart: the eight groups of a warp then
-// store to disjoint banks.
-constexpr int RSTRIDE4 = 28;
-__device__ __forceinline__ void moments_out4(float *scr, int c4, const float m[6], bool valid, float4 *acc,
-                                             uint32_t vg) {
-    __syncwarp();
-#pragma unroll
-    for (int q = 0; q < 6; ++q) scr[q * 4 + c4] = m[q];
-    __syncwarp();
-    float *dst = reinterpret_cast<float *>(acc + 2 * (size_t)vg);
-    {
-        const float4 a = *reinterpret_cast<const float4 *>(scr + c4 * 4);
-        const float v = (a.x + a.y) + (a.z + a.w);
-        if (valid && v != 0.f) atomicAdd(dst + c4, v);
-    }
-    if (c4 < 2) {
-        const float4 a = *reinterpret_cast<const float4 *>(scr + (c4 + 4) * 4);
-        const float v = (a.x + a.y) + (a.z + a.w);
-        if (valid && v != 0.f) atomicAdd(dst + c4 + 4, v);
     }
 }
 
@@ -701,12 +674,12 @@ cudaError_t launch_splat_fwd(const uint2 *rangesI, const uint32_t *vals, const I
 // a10: adjoint of the imaging splat.  Per (view, Gaussian) the moments of
 // w = dL/dS * exp(-delta_I/2); the parameter adjoint turns them into
 // dL/dI = c M0, dL/du_I, dL/dconic_I and dL/dc.  No pixel depends on
-// another here, so the kernel is Gaussian-parallel: four threads per
-// Gaussian walk its hit blocks, each thread two columns (four rows each) per
-// block, with dL/dS read from shared memory as one float4 per column; the four
-// partial moments meet in shared memory, and four threads add the six moments
-// and issue their atomics.  (Against eight threads of one column each, the
-// per-block and per-Gaussian work is shared by twice the pixels: -9 %.)
+// another here, so the kernel is Gaussian-parallel: two threads per
+// Gaussian walk its hit blocks, each thread four columns (four rows each) per
+// block, with dL/dS read from shared memory as one float4 per column; the two
+// partial moments meet by one shuffle each, and each thread issues three of
+// the six atomics.  (Against eight threads of one column each, the per-block
+// and per-Gaussian work is shared by four times the pixels: -13 %.)
 // ---------------------------------------------------------------------------
 template <int NB>
 __device__ __forceinline__ void
@@ -721,7 +694,6 @@ splat_bwd_tile(const int tile, const StatusDev *st, const uint2 *__restrict__ ra
     __shared__ uint8_t sperm[NB];
     __shared__ __align__(16) float sg[TILE_PIX];  // dL/dS of the tile's pixels, in table layout
     __shared__ __align__(16) float zero4[4];
-    __shared__ __align__(16) float sred[64 * RSTRIDE4];  // moment reduction scratch, one slot per group of 4
     const int t = threadIdx.x, warp = t >> 5;
     if (t < 4) zero4[t] = 0.f;
     const TileCtx c = tile_ctx(views, V, tile);
@@ -754,11 +726,12 @@ splat_bwd_tile(const int tile, const StatusDev *st, const uint2 *__restrict__ ra
         const int nb = min(NB, (int)(r.y - base));
         for (int j0 = warp * 32; j0 < nb; j0 += 256) order_by_blocks(sM, j0, min(32, nb - j0), sperm + j0);
         __syncthreads();
-        // four threads per Gaussian, each two columns (c4 and c4 + 4) of every
-        // block; 64 Gaussians at a time, a warp's eight in one 32-entry window
-        for (int j0 = 0; j0 < nb; j0 += 64) {
-            const int g = t >> 2, c4 = t & 3;
-            const int w0 = j0 + (g & 32);
+        // two threads per Gaussian, each four columns (c2, c2 + 2, c2 + 4,
+        // c2 + 6) of every block; 128 Gaussians at a time, a warp's sixteen
+        // in one 32-entry window
+        for (int j0 = 0; j0 < nb; j0 += 128) {
+            const int g = t >> 1, c2 = t & 1;
+            const int w0 = j0 + (g & 96);
             const int k = w0 < nb ? w0 + sperm[w0 + (g & 31)] : nb;
             const int ks = k < nb ? k : 0;
             const uint32_t mb = k < nb ? sM[k] : 0u;
@@ -767,24 +740,21 @@ splat_bwd_tile(const int tile, const StatusDev *st, const uint2 *__restrict__ ra
             const float4 G = sG[ks];
             const float qc2 = 2.f * G.z;
             const float2 uv = sU[ks];
-            const float dxa0 = (float)c4 - uv.x, dy00 = -uv.y;
+            const float dxa0 = (float)c2 - uv.x, dy00 = -uv.y;
             float m[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
             const int rounds = __reduce_max_sync(0xffffffffu, cnt);
             for (int i = 0; i < rounds; ++i) {
                 const int b = (int)(bl & 7u);
                 bl >>= 4;
                 const bool live = i < cnt;
-                const float *srca = live ? sg + 32 * b + 4 * c4 : zero4;  // no block left: dL/dS = 0
-                const float *srcb = live ? srca + 16 : zero4;
+                const float *src = live ? sg + 32 * b + 4 * c2 : zero4;  // no block left: dL/dS = 0
+                const int step = live ? 8 : 0;
                 const float dxa = (b & 1) ? dxa0 + 8.f : dxa0;
                 const float dy0 = fmaf(4.f, small_u2f((uint32_t)b >> 1), dy00);
 #pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const float dx = h ? dxa + 4.f : dxa;
-                    const float4 g4 = *reinterpret_cast<const float4 *>(h ? srcb : srca);
-                    // exponent along the column: qa dx^2 + (qb dx) dy + qc dy^2 at the
-                    // first row, then by differences: from row dy to dy + 1 it grows
-                    // by qb dx + qc (2 dy + 1), which grows by 2 qc per row
+                for (int h = 0; h < 4; ++h) {
+                    const float dx = dxa + 2.f * (float)h;
+                    const float4 g4 = *reinterpret_cast<const float4 *>(src + step * h);
                     const float Aq = G.x * dx * dx, Bq = G.y * dx;
                     float4 w;
                     float q = fmaf(fmaf(G.z, dy0, Bq), dy0, Aq);
@@ -801,7 +771,18 @@ splat_bwd_tile(const int tile, const StatusDev *st, const uint2 *__restrict__ ra
                     block_moments(w, dx, dy0, m);
                 }
             }
-            moments_out4(sred + g * RSTRIDE4, c4, m, k < nb, accI, sid[ks]);
+            // the pair's partial moments: add across the two lanes, then lane c2
+            // issues the atomics of moments c2, c2 + 2, c2 + 4
+#pragma unroll
+            for (int q = 0; q < 6; ++q) m[q] += __shfl_xor_sync(0xffffffffu, m[q], 1);
+            if (k < nb) {
+                float *dst = reinterpret_cast<float *>(accI + 2 * (size_t)sid[ks]);
+#pragma unroll
+                for (int q = 0; q < 3; ++q) {
+                    const float v = c2 ? m[2 * q + 1] : m[2 * q];
+                    if (v != 0.f) atomicAdd(dst + 2 * q + c2, v);
+                }
+            }
         }
     }
 }
