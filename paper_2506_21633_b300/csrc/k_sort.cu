@@ -514,6 +514,15 @@ k_emit(const uint32_t *__restrict__ sorted_vg, const unsigned long long *__restr
             const uint32_t tmask = valid ? (p ? maskI[vg] : maskC[vg]) : 0u;
             const unsigned long long off = valid ? soff[(int64_t)p * VG + k] : 0ull;
             const uint32_t cnt = valid ? (uint32_t)scnt[(int64_t)p * VG + k] : 0u;
+            // rectangles of <= 32 tiles: ceil(2^16 / w), so that the row of a bit
+            // index d < 32 is (d * rinv) >> 16 (exact: the error d (rinv - 2^16 / w) / 2^16
+            // is below 32 / 2^16 < 1 / w); one division per Gaussian, none per instance
+            uint32_t rinv = 0u;
+            {
+                const uint32_t tw = (rect.x >> 16) - (rect.x & 0xffffu) + 1u;
+                const uint32_t th = (rect.y >> 16) - (rect.y & 0xffffu) + 1u;
+                if (valid && cnt > 0u && tw * th <= 32u) rinv = (65536u + tw - 1u) / tw;
+            }
             const unsigned long long off0 = __shfl_sync(full, off, 0);
             // start of this lane's range relative to lane 0 (an invalid lane
             // gets a start no item reaches)
@@ -531,6 +540,7 @@ k_emit(const uint32_t *__restrict__ sorted_vg, const unsigned long long *__restr
                 const uint32_t o_rel = __shfl_sync(full, rel, o);
                 const uint32_t o_rx = __shfl_sync(full, rect.x, o), o_ry = __shfl_sync(full, rect.y, o);
                 const uint32_t o_mask = __shfl_sync(full, tmask, o);
+                const uint32_t o_rinv = __shfl_sync(full, rinv, o);
                 const uint32_t o_kb = __shfl_sync(full, key_base, o), o_vg = __shfl_sync(full, vg, o);
                 const int o_tx = __shfl_sync(full, tiles_x, o);
                 if (i < total) {
@@ -538,8 +548,9 @@ k_emit(const uint32_t *__restrict__ sorted_vg, const unsigned long long *__restr
                     const uint32_t h = (o_ry >> 16) - ty0 + 1u;
                     // the d-th tile of the Gaussian's set: of its rectangle, or
                     // the d-th set bit of its tile mask (rectangles of <= 32 tiles)
-                    const uint32_t d = w * h <= 32u ? nth_set_bit(o_mask, i - o_rel) : i - o_rel;
-                    const uint32_t q = d / w;
+                    const bool small = w * h <= 32u;
+                    const uint32_t d = small ? nth_set_bit(o_mask, i - o_rel) : i - o_rel;
+                    const uint32_t q = small ? (d * o_rinv) >> 16 : d / w;
                     const uint32_t tx = tx0 + (d - q * w);
                     const unsigned long long pos = off0 + i;
                     if (SDGR_IN_BOUNDS(st, pos < (unsigned long long)cap)) {
