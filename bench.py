@@ -436,6 +436,15 @@ def run_sdgr(args):
                 "traffic": kernel_traffic(dom), "kernel": KERNEL_NAME.get(dom, dom)}
     roof["stage_ms_per_step"] = {k: round(prof[k][0] / max(args.steps, 1), 4) for k in prof}
     roof["stage_share"] = share
+    # every raster kernel against the same FP32-pipe peak (algorithmic ops per in-cutoff pair)
+    alu_peak = alu_peak_tops(sms, sm_max)
+    roof["raster_kernels"] = {}
+    for k, (fp, mu) in ALG_OPS.items():
+        if k in stage_ms and stage_ms[k][0] > 0:
+            ach = pairs[PLANE[k]] * (fp + 8 * mu) / (stage_ms[k][0] / 1e3) / 1e12
+            roof["raster_kernels"][KERNEL_NAME[k]] = {"ms_per_launch": round(stage_ms[k][0], 4),
+                                                      "ops_per_pair": fp + 8 * mu, "achieved": round(ach, 3),
+                                                      "frac": round(ach / alu_peak, 4)}
 
     out = {
         "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
