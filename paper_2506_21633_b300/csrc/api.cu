@@ -29,7 +29,7 @@ struct Layout {
     size_t scnt, soff, scan64;
     size_t ik0, iv0, ik1, iv1;
     size_t hist, scan32, ranges, segs, order, work, vhist, voff, vt, vbase, vscan;
-    size_t A, Tstop, last, accI, accC;
+    size_t A, Tend, last, accI, accC;
     size_t total;
 };
 
@@ -92,7 +92,7 @@ Layout make_layout(const sdgr_caps *c) {
     L.vbase = take(2 * V * 4);
     L.vscan = take(scan_scratch_elems((int64_t)(2 * V)) * 4);
     L.A = take(VG * 4);
-    L.Tstop = take(NP * 4);
+    L.Tend = take(NP * 4);
     L.last = take(NP * 4);
     L.accI = take(VG * 2 * sizeof(float4));
     L.accC = take(VG * 2 * sizeof(float4));
@@ -486,7 +486,7 @@ sdgr_status sdgr_render_fwd(sdgr_ws *ws, float *images, float *intensity, void *
     CK(raster_sched(ws, 0, s, sc));
     int pk = prof_begin(ws, SDGR_STAGE_INTENSITY_FWD, s);
     CK(launch_intensity_fwd(ranges, ws->inst_vals, ws->at<CompRec>(L.comp), views, ws->V, ws->tiles, cut,
-                            t_floor(ws->cfg.T_min), ws->cfg.alpha_mode, st, A, ws->at<float>(L.Tstop),
+                            t_floor(ws->cfg.T_min), ws->cfg.alpha_mode, st, A, ws->at<float>(L.Tend),
                             ws->at<int32_t>(L.last), sc, s));
     prof_end(ws, pk, s);
     CK(raster_sched(ws, 1, s, sc));
@@ -527,7 +527,7 @@ sdgr_status sdgr_render_bwd(sdgr_ws *ws, const float *dL_dimages, float *grads, 
     CK(raster_sched(ws, 3, s, sc));
     pk = prof_begin(ws, SDGR_STAGE_INTENSITY_BWD, s);
     CK(launch_intensity_bwd(ranges, ws->inst_vals, ws->at<CompRec>(L.comp), ws->at<ImgRec>(L.img), accI,
-                            ws->at<float>(L.Tstop), ws->at<int32_t>(L.last), views, ws->V, ws->tiles, cut,
+                            ws->at<float>(L.Tend), ws->at<int32_t>(L.last), views, ws->V, ws->tiles, cut,
                             ws->cfg.alpha_mode, st, accC, sc, s));
     prof_end(ws, pk, s);
     pk = prof_begin(ws, SDGR_STAGE_PARAM_BWD, s);

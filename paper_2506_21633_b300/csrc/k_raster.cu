@@ -355,22 +355,23 @@ __device__ __forceinline__ void stage_comp(const CompRec *__restrict__ comp, uin
 // ---------------------------------------------------------------------------
 // a7: intensity pass.  Per ray (cell centre): T = 1; for each Gaussian in
 // depth order: alpha = o exp(-delta/2) within the cutoff; the Gaussian
-// receives alpha T; T *= 1 - alpha.  The ray stops once T < Tfloor.  For the
-// adjoint each ray records the index just past its last in-cutoff Gaussian
-// (negated if the ray stopped at the floor) and the transmittance in front of
-// that Gaussian.  The pair update is branch-free: a pair outside the cutoff
-// (or on a stopped ray) gets weight 0, which leaves T unchanged.
+// receives alpha T; T *= 1 - alpha.  The ray stops once T < Tfloor (the pair
+// that takes it below the floor is the last one it takes).  For the adjoint a
+// ray that stopped records the negated index just past its stopping Gaussian
+// and the transmittance in front of it; any other ray its transmittance
+// behind its last pair and an index past its last in-cutoff Gaussian (just
+// past the last Gaussian that reaches its warp's block).  The pair update is
+// branch-free: a pair outside the cutoff gets weight 0, which leaves T
+// unchanged; a stopped ray carries T = 0.
 //
-// The ray carries Ts = 2^23 T.  Scaling by a power of two commutes with every
-// rounding here (all values stay normal: T >= 2^-100 before a factor, and a
-// factor 1 - alpha is 0 or >= 2^-24), so Ts / 2^23 has exactly the bits of
-// the unscaled recursion that the adjoint repeats.  With it one FMA gives the
-// pair's fixed-point weight: fma(alpha, Ts, 2^23) lies in [2^23, 2^24], where
+// The ray carries Ts = 2^23 T (exact while T is normal).  With it one FMA
+// gives the pair's fixed-point weight: fma(alpha, Ts, 2^23) lies in [2^23, 2^24], where
 // floats are the integers, so its bit pattern is 0x4B000000 + round(2^23
 // alpha T); the 32 lanes' patterns add up (mod 2^32) to 32 x 0x4B000000 =
 // 0x60000000 (mod 2^32) plus the warp's sum, at most 2^28.
 // ---------------------------------------------------------------------------
-constexpr float S23 = 8388608.f;  // 2^23: scale of the intensity pass's transmittance
+constexpr float S23 = 8388608.f;         // 2^23: scale of the intensity pass's transmittance
+constexpr uint32_t S23_BITS = 0x4B000000u;  // bit pattern of 2^23
 
 // TfloorS: the transmittance floor times 2^23.  Four warps per tile, each on
 // an 8 x 8 block of rays with two rays per lane (rows r and r + 4 of the
@@ -383,7 +384,7 @@ template <int AM, int NB>
 __device__ __forceinline__ void
 intensity_fwd_tile(const int tile, const StatusDev *st, const uint2 *__restrict__ ranges, const uint32_t *__restrict__ vals,
                    const CompRec *__restrict__ comp, const ViewDev *__restrict__ views, int V, float cut, float TfloorS,
-                   float *__restrict__ A, float *__restrict__ Tstop, int32_t *__restrict__ last) {
+                   float *__restrict__ A, float *__restrict__ Tend, int32_t *__restrict__ last) {
     constexpr int NT = 128;
     constexpr int PER = NB / NT;  // records staged per thread
     __shared__ float4 sP[NB];  // (qa, qb, qc, l1)
@@ -391,9 +392,13 @@ intensity_fwd_tile(const int tile, const StatusDev *st, const uint2 *__restrict_
     __shared__ uint32_t sM[NB];
     __shared__ uint32_t sid[NB];
     __shared__ uint32_t sAcc[NB];  // sum of alpha T over the tile's 256 rays, in units of 2^-23 (< 2^31)
-    __shared__ uint8_t sHL[4 * 32];  // per warp: its hit list of the current slice
+    __shared__ uint16_t sHL[4 * 32];  // per warp: its hit list of the current slice
+    // per ray (thread t: rays t and t + 128) once it stopped: T in front of its
+    // stopping pair, and -(list index of that pair + 1); written by its own thread
+    __shared__ float sTe[2 * NT];
+    __shared__ int32_t sLj[2 * NT];
     const int t = threadIdx.x, w = t >> 5, lane = t & 31;
-    uint8_t *const wl = sHL + 32 * w;
+    uint16_t *const wl = sHL + 32 * w;
     int nh = 0;
     TileCtx c;
     c.v = view_of_tile(views, V, tile);
@@ -424,8 +429,19 @@ intensity_fwd_tile(const int tile, const StatusDev *st, const uint2 *__restrict_
     const uint2 r = ranges[tile];
     const float cutm = cut_margin(cut);
     constexpr uint32_t WARP_BIAS = 0xC0000000u;  // 64 x bits(2^23), mod 2^32
-    float T0 = in0 ? S23 : 0.f, T1 = in1 ? S23 : 0.f, Tp0 = S23, Tp1 = S23;  // a ray outside the image takes no pair
-    int32_t lj0 = 0, lj1 = 0;
+    float T0 = in0 ? S23 : 0.f, T1 = in1 ? S23 : 0.f;  // a ray outside the image takes no pair
+    sLj[t] = 0;
+    sLj[t + NT] = 0;
+    int32_t wb = 0;  // 1 + the list index of the warp's last hit
+    // opacities of the lane's two pairs with the staged record at byte offset off
+    const auto alphas = [&](uint32_t off, float &a0, float &a1) {
+        const float4 P = *reinterpret_cast<const float4 *>(reinterpret_cast<const char *>(sP) + off);
+        const float4 Q = *reinterpret_cast<const float4 *>(reinterpret_cast<const char *>(sQ) + off);
+        const float q0 = poly_q(P, Q.x, Q.y, L0);
+        const float q1 = poly_q(P, Q.x, Q.y, L1);
+        a0 = alpha_of<AM>(Q.z, q0 >= cut ? ex2_approx(q0) : 0.f);
+        a1 = alpha_of<AM>(Q.z, q1 >= cut ? ex2_approx(q1) : 0.f);
+    };
     int nb = 0;  // Gaussians staged in the current batch
     uint32_t vnext[PER];  // next batch's list entries, loaded one batch ahead
     unrolled<PER>([&](int u) { vnext[u] = r.x + t + NT * u < r.y ? vals[r.x + t + NT * u] : 0u; });
@@ -453,40 +469,67 @@ intensity_fwd_tile(const int tile, const StatusDev *st, const uint2 *__restrict_
         __syncthreads();
         nb = min(NB, (int)(r.y - base));
         for (int sub = 0; sub < nb; sub += 32) {
-            // this warp's hits as staged indices, in list order
+            // this warp's hits in list order, as byte offsets of the staged records
             {
                 const uint32_t hm = warp_hits(sM, sub, min(32, nb - sub));
                 __syncwarp();  // every lane has read the previous slice's list
-                if ((hm >> lane) & 1u) wl[__popc(hm & ((1u << lane) - 1u))] = (uint8_t)lane;
+                if ((hm >> lane) & 1u) wl[__popc(hm & ((1u << lane) - 1u))] = (uint16_t)(16 * (sub + lane));
                 nh = __popc(hm);
                 __syncwarp();
             }
-            const int32_t kb = (int32_t)(base + sub + 1);
             // the warp's 64 rays are summed in fixed point by one redux per hit;
-            // lane j keeps the warp's sum for staged Gaussian sub + j, which goes
-            // to shared memory once per 32 staged Gaussians
+            // lane j keeps the warp's biased sum for staged Gaussian sub + j,
+            // which goes to shared memory once per 32 staged Gaussians.  The
+            // loop does not test the floor: a ray that falls below it is found
+            // after the slice, which is then replayed for it.
+            const uint32_t myoff = 16u * (uint32_t)(sub + lane);
+            const float T0s = T0, T1s = T1;
             uint32_t mine = 0u;
             for (int i = 0; i < nh; ++i) {
-                const int jj = wl[i];
-                const float4 P = sP[sub + jj];
-                const float4 Q = sQ[sub + jj];
-                const float q0 = poly_q(P, Q.x, Q.y, L0);
-                const float q1 = poly_q(P, Q.x, Q.y, L1);
-                const bool i0 = (q0 >= cut) & (T0 >= TfloorS);
-                const bool i1 = (q1 >= cut) & (T1 >= TfloorS);
-                const float a0 = alpha_of<AM>(Q.z, i0 ? ex2_approx(q0) : 0.f);
-                const float a1 = alpha_of<AM>(Q.z, i1 ? ex2_approx(q1) : 0.f);
+                const uint32_t off = wl[i];
+                float a0, a1;
+                alphas(off, a0, a1);
                 const uint32_t f = __float_as_uint(__fmaf_rn(a0, T0, S23)) + __float_as_uint(__fmaf_rn(a1, T1, S23));
                 const uint32_t ws = __reduce_add_sync(0xffffffffu, f);
-                mine = lane == jj ? ws - WARP_BIAS : mine;
-                Tp0 = i0 ? T0 : Tp0;
-                Tp1 = i1 ? T1 : Tp1;
-                lj0 = i0 ? kb + jj : lj0;
-                lj1 = i1 ? kb + jj : lj1;
-                T0 = __fmul_rn(T0, __fsub_rn(1.f, a0));
-                T1 = __fmul_rn(T1, __fsub_rn(1.f, a1));
+                mine = off == myoff ? ws : mine;
+                T0 = __fmaf_rn(-a0, T0, T0);
+                T1 = __fmaf_rn(-a1, T1, T1);
             }
-            if (mine != 0u) atomicAdd(&sAcc[sub + lane], mine);
+            // Rays that fell below the floor in this slice (once per ray at
+            // most): the same arithmetic again from the slice's start finds the
+            // stopping pair (T in front of it at or above the floor, behind it
+            // below) and takes the weights of the pairs behind it back out of
+            // the sums (integers: exactly).
+            const bool x0 = (T0 < TfloorS) & (T0s >= TfloorS);
+            const bool x1 = (T1 < TfloorS) & (T1s >= TfloorS);
+            if (__any_sync(0xffffffffu, x0 | x1)) {
+                float R0 = T0s, R1 = T1s;
+                for (int i = 0; i < nh; ++i) {
+                    const uint32_t off = wl[i];
+                    float a0, a1;
+                    alphas(off, a0, a1);
+                    const float N0 = __fmaf_rn(-a0, R0, R0), N1 = __fmaf_rn(-a1, R1, R1);
+                    const uint32_t g0 = x0 & (R0 < TfloorS) ? __float_as_uint(__fmaf_rn(a0, R0, S23)) - S23_BITS : 0u;
+                    const uint32_t g1 = x1 & (R1 < TfloorS) ? __float_as_uint(__fmaf_rn(a1, R1, S23)) - S23_BITS : 0u;
+                    const uint32_t gs = __reduce_add_sync(0xffffffffu, g0 + g1);
+                    mine = off == myoff ? mine - gs : mine;
+                    const int32_t k1 = (int32_t)(base + 1u + (off >> 4));  // list index + 1
+                    if (x0 & (R0 >= TfloorS) & (N0 < TfloorS)) {
+                        sTe[t] = R0;
+                        sLj[t] = -k1;
+                    }
+                    if (x1 & (R1 >= TfloorS) & (N1 < TfloorS)) {
+                        sTe[t + NT] = R1;
+                        sLj[t + NT] = -k1;
+                    }
+                    R0 = N0;
+                    R1 = N1;
+                }
+                T0 = x0 ? 0.f : T0;  // a stopped ray adds nothing further
+                T1 = x1 ? 0.f : T1;
+            }
+            if (nh > 0) wb = (int32_t)(base + 1u + (wl[nh - 1] >> 4));
+            if (mine != 0u && mine != WARP_BIAS) atomicAdd(&sAcc[sub + lane], mine - WARP_BIAS);
         }
     }
     __syncthreads();
@@ -496,13 +539,15 @@ intensity_fwd_tile(const int tile, const StatusDev *st, const uint2 *__restrict_
     });
     if (in0) {
         const int64_t pix = vd.pix_off + (int64_t)py0 * vd.NA + px;
-        Tstop[pix] = Tp0 * (1.f / S23);
-        last[pix] = T0 < TfloorS ? -lj0 : lj0;  // negative: the ray stopped at the floor
+        const int32_t lj = sLj[t];
+        Tend[pix] = (lj < 0 ? sTe[t] : T0) * (1.f / S23);
+        last[pix] = lj < 0 ? lj : wb;
     }
     if (in1) {
         const int64_t pix = vd.pix_off + (int64_t)py1 * vd.NA + px;
-        Tstop[pix] = Tp1 * (1.f / S23);
-        last[pix] = T1 < TfloorS ? -lj1 : lj1;
+        const int32_t lj = sLj[t + NT];
+        Tend[pix] = (lj < 0 ? sTe[t + NT] : T1) * (1.f / S23);
+        last[pix] = lj < 0 ? lj : wb;
     }
 }
 
@@ -510,10 +555,10 @@ template <int AM, int NB>
 __global__ void __launch_bounds__(128)
 k_intensity_fwd(const uint2 *__restrict__ ranges, const uint32_t *__restrict__ vals, const CompRec *__restrict__ comp,
                 const ViewDev *__restrict__ views, int V, float cut, float TfloorS, const StatusDev *st,
-                float *__restrict__ A, float *__restrict__ Tstop, int32_t *__restrict__ last, const TileSched sc) {
+                float *__restrict__ A, float *__restrict__ Tend, int32_t *__restrict__ last, const TileSched sc) {
     if (st->code != SDGR_OK) return;
     for_tiles(sc, st, [&](int tile) {
-        intensity_fwd_tile<AM, NB>(tile, st, ranges, vals, comp, views, V, cut, TfloorS, A, Tstop, last);
+        intensity_fwd_tile<AM, NB>(tile, st, ranges, vals, comp, views, V, cut, TfloorS, A, Tend, last);
     });
 }
 
@@ -524,16 +569,16 @@ static unsigned raster_grid(int tiles, const TileSched &sc) {
 
 cudaError_t launch_intensity_fwd(const uint2 *ranges, const uint32_t *vals, const CompRec *comp, const ViewDev *views,
                                  int V, int tiles, float cut, float Tfloor, int alpha_mode, const StatusDev *st,
-                                 float *A, float *Tstop, int32_t *last, const TileSched &sched, cudaStream_t s) {
+                                 float *A, float *Tend, int32_t *last, const TileSched &sched, cudaStream_t s) {
     if (tiles <= 0) return cudaSuccess;
     const unsigned grid = raster_grid(tiles, sched);
     const int v = (alpha_mode ? 2 : 0) + (sched.nb == 512 ? 1 : 0);
     const float TfloorS = Tfloor * S23;  // exact: a power-of-two scale of a normal float
     switch (v) {
-        case 0: k_intensity_fwd<0, 256><<<grid, TILE_PIX / 2, 0, s>>>(ranges, vals, comp, views, V, cut, TfloorS, st, A, Tstop, last, sched); break;
-        case 1: k_intensity_fwd<0, 512><<<grid, TILE_PIX / 2, 0, s>>>(ranges, vals, comp, views, V, cut, TfloorS, st, A, Tstop, last, sched); break;
-        case 2: k_intensity_fwd<1, 256><<<grid, TILE_PIX / 2, 0, s>>>(ranges, vals, comp, views, V, cut, TfloorS, st, A, Tstop, last, sched); break;
-        default: k_intensity_fwd<1, 512><<<grid, TILE_PIX / 2, 0, s>>>(ranges, vals, comp, views, V, cut, TfloorS, st, A, Tstop, last, sched); break;
+        case 0: k_intensity_fwd<0, 256><<<grid, TILE_PIX / 2, 0, s>>>(ranges, vals, comp, views, V, cut, TfloorS, st, A, Tend, last, sched); break;
+        case 1: k_intensity_fwd<0, 512><<<grid, TILE_PIX / 2, 0, s>>>(ranges, vals, comp, views, V, cut, TfloorS, st, A, Tend, last, sched); break;
+        case 2: k_intensity_fwd<1, 256><<<grid, TILE_PIX / 2, 0, s>>>(ranges, vals, comp, views, V, cut, TfloorS, st, A, Tend, last, sched); break;
+        default: k_intensity_fwd<1, 512><<<grid, TILE_PIX / 2, 0, s>>>(ranges, vals, comp, views, V, cut, TfloorS, st, A, Tend, last, sched); break;
     }
     note_launch();
     return cudaGetLastError();
@@ -831,7 +876,7 @@ template <int AM>
 __device__ __forceinline__ void
 intensity_bwd_tile(const int tile, const StatusDev *st, const uint2 *__restrict__ ranges, const uint32_t *__restrict__ vals,
                    const CompRec *__restrict__ comp, const ImgRec *__restrict__ img, const float4 *__restrict__ accI,
-                   const float *__restrict__ Tstop, const int32_t *__restrict__ last,
+                   const float *__restrict__ Tend, const int32_t *__restrict__ last,
                    const ViewDev *__restrict__ views, int V, float cut, float4 *__restrict__ accC, const uint32_t *sBL) {
     __shared__ float4 sP[BATCH];  // (qa, qb, qc, l1)
     __shared__ float4 sQ[BATCH];  // (l2, c0, o, chat)
@@ -852,8 +897,10 @@ intensity_bwd_tile(const int tile, const StatusDev *st, const uint2 *__restrict_
     const uint2 r = ranges[tile];
     const int32_t rec = c.inside ? last[c.pix] : 0;
     const int32_t mylast = rec < 0 ? -rec : rec;  // negative: the ray stopped at the floor there
-    float T = c.inside ? Tstop[c.pix] : 0.f;  // 0 outside the image: such a lane adds nothing
-    bool first = mylast > 0;  // a ray without in-cutoff pairs never meets one here either
+    float T = c.inside ? Tend[c.pix] : 0.f;  // 0 outside the image: such a lane adds nothing
+    // a stopped ray holds T in front of its stopping pair, which it takes
+    // without a division; any other ray holds T behind its last pair
+    bool first = rec < 0;
     if (t == 0) smax = 0;
     __syncthreads();
     if (mylast > 0) atomicMax(&smax, mylast);
@@ -904,12 +951,10 @@ intensity_bwd_tile(const int tile, const StatusDev *st, const uint2 *__restrict_
                 nh = __popc(hm);
                 __syncwarp();
             }
-            // fast path: every ray of the warp is past its first in-cutoff
-            // Gaussian (walking back to front: the last pair the forward pass
-            // took, the stopping one on a ray that stopped at the floor) --
-            // then every in-cutoff pair still ahead has a lower list index, so
-            // the forward pass took it (no index bound), and T is always
-            // rebuilt by division
+            // fast path: no ray of the warp is a stopped one still behind its
+            // stopping pair (walking back to front) -- then the forward pass
+            // took every in-cutoff pair still ahead (no index bound), and T is
+            // always rebuilt by division
             if (__all_sync(0xffffffffu, !first)) {
                 for (int i = 0; i < nh; i += 2) {
                     // two hits per iteration, back to front (the second may be absent)
@@ -1018,7 +1063,7 @@ intensity_bwd_tile(const int tile, const StatusDev *st, const uint2 *__restrict_
 template <int AM>
 __global__ void __launch_bounds__(256)
 k_intensity_bwd(const uint2 *__restrict__ ranges, const uint32_t *__restrict__ vals, const CompRec *__restrict__ comp,
-                const ImgRec *__restrict__ img, const float4 *__restrict__ accI, const float *__restrict__ Tstop,
+                const ImgRec *__restrict__ img, const float4 *__restrict__ accI, const float *__restrict__ Tend,
                 const int32_t *__restrict__ last, const ViewDev *__restrict__ views, int V, float cut,
                 const StatusDev *st, float4 *__restrict__ accC, const TileSched sc) {
     if (st->code != SDGR_OK) return;
@@ -1026,20 +1071,20 @@ k_intensity_bwd(const uint2 *__restrict__ ranges, const uint32_t *__restrict__ v
     sBL[threadIdx.x] = block_list(threadIdx.x);
     __syncthreads();
     for_tiles(sc, st, [&](int tile) {
-        intensity_bwd_tile<AM>(tile, st, ranges, vals, comp, img, accI, Tstop, last, views, V, cut, accC, sBL);
+        intensity_bwd_tile<AM>(tile, st, ranges, vals, comp, img, accI, Tend, last, views, V, cut, accC, sBL);
     });
 }
 
 cudaError_t launch_intensity_bwd(const uint2 *ranges, const uint32_t *vals, const CompRec *comp, const ImgRec *img,
-                                 const float4 *accI, const float *Tstop, const int32_t *last, const ViewDev *views,
+                                 const float4 *accI, const float *Tend, const int32_t *last, const ViewDev *views,
                                  int V, int tiles, float cut, int alpha_mode, const StatusDev *st, float4 *accC,
                                  const TileSched &sched, cudaStream_t s) {
     if (tiles <= 0) return cudaSuccess;
     if (alpha_mode)
-        k_intensity_bwd<1><<<raster_grid(tiles, sched), TILE_PIX, 0, s>>>(ranges, vals, comp, img, accI, Tstop, last,
+        k_intensity_bwd<1><<<raster_grid(tiles, sched), TILE_PIX, 0, s>>>(ranges, vals, comp, img, accI, Tend, last,
                                                                           views, V, cut, st, accC, sched);
     else
-        k_intensity_bwd<0><<<raster_grid(tiles, sched), TILE_PIX, 0, s>>>(ranges, vals, comp, img, accI, Tstop, last,
+        k_intensity_bwd<0><<<raster_grid(tiles, sched), TILE_PIX, 0, s>>>(ranges, vals, comp, img, accI, Tend, last,
                                                                           views, V, cut, st, accC, sched);
     note_launch();
     return cudaGetLastError();

@@ -231,7 +231,7 @@ cudaError_t launch_ranges(const uint32_t *keys, StatusDev *st, int64_t cap, int6
 // raster passes
 cudaError_t launch_intensity_fwd(const uint2 *ranges, const uint32_t *vals, const CompRec *comp, const ViewDev *views,
                                  int V, int tiles, float cut, float Tfloor, int alpha_mode, const StatusDev *st, float *A,
-                                 float *Tstop, int32_t *last, const TileSched &sched, cudaStream_t s);
+                                 float *Tend, int32_t *last, const TileSched &sched, cudaStream_t s);
 cudaError_t launch_splat_fwd(const uint2 *rangesI, const uint32_t *vals, const ImgRec *img, const CompRec *comp,
                              const float *A, const ViewDev *views, int V, int tiles, float cut, const StatusDev *st,
                              float *images, const TileSched &sched, cudaStream_t s);
@@ -239,7 +239,7 @@ cudaError_t launch_splat_bwd(const uint2 *rangesI, const uint32_t *vals, const I
                              const ViewDev *views, int V, int tiles, float cut, const StatusDev *st, float4 *accI,
                              const TileSched &sched, cudaStream_t s);
 cudaError_t launch_intensity_bwd(const uint2 *ranges, const uint32_t *vals, const CompRec *comp, const ImgRec *img,
-                                 const float4 *accI, const float *Tstop, const int32_t *last, const ViewDev *views,
+                                 const float4 *accI, const float *Tend, const int32_t *last, const ViewDev *views,
                                  int V, int tiles, float cut, int alpha_mode, const StatusDev *st, float4 *accC,
                                  const TileSched &sched, cudaStream_t s);
 // CTAs per SM of a raster kernel at 256 threads (occupancy query, cached).
