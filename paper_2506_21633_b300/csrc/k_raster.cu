@@ -40,6 +40,8 @@
 // moment adds them and issues its atomic.  Entries of
 // blocks that a Gaussian does not reach are never written and never read.  The
 // splat adjoint is Gaussian-parallel over the same hit blocks.
+#include <type_traits>
+
 #include "sdgr_internal.cuh"
 
 namespace sdgr {
@@ -619,7 +621,9 @@ splat_fwd_tile(const int tile, const StatusDev *st, const uint2 *__restrict__ ra
     __shared__ float4 sP[NB];  // (qa, qb, qc, l1)
     __shared__ float4 sQ[NB];  // (l2, c0, c I, 4 l2)
     __shared__ uint32_t sM[NB];
+    __shared__ uint16_t sHL[4 * 32];  // per warp: its hit list of the current slice
     const int t = threadIdx.x, w = t >> 5, l = t & 31;
+    uint16_t *const wl = sHL + 32 * w;
     TileCtx c;
     c.v = view_of_tile(views, V, tile);
     const ViewDev &vd = views[c.v];
@@ -675,11 +679,16 @@ splat_fwd_tile(const int tile, const StatusDev *st, const uint2 *__restrict__ ra
         __syncthreads();
         const int nb = min(NB, (int)(r.y - base));
         for (int k0 = 0; k0 < nb; k0 += 32) {
-            uint32_t hm = warp_hits(sM, k0, min(32, nb - k0));
-            while (hm) {
-                const int k = k0 + __ffs(hm) - 1;
-                hm &= hm - 1;
-                const float4 P0 = sP[k], Q0 = sQ[k];
+            // this warp's hits in list order, as byte offsets of the staged records
+            const uint32_t hm = warp_hits(sM, k0, min(32, nb - k0));
+            __syncwarp();  // every lane has read the previous slice's list
+            if ((hm >> l) & 1u) wl[__popc(hm & ((1u << l) - 1u))] = (uint16_t)(16 * (k0 + l));
+            const int nh = __popc(hm);
+            __syncwarp();
+            for (int i = 0; i < nh; ++i) {
+                const uint32_t off = wl[i];
+                const float4 P0 = *reinterpret_cast<const float4 *>(reinterpret_cast<const char *>(sP) + off);
+                const float4 Q0 = *reinterpret_cast<const float4 *>(reinterpret_cast<const char *>(sQ) + off);
                 const float q0 = poly_q(P0, Q0.x, Q0.y, L);
                 const float q1 = q0 + fmaf(P0.y, X4, fmaf(P0.z, Yt, Q0.w));
                 if (q0 >= cut) acc0 = fmaf(Q0.z, ex2_approx(q0), acc0);
@@ -951,87 +960,58 @@ intensity_bwd_tile(const int tile, const StatusDev *st, const uint2 *__restrict_
                 nh = __popc(hm);
                 __syncwarp();
             }
+            // one hit: the pair's exponent q with the staged record (Q.z: opacity
+            // field, Q.w: c-hat); FAST: no index bound and no stopped ray ahead
+            // of its stopping pair in the warp
+            const auto hit = [&](auto fast, int j, float q, const float4 &Q) {
+                constexpr bool F = decltype(fast)::value;
+                const bool in = F ? q >= cut : (q >= cut) & (sub + j < lim);
+                const float e = in ? ex2_approx(q) : 0.f;
+                const float alpha = alpha_of<AM>(Q.z, e);
+                // relative error of a few ulp per step; the factor 1 - alpha is
+                // the forward's.  Outside the cutoff alpha = 0, and
+                // rcp.approx(1) is exactly 1 (the library's device self-check),
+                // so T stays as it is.
+                const float om = __fsub_rn(1.f, alpha);
+                const float Td = T * rcp_approx(om);
+                if constexpr (F) {
+                    T = Td;
+                } else {
+                    T = (in & !first) ? Td : T;
+                    first = first & !in;
+                }
+                const float d = Q.w - B;
+                B = fmaf(alpha, d, B);
+                // weight of the profile: d alpha / d G = o, or tau (1 - alpha)
+                W[j * WSTRIDE + c.toff] = T * d * (AM ? e * om : e);
+            };
+            // the hit list back to front, two hits per iteration, then an odd one
+            const auto walk = [&](auto fast) {
+                int i = 0;
+                for (; i + 1 < nh; i += 2) {
+                    const uint32_t pr = *reinterpret_cast<const uint16_t *>(wl + i);
+                    const int j0 = (int)(pr & 0xffu), j1 = (int)(pr >> 8);
+                    const float4 P0 = sP[sub + j0], Q0 = sQ[sub + j0];
+                    const float4 P1 = sP[sub + j1], Q1 = sQ[sub + j1];
+                    const float q0 = poly_q(P0, Q0.x, Q0.y, L);
+                    const float q1 = poly_q(P1, Q1.x, Q1.y, L);
+                    hit(fast, j0, q0, Q0);
+                    hit(fast, j1, q1, Q1);
+                }
+                if (i < nh) {
+                    const int j0 = wl[i];
+                    const float4 P0 = sP[sub + j0], Q0 = sQ[sub + j0];
+                    hit(fast, j0, poly_q(P0, Q0.x, Q0.y, L), Q0);
+                }
+            };
             // fast path: no ray of the warp is a stopped one still behind its
             // stopping pair (walking back to front) -- then the forward pass
             // took every in-cutoff pair still ahead (no index bound), and T is
             // always rebuilt by division
-            if (__all_sync(0xffffffffu, !first)) {
-                for (int i = 0; i < nh; i += 2) {
-                    // two hits per iteration, back to front (the second may be absent)
-                    const uint32_t pr = *reinterpret_cast<const uint16_t *>(wl + i);
-                    const int j0 = (int)(pr & 0xffu);
-                    const bool two = i + 1 < nh;
-                    const int j1 = two ? (int)(pr >> 8) : j0;
-                    const float4 P0 = sP[sub + j0], Q0 = sQ[sub + j0];
-                    const float4 P1 = sP[sub + j1], Q1 = sQ[sub + j1];
-                    const float q0 = poly_q(P0, Q0.x, Q0.y, L);
-                    const float q1 = poly_q(P1, Q1.x, Q1.y, L);
-                    {
-                        const bool in = q0 >= cut;
-                        const float e = in ? ex2_approx(q0) : 0.f;
-                        const float alpha = alpha_of<AM>(Q0.z, e);
-                        // relative error of a few ulp per step; the factor 1 - alpha is
-                        // the forward's (same alpha bits, same rounding).  Outside the
-                        // cutoff alpha = 0, and rcp.approx(1) is exactly 1 (the
-                        // library's device self-check), so T stays as it is.
-                        const float om = __fsub_rn(1.f, alpha);
-                        T = T * rcp_approx(om);
-                        const float d = Q0.w - B;
-                        B = fmaf(alpha, d, B);
-                        // weight of the profile: d alpha / d G = o, or tau (1 - alpha)
-                        W[j0 * WSTRIDE + c.toff] = T * d * (AM ? e * om : e);
-                    }
-                    {
-                        const bool in = two & (q1 >= cut);
-                        const float e = in ? ex2_approx(q1) : 0.f;
-                        const float alpha = alpha_of<AM>(Q1.z, e);
-                        const float om = __fsub_rn(1.f, alpha);
-                        T = T * rcp_approx(om);
-                        const float d = Q1.w - B;
-                        B = fmaf(alpha, d, B);
-                        if (two) W[j1 * WSTRIDE + c.toff] = T * d * (AM ? e * om : e);
-                    }
-                }
-            } else {
-                for (int i = 0; i < nh; i += 2) {
-                    // two hits per iteration, back to front (the second may be absent)
-                    const uint32_t pr = *reinterpret_cast<const uint16_t *>(wl + i);
-                    const int j0 = (int)(pr & 0xffu);
-                    const bool two = i + 1 < nh;
-                    const int j1 = two ? (int)(pr >> 8) : j0;
-                    const float4 P0 = sP[sub + j0], Q0 = sQ[sub + j0];
-                    const float4 P1 = sP[sub + j1], Q1 = sQ[sub + j1];
-                    const float q0 = poly_q(P0, Q0.x, Q0.y, L);
-                    const float q1 = poly_q(P1, Q1.x, Q1.y, L);
-                    {
-                        const bool in = (q0 >= cut) & (sub + j0 < lim);
-                        const float e = in ? ex2_approx(q0) : 0.f;
-                        const float alpha = alpha_of<AM>(Q0.z, e);
-                        // relative error of a few ulp per step; the factor 1 - alpha is
-                        // the forward's (same alpha bits, same rounding)
-                        const float om = __fsub_rn(1.f, alpha);
-                        const float Td = T * rcp_approx(om);
-                        T = (in & !first) ? Td : T;
-                        first = first & !in;
-                        const float d = Q0.w - B;
-                        B = fmaf(alpha, d, B);
-                        // weight of the profile: d alpha / d G = o, or tau (1 - alpha)
-                        W[j0 * WSTRIDE + c.toff] = T * d * (AM ? e * om : e);
-                    }
-                    {
-                        const bool in = two & (q1 >= cut) & (sub + j1 < lim);
-                        const float e = in ? ex2_approx(q1) : 0.f;
-                        const float alpha = alpha_of<AM>(Q1.z, e);
-                        const float om = __fsub_rn(1.f, alpha);
-                        const float Td = T * rcp_approx(om);
-                        T = (in & !first) ? Td : T;
-                        first = first & !in;
-                        const float d = Q1.w - B;
-                        B = fmaf(alpha, d, B);
-                        if (two) W[j1 * WSTRIDE + c.toff] = T * d * (AM ? e * om : e);
-                    }
-                }
-            }
+            if (__all_sync(0xffffffffu, !first))
+                walk(std::true_type{});
+            else
+                walk(std::false_type{});
             __syncthreads();
             const int j = sperm[sl * SUB + (t >> 3)], cc = t & 7;
             const uint32_t mb = j < ns ? sM[sub + j] : 0u;
