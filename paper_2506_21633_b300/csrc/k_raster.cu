@@ -685,6 +685,7 @@ splat_fwd_tile(const int tile, const StatusDev *st, const uint2 *__restrict__ ra
             if ((hm >> l) & 1u) wl[__popc(hm & ((1u << l) - 1u))] = (uint16_t)(16 * (k0 + l));
             const int nh = __popc(hm);
             __syncwarp();
+#pragma unroll 8
             for (int i = 0; i < nh; ++i) {
                 const uint32_t off = wl[i];
                 const float4 P0 = *reinterpret_cast<const float4 *>(reinterpret_cast<const char *>(sP) + off);
