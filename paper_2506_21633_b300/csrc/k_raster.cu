@@ -487,6 +487,7 @@ intensity_fwd_tile(const int tile, const StatusDev *st, const uint2 *__restrict_
             const uint32_t myoff = 16u * (uint32_t)(sub + lane);
             const float T0s = T0, T1s = T1;
             uint32_t mine = 0u;
+#pragma unroll 8
             for (int i = 0; i < nh; ++i) {
                 const uint32_t off = wl[i];
                 float a0, a1;
