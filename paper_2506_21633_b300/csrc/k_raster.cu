@@ -969,23 +969,36 @@ intensity_bwd_tile(const int tile, const StatusDev *st, const uint2 *__restrict_
                 constexpr bool F = decltype(fast)::value;
                 const bool in = F ? q >= cut : (q >= cut) & (sub + j < lim);
                 const float e = in ? ex2_approx(q) : 0.f;
-                const float alpha = alpha_of<AM>(Q.z, e);
-                // relative error of a few ulp per step; the factor 1 - alpha is
-                // the forward's.  Outside the cutoff alpha = 0, and
-                // rcp.approx(1) is exactly 1 (the library's device self-check),
-                // so T stays as it is.
-                const float om = __fsub_rn(1.f, alpha);
-                const float Td = T * rcp_approx(om);
-                if constexpr (F) {
-                    T = Td;
+                // T in front of the pair: T behind it / (1 - alpha), relative
+                // error of a few ulp per step.  Outside the cutoff alpha = 0,
+                // and rcp.approx(1) is exactly 1 (the library's device
+                // self-check), so T stays as it is.
+                const auto rebuild = [&](float om) {
+                    const float Td = T * rcp_approx(om);
+                    if constexpr (F) {
+                        T = Td;
+                    } else {
+                        T = (in & !first) ? Td : T;
+                        first = first & !in;
+                    }
+                };
+                if constexpr (AM == 0) {
+                    // alpha = o e: 1 - alpha in one rounding, and B += alpha d
+                    // as o (e d), e d being the weight's factor as well
+                    rebuild(__fmaf_rn(-Q.z, e, 1.f));
+                    const float ed = e * (Q.w - B);
+                    B = fmaf(Q.z, ed, B);
+                    // weight of the profile: d alpha / d G = o
+                    W[j * WSTRIDE + c.toff] = T * ed;
                 } else {
-                    T = (in & !first) ? Td : T;
-                    first = first & !in;
+                    const float alpha = alpha_of<AM>(Q.z, e);
+                    const float om = __fsub_rn(1.f, alpha);
+                    rebuild(om);
+                    const float d = Q.w - B;
+                    B = fmaf(alpha, d, B);
+                    // weight of the profile: d alpha / d G = tau (1 - alpha)
+                    W[j * WSTRIDE + c.toff] = T * d * (e * om);
                 }
-                const float d = Q.w - B;
-                B = fmaf(alpha, d, B);
-                // weight of the profile: d alpha / d G = o, or tau (1 - alpha)
-                W[j * WSTRIDE + c.toff] = T * d * (AM ? e * om : e);
             };
             // the hit list back to front, two hits per iteration, then an odd one
             const auto walk = [&](auto fast) {
