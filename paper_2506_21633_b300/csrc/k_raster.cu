@@ -897,10 +897,10 @@ intensity_bwd_tile(const int tile, const StatusDev *st, const uint2 *__restrict_
     __shared__ uint8_t sperm[BATCH];
     __shared__ __align__(16) float W[SUB * WSTRIDE];
     __shared__ __align__(16) float zero4[4];
-    __shared__ __align__(4) uint8_t sHL[8 * 32];  // per warp: its hit list of the current slice
+    __shared__ __align__(4) uint16_t sHL[8 * 32];  // per warp: its hit list of the current slice
     __shared__ int smax;
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
-    uint8_t *const wl = sHL + 32 * warp;
+    uint16_t *const wl = sHL + 32 * warp;
     int nh = 0;
     if (t < 4) zero4[t] = 0.f;
     const TileCtx c = tile_ctx(views, V, tile);
@@ -955,19 +955,25 @@ intensity_bwd_tile(const int tile, const StatusDev *st, const uint2 *__restrict_
         for (int sl = 0; sl * SUB < nb; ++sl) {
             const int send = nb - sl * SUB, sub = max(0, send - SUB);
             const int ns = send - sub;
-            // this warp's hits as staged indices, back to front (descending)
+            // this warp's hits back to front (descending), as byte offsets 16 k
+            // of the staged records k
             {
                 const uint32_t hm = warp_hits(sM, sub, ns);
-                if ((hm >> lane) & 1u) wl[__popc(hm >> lane) - 1] = (uint8_t)lane;
+                if ((hm >> lane) & 1u) wl[__popc(hm >> lane) - 1] = (uint16_t)(16 * (sub + lane));
                 nh = __popc(hm);
                 __syncwarp();
             }
-            // one hit: the pair's exponent q with the staged record (Q.z: opacity
-            // field, Q.w: c-hat); FAST: no index bound and no stopped ray ahead
-            // of its stopping pair in the warp
-            const auto hit = [&](auto fast, int j, float q, const float4 &Q) {
+            // the table entry of staged record k for this ray: byte
+            // 66 (16 k) + wb = 4 ((k - sub) WSTRIDE + toff)
+            static_assert(WSTRIDE * 4 == 66 * 16, "weight table row: 66 record strides");
+            const int wb = 4 * c.toff - 4 * WSTRIDE * sub;
+            // one hit: the pair's exponent q with the staged record at byte
+            // offset off (Q.z: opacity field, Q.w: c-hat); FAST: no index bound
+            // and no stopped ray ahead of its stopping pair in the warp
+            const auto hit = [&](auto fast, uint32_t off, float q, const float4 &Q) {
                 constexpr bool F = decltype(fast)::value;
-                const bool in = F ? q >= cut : (q >= cut) & (sub + j < lim);
+                const bool in = F ? q >= cut : (q >= cut) & ((int)(off >> 4) < lim);
+                float *const wp = reinterpret_cast<float *>(reinterpret_cast<char *>(W) + (int)(off * 66u) + wb);
                 const float e = in ? ex2_approx(q) : 0.f;
                 // T in front of the pair: T behind it / (1 - alpha), relative
                 // error of a few ulp per step.  Outside the cutoff alpha = 0,
@@ -989,7 +995,7 @@ intensity_bwd_tile(const int tile, const StatusDev *st, const uint2 *__restrict_
                     const float ed = e * (Q.w - B);
                     B = fmaf(Q.z, ed, B);
                     // weight of the profile: d alpha / d G = o
-                    W[j * WSTRIDE + c.toff] = T * ed;
+                    *wp = T * ed;
                 } else {
                     const float alpha = alpha_of<AM>(Q.z, e);
                     const float om = __fsub_rn(1.f, alpha);
@@ -997,26 +1003,29 @@ intensity_bwd_tile(const int tile, const StatusDev *st, const uint2 *__restrict_
                     const float d = Q.w - B;
                     B = fmaf(alpha, d, B);
                     // weight of the profile: d alpha / d G = tau (1 - alpha)
-                    W[j * WSTRIDE + c.toff] = T * d * (e * om);
+                    *wp = T * d * (e * om);
                 }
             };
             // the hit list back to front, two hits per iteration, then an odd one
             const auto walk = [&](auto fast) {
                 int i = 0;
+                const auto rec = [&](const float4 *a, uint32_t off) {
+                    return *reinterpret_cast<const float4 *>(reinterpret_cast<const char *>(a) + off);
+                };
                 for (; i + 1 < nh; i += 2) {
-                    const uint32_t pr = *reinterpret_cast<const uint16_t *>(wl + i);
-                    const int j0 = (int)(pr & 0xffu), j1 = (int)(pr >> 8);
-                    const float4 P0 = sP[sub + j0], Q0 = sQ[sub + j0];
-                    const float4 P1 = sP[sub + j1], Q1 = sQ[sub + j1];
+                    const uint32_t pr = *reinterpret_cast<const uint32_t *>(wl + i);
+                    const uint32_t o0 = pr & 0xffffu, o1 = pr >> 16;
+                    const float4 P0 = rec(sP, o0), Q0 = rec(sQ, o0);
+                    const float4 P1 = rec(sP, o1), Q1 = rec(sQ, o1);
                     const float q0 = poly_q(P0, Q0.x, Q0.y, L);
                     const float q1 = poly_q(P1, Q1.x, Q1.y, L);
-                    hit(fast, j0, q0, Q0);
-                    hit(fast, j1, q1, Q1);
+                    hit(fast, o0, q0, Q0);
+                    hit(fast, o1, q1, Q1);
                 }
                 if (i < nh) {
-                    const int j0 = wl[i];
-                    const float4 P0 = sP[sub + j0], Q0 = sQ[sub + j0];
-                    hit(fast, j0, poly_q(P0, Q0.x, Q0.y, L), Q0);
+                    const uint32_t o0 = wl[i];
+                    const float4 P0 = rec(sP, o0), Q0 = rec(sQ, o0);
+                    hit(fast, o0, poly_q(P0, Q0.x, Q0.y, L), Q0);
                 }
             };
             // fast path: no ray of the warp is a stopped one still behind its
