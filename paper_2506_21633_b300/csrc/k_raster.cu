@@ -214,9 +214,11 @@ __device__ __forceinline__ void block_moments(const float4 &w, float dx, float d
 }
 
 // Block list of an 8-bit block set m: the indices of its set bits in
-// increasing order, four bits each (the i-th in bits 4i .. 4i + 3).  Built
-// once per CTA into a 256-entry shared table, so that a phase-2 loop walks a
-// Gaussian's blocks with a shift and a mask per block.
+// increasing order, four bits each (the i-th in bits 4i .. 4i + 3), and 8 in
+// the nibbles past them (a block of zeros for a loop that walks more blocks
+// than the set has).  Built once per CTA into a 256-entry shared table, so
+// that a phase-2 loop walks a Gaussian's blocks with a shift and a mask per
+// block.
 __device__ __forceinline__ uint32_t block_list(uint32_t m) {
     uint32_t l = 0u;
     int n = 0;
@@ -226,7 +228,7 @@ __device__ __forceinline__ uint32_t block_list(uint32_t m) {
             l |= (uint32_t)b << (4 * n);
             ++n;
         }
-    return l;
+    return n < 8 ? l | (0x88888888u << (4 * n)) : l;
 }
 
 // Sum of the six moments over a group of eight threads (cc = 0..7) and one
@@ -748,14 +750,15 @@ splat_bwd_tile(const int tile, const StatusDev *st, const uint2 *__restrict__ ra
     __shared__ uint32_t sM[NB];
     __shared__ uint32_t sid[NB];
     __shared__ uint8_t sperm[NB];
-    __shared__ __align__(16) float sg[TILE_PIX];  // dL/dS of the tile's pixels, in table layout
-    __shared__ __align__(16) float zero4[4];
+    // dL/dS of the tile's pixels in table layout, then a block of zeros (block
+    // index 8 of the padded block lists)
+    __shared__ __align__(16) float sg[TILE_PIX + 32];
     const int t = threadIdx.x, warp = t >> 5;
-    if (t < 4) zero4[t] = 0.f;
     const TileCtx c = tile_ctx(views, V, tile);
     const uint2 r = rangesI[tile];
     const float g = c.inside ? dLdS[c.pix] : 0.f;
     sg[c.toff] = g;
+    if (t < 32) sg[TILE_PIX + t] = 0.f;
     if (__syncthreads_count(g != 0.f) == 0) return;
     const float cutm = cut_margin(cut);
     uint32_t vnext[PER];  // next batch's list entries, loaded one batch ahead
@@ -800,11 +803,10 @@ splat_bwd_tile(const int tile, const StatusDev *st, const uint2 *__restrict__ ra
             float m[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
             const int rounds = __reduce_max_sync(0xffffffffu, cnt);
             for (int i = 0; i < rounds; ++i) {
-                const int b = (int)(bl & 7u);
+                const int b = (int)(bl & 15u);  // 8 past the Gaussian's blocks: zeros
                 bl >>= 4;
-                const bool live = i < cnt;
-                const float *src = live ? sg + 32 * b + 4 * c2 : zero4;  // no block left: dL/dS = 0
-                const int step = live ? 8 : 0;
+                const float *src = sg + 32 * b + 4 * c2;
+                constexpr int step = 8;
                 const float dxa = (b & 1) ? dxa0 + 8.f : dxa0;
                 const float dy0 = fmaf(4.f, small_u2f((uint32_t)b >> 1), dy00);
 #pragma unroll
