@@ -121,8 +121,9 @@ __device__ __forceinline__ LaneXY lane_xy() {
 // relative to the tile origin and the pre-scaled conic (qa, qb, qc), the
 // exponent qa dx^2 + qb dx dy + qc dy^2 at dx = X - u, dy = Y - v equals
 // qa X^2 + qb XY + qc Y^2 + l1 X + l2 Y + c0.  Explicit round-to-nearest
-// intrinsics: every kernel that evaluates a pair must get the same bits (the
-// adjoint rebuilds the transmittance from the forward's factors).
+// intrinsics: the intensity pass and its adjoint get the same exponent bits
+// for a pair, so they agree on which pairs are inside the cutoff (the adjoint
+// divides out exactly the factors the forward multiplied in).
 __device__ __forceinline__ void poly_coeffs(float u, float v, float qa, float qb, float qc, float4 &P, float2 &Q) {
     const float l1 = -__fmaf_rn(2.f * qa, u, __fmul_rn(qb, v));
     const float l2 = -__fmaf_rn(2.f * qc, v, __fmul_rn(qb, u));
@@ -279,7 +280,7 @@ __device__ __forceinline__ void order_by_blocks(const uint32_t *sM, int k0, int 
 // Opacity of a pair from the record's opacity field o (o itself, or the
 // optical depth tau of the Beer-Lambert mode AM = 1) and the profile
 // e = exp(-delta/2) (0 for a pair that is skipped).  Explicit round-to-nearest
-// operations: the intensity pass and its adjoint must get the same bits.
+// operations, reproducible wherever a pair is evaluated.
 template <int AM>
 __device__ __forceinline__ float alpha_of(float o, float e) {
     if (AM == 0) return __fmul_rn(o, e);
