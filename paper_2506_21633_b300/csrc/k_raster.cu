@@ -47,6 +47,7 @@
 namespace sdgr {
 
 constexpr int BATCH = 256;    // Gaussian records staged per batch by the intensity adjoint
+static_assert(BATCH <= TILE_PIX && BATCH % 32 == 0, "the intensity adjoint stages one record per thread");
 constexpr int SUB = 32;       // Gaussians per weight table
 constexpr int WSTRIDE = 264;  // row stride of the weight table (floats)
 
@@ -1159,14 +1160,15 @@ template <typename Rec>
 __global__ void __launch_bounds__(256)
 k_count_pairs(const uint2 *__restrict__ ranges, const uint32_t *__restrict__ vals, const Rec *__restrict__ rec,
               const ViewDev *__restrict__ views, int V, float cut, unsigned long long *out) {
-    __shared__ float4 sA[BATCH];
-    __shared__ float sC[BATCH];
+    constexpr int CB = TILE_PIX;  // records staged per batch: one per thread of the launch
+    __shared__ float4 sA[CB];
+    __shared__ float sC[CB];
     const int t = threadIdx.x;
     const TileCtx c = tile_ctx(views, V, blockIdx.x);
     const uint2 r = ranges[blockIdx.x];
     const float fx = (float)c.px, fy = (float)c.py;
     unsigned int n = 0;
-    for (uint32_t base = r.x; base < r.y; base += BATCH) {
+    for (uint32_t base = r.x; base < r.y; base += CB) {
         __syncthreads();
         const uint32_t j = base + t;
         if (j < r.y) {
@@ -1175,7 +1177,7 @@ k_count_pairs(const uint2 *__restrict__ ranges, const uint32_t *__restrict__ val
             sC[t] = p[1].x;
         }
         __syncthreads();
-        const int nb = min(BATCH, (int)(r.y - base));
+        const int nb = min(CB, (int)(r.y - base));
         if (c.inside)
             for (int k = 0; k < nb; ++k) {
                 const float4 a = sA[k];
