@@ -7,9 +7,15 @@ adjoint, intensity adjoint, parameter adjoint, Adam -- every kernel of the
 hot path, on synthetic inputs shaped like the paper's (a 6x3x2 m vehicle-
 sized box of 300k randomly rotated Gaussians, 64 views with grazing angles
 U[30, 60] deg, 1024x1024 images at 0.01 m).  The L1 target is the rendering
-of the unperturbed scene; the optimised scene is a perturbed copy.
+of the unperturbed scene; the optimised scene is a perturbed copy.  The K
+timed steps are one replay of a captured CUDA graph of K such steps.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl sdgr|reference]
+
+The default line also carries, at N = 1, the rest of the metric in shortened
+runs: the uneven batch (256 scenes, batched vs plain; `config4`) and serving
+under Poisson arrivals (p50/p99; `serving`).  `--workload config4` and
+`--workload serve` run each of them in full on its own.
 
 For N > 1 (one process per GPU under torchrun) every rank runs its own
 independent replica of the workload (different views): weak scaling, no
@@ -36,16 +42,18 @@ if ROOT not in sys.path:
 METRIC = "fwd+bwd views/s at 300k Gaussians, 1024² (batched vs plain); serving p50/p99 ms"
 UNIT = "views/s"
 
-# Algorithmic work per in-cutoff (pixel, Gaussian) pair: (FP32 ops, MUFU ops).
-# FP32-pipe-equivalent ops = fp32 + 8 * mufu (the SFU has 16 lanes per SM,
-# the FP32 pipe 128).  The exponent counts 5 ops (a quadratic in the pixel's
-# tile-local coordinates with per-tile coefficients).  Derivation in the
-# design notes.
+# Algorithmic instructions per in-cutoff (pixel, Gaussian) pair: (FP32
+# add/mul/fma, ex2, rcp).  The exponent counts 5 (a quadratic in the pixel's
+# tile-local coordinates with per-tile coefficients).  An FP32 instruction
+# takes one of the SM's 128 lane-issue slots per cycle; an SFU instruction
+# takes what it was measured to cost inside an FP32 stream (sdgr_pipe_rates,
+# live) and also occupies the SFU pipe at its measured rate.  Derivation in
+# the design notes.
 ALG_OPS = {
-    "intensity_fwd": (11, 1),
-    "splat_fwd": (7, 1),
-    "splat_bwd": (18, 1),
-    "intensity_bwd": (26, 2),
+    "intensity_fwd": (11, 1, 0),
+    "splat_fwd": (7, 1, 0),
+    "splat_bwd": (18, 1, 0),
+    "intensity_bwd": (26, 1, 1),
 }
 PLANE = {"intensity_fwd": 0, "splat_fwd": 1, "splat_bwd": 1, "intensity_bwd": 0}
 KERNEL_NAME = {"intensity_fwd": "k_intensity_fwd", "splat_fwd": "k_splat_fwd", "splat_bwd": "k_splat_bwd",
@@ -69,6 +77,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-config4", action="store_true", help="skip the uneven-batch (config 4) leg")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving (config 5) leg")
     return ap.parse_args()
 
 
@@ -181,7 +191,7 @@ def measured_peaks():
 
 
 def alu_peak_tops(sms, mhz):
-    """FP32-pipe peak: SMs x 128 lanes x clock (ops/s), in Tops/s."""
+    """Lane-issue peak (= FP32 peak): SMs x 128 lanes x clock, in Tops/s."""
     return sms * 128 * mhz * 1e6 / 1e12
 
 
@@ -229,6 +239,46 @@ def workload(name, rank):
     return params, start, views, desc
 
 
+def sfu_slot_cost(rates):
+    """Issue-slot cost of one ex2 and one rcp inside an FP32 stream, from the
+    measured rates of streams with one SFU instruction per seven fma: eight
+    instructions take 8 r_fma / r_mix slots, seven of them fma."""
+    out = {}
+    for k in ("ex2", "rcp"):
+        mix = (rates or {}).get(k + "_in_ffma_stream")
+        fma = (rates or {}).get("ffma")
+        out[k] = max(1.0, 8.0 * fma / mix - 7.0) if mix and fma else 8.0  # no measurement: SFU lanes 16 of 128
+    return out
+
+
+def raster_roofline(stage_ms, pairs, sms, mhz, rates):
+    """Per raster kernel: the least time its algorithmic instructions need on
+    this GPU against its measured time.  Peak: SMs x 128 lane-issue slots per
+    cycle (the FP32 lane count).  An FP32 instruction takes one slot, an SFU
+    instruction the slots it was measured to cost inside an FP32 stream;
+    separately, the SFU pipe at its measured rate.  The larger bound binds."""
+    out = {}
+    f = mhz * 1e6
+    w = sfu_slot_cost(rates)
+    r_ex2 = (rates or {}).get("ex2") or 16.0
+    r_rcp = (rates or {}).get("rcp") or 16.0
+    for k, (fp, ex2, rcp) in ALG_OPS.items():
+        if k not in stage_ms or stage_ms[k] <= 0:
+            continue
+        n = pairs[PLANE[k]]
+        t = stage_ms[k] / 1e3
+        slots = fp + w["ex2"] * ex2 + w["rcp"] * rcp
+        t_issue = n * slots / (sms * 128 * f)
+        t_sfu = n * (ex2 / r_ex2 + rcp / r_rcp) / (sms * f)
+        ach = n * slots / t / 1e12
+        out[KERNEL_NAME[k]] = {"ms_per_launch": round(stage_ms[k], 4), "pairs_per_launch": n,
+                               "instr_per_pair": {"fp32": fp, "ex2": ex2, "rcp": rcp},
+                               "slots_per_pair": round(slots, 3), "achieved": round(ach, 3),
+                               "frac": round(max(t_issue, t_sfu) / t, 4), "frac_issue": round(t_issue / t, 4),
+                               "frac_sfu_pipe": round(t_sfu / t, 4), "binds": "issue" if t_issue >= t_sfu else "sfu"}
+    return out
+
+
 def run_sdgr(args):
     import numpy as np
     import torch
@@ -236,13 +286,22 @@ def run_sdgr(args):
     torch.cuda.set_device(local)
     dist_setup("nccl")
     dev = torch.device("cuda", local)
-    from paper_2506_21633_b300 import _lib, tune
-    from paper_2506_21633_b300.render import Renderer, adam_step, l1_loss, views_npix
+    from paper_2506_21633_b300 import _lib
+    from paper_2506_21633_b300.batch import FusedStep
+    from paper_2506_21633_b300.render import Renderer, l1_loss, views_npix
 
     params, start, views, desc = workload(args.workload, rank)
     V = len(views)
     npix = views_npix(views)
     stream = torch.cuda.current_stream(dev)
+    K = args.steps
+
+    # pipe rates of this GPU (the roofline's SFU bound)
+    rates = None
+    if rank == 0:
+        scratch = torch.empty(_lib.PIPE_RATES_SCRATCH, dtype=torch.uint8, device=dev)
+        rates = {k: round(v, 3) for k, v in _lib.sdgr_pipe_rates(scratch.data_ptr(), stream.cuda_stream).items()}
+        del scratch
 
     # targets: rendering of the unperturbed scene
     tgt_renderer = Renderer(device=dev)
@@ -250,89 +309,72 @@ def run_sdgr(args):
     tgt_renderer.prepare(p_true, views)
     targets = tgt_renderer.forward()
     torch.cuda.synchronize(dev)
-    del tgt_renderer
+    del tgt_renderer, p_true
 
     p = torch.from_numpy(start.astype(np.float32)).to(dev).contiguous()
-    m = torch.zeros_like(p)
-    v = torch.zeros_like(p)
-    grads = torch.empty_like(p)
-    images = torch.empty(npix, dtype=torch.float32, device=dev)
-    dLdS = torch.empty_like(images)
-    loss = torch.empty(1, dtype=torch.float32, device=dev)
-    r = Renderer(device=dev)
-    r.prepare(p, views)  # learns the instance capacity (one host sync)
-    state = {"t": 0}
-
-    def step():
-        state["t"] += 1
-        r.prepare(p, views, check=False)
-        r.forward(images=images)
-        l1_loss(images, targets, dLdS, loss)
-        r.backward(dLdS, grads)
-        adam_step(p, grads, m, v, LR, state["t"])
-
-    for _ in range(max(args.warmup, 0)):
-        step()
-    torch.cuda.synchronize(dev)
-    code, required = r.status()
-    if code != _lib.SDGR_OK:  # capacity grew during warm-up: re-plan once
-        r.prepare(p, views, instances=int(required * 1.2))
-        for _ in range(max(args.warmup, 1)):
-            step()
-        torch.cuda.synchronize(dev)
-        code, required = r.status()
-        assert code == _lib.SDGR_OK, "device status %d" % code
-    pairs = r.count_pairs()
+    fs = FusedStep(p, views, targets, lr=LR)  # learns the instance capacity (one host sync)
     schedule_ms, stage_batch_ms = None, None
-    if args.schedule == "auto":  # untimed: the schedule, then each raster kernel's staging batch
-        _, schedule_ms = tune.tune_schedule(r, step, steps=2)
+    if args.schedule == "auto":  # untimed; the optimiser state is restored afterwards
+        _, schedule_ms = fs.autotune(steps=2)
         schedule_ms = {k: round(v, 3) for k, v in schedule_ms.items()}
         stage_batch_ms = {k: {nb: round(ms, 3) for nb, ms in d.items()}
-                          for k, (_, d) in tune.tune_stage_batches(r, step, steps=2).items()}
+                          for k, (_, d) in fs.stage_batch_ms.items()}
     else:
-        r.set_schedule(args.schedule)
-    r.profile(True)
-    r.profile_read(reset=True)
+        fs.r.set_schedule(args.schedule)
 
-    # ---- timed region (device time, CUDA events on the launching stream)
+    # warm-up: W replays of the one-step graph
+    fs.capture()
+    for attempt in range(3):
+        for _ in range(max(args.warmup, 0)):
+            fs.step()
+        if fs.check():  # capacity: on overflow the workspace grows, the graph is captured again
+            break
+    else:
+        raise RuntimeError("instance capacity still exceeded after warm-up")
+    pairs = fs.r.count_pairs()
+
+    # the timed region is one replay of a graph of K steps (stage events inside
+    # it as graph nodes); one untimed replay first
+    gK = fs.capture_graph(steps=K, profile=True)
+    launches = fs.graph_launches
+    gK.replay()
+    assert fs.check(), "instance capacity exceeded in the K-step graph"
+
     sampler = ClockSampler(local) if rank == 0 else None
     barrier()
     torch.cuda.synchronize(dev)
     if sampler:
         sampler.start()
         time.sleep(0.3)
-    launches0 = _lib.sdgr_launch_count()
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
-    for _ in range(args.steps):
-        step()
+    gK.replay()
     ev1.record(stream)
     torch.cuda.synchronize(dev)
-    launches = _lib.sdgr_launch_count() - launches0
     clocks = sampler.stop() if sampler else None
     barrier()
     ms_local = ev0.elapsed_time(ev1)
-    prof = r.profile_read(reset=True)
-    r.profile(False)
-    code, _ = r.status()
+    prof = fs.r.profile_read(reset=True)
+    code, _ = fs.r.status()
     assert code == _lib.SDGR_OK, "device status %d after the timed region" % code
     ms_max = max_over_ranks(ms_local, dev)
-    views_total = sum_over_ranks(V * args.steps, dev)
+    views_total = sum_over_ranks(V * K, dev)
     value = views_total / (ms_max / 1e3)
-    ms_per_step = ms_max / args.steps
+    ms_per_step = ms_max / K
+    del gK
 
     # ---- plain: per-view calls with a stream sync after each view
     plain = None
     if not args.no_plain and rank == 0:
         rp = Renderer(device=dev)
         gacc = torch.empty_like(p)
-        one = [views[0]]
-        rp.prepare(p, one, instances=r.n_inst)  # the batch total bounds any single view
+        images, dLdS = fs.images, fs.dLdS
+        loss = torch.empty(1, dtype=torch.float32, device=dev)
+        rp.prepare(p, [views[0]], instances=fs.r.n_inst)  # the batch total bounds any single view
         n_plain_steps = 2
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
-        off = 0
         for s in range(n_plain_steps):
             off = 0
             for k, vw in enumerate(views):
@@ -346,33 +388,35 @@ def run_sdgr(args):
                 off += n
         torch.cuda.synchronize(dev)
         t_plain = (time.perf_counter() - t0) / n_plain_steps
-        code, _ = rp.status()
-        plain = {"value": V / t_plain, "unit": UNIT, "ms_per_step": t_plain * 1e3,
+        plain = {"value": round(V / t_plain, 3), "unit": UNIT, "ms_per_step": round(t_plain * 1e3, 3),
                  "how": "per-view preprocess/sort/fwd/loss/bwd calls, stream sync after each view"}
-        del rp
+        del rp, gacc
 
-    # ---- end to end through the public API with host buffers: every step copies
-    # its targets from pinned host memory (on a copy stream, into one of two
-    # device buffers, while the previous step computes) and reads its loss back
-    # to the host (read after the next step has been enqueued)
+    # ---- end to end through the public API with host buffers: every step
+    # copies its targets from pinned host memory (copy stream, into one of two
+    # device buffers, each with its own captured one-step graph, while the
+    # previous step computes) and reads its loss back to the host (after the
+    # next step has been enqueued)
     e2e = None
     if not args.no_e2e:
         host_t = torch.empty(npix, dtype=torch.float32, pin_memory=True)
         host_t.copy_(targets.cpu())
         tbuf = [torch.empty_like(targets) for _ in range(2)]
+        for b in range(2):
+            tbuf[b].copy_(targets)
+        graphs = [fs.capture_graph(targets=tbuf[b]) for b in range(2)]
         loss_host = torch.zeros(2, dtype=torch.float32, pin_memory=True)
         copy_stream = torch.cuda.Stream(device=dev)
         ev_copied = [torch.cuda.Event() for _ in range(2)]
         ev_used = [torch.cuda.Event() for _ in range(2)]
         ev_loss = [torch.cuda.Event() for _ in range(2)]
-        n_e2e = max(3, min(args.steps, 10))
         losses = []
 
         def h2d(k):
             b = k % 2
             with torch.cuda.stream(copy_stream):
                 if k >= 2:
-                    copy_stream.wait_event(ev_used[b])  # step k - 2 has read this buffer
+                    copy_stream.wait_event(ev_used[b])  # step k - 2 has finished with this buffer
                 tbuf[b].copy_(host_t, non_blocking=True)
                 ev_copied[b].record(copy_stream)
 
@@ -380,88 +424,79 @@ def run_sdgr(args):
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
         h2d(0)
-        for k in range(n_e2e):
+        for k in range(K):
             b = k % 2
-            if k + 1 < n_e2e:
+            if k + 1 < K:
                 h2d(k + 1)
             stream.wait_event(ev_copied[b])
-            state["t"] += 1
-            r.prepare(p, views, check=False)
-            r.forward(images=images)
-            l1_loss(images, tbuf[b], dLdS, loss)
+            graphs[b].replay()
             ev_used[b].record(stream)
-            r.backward(dLdS, grads)
-            adam_step(p, grads, m, v, LR, state["t"])
-            loss_host[b].copy_(loss[0], non_blocking=True)
+            loss_host[b].copy_(fs.loss[0], non_blocking=True)
             ev_loss[b].record(stream)
             if k >= 1:
                 ev_loss[1 - b].synchronize()
                 losses.append(float(loss_host[1 - b]))
-        ev_loss[(n_e2e - 1) % 2].synchronize()
-        losses.append(float(loss_host[(n_e2e - 1) % 2]))
+        ev_loss[(K - 1) % 2].synchronize()
+        losses.append(float(loss_host[(K - 1) % 2]))
         torch.cuda.synchronize(dev)
         t_e2e = max_over_ranks(time.perf_counter() - t0, dev)
-        views_e2e = sum_over_ranks(V * n_e2e, dev)
-        assert len(losses) == n_e2e and all(math.isfinite(x) for x in losses)
-        e2e = {"value": views_e2e / t_e2e, "unit": UNIT, "h2d_bytes_per_step": int(npix * 4),
-               "d2h_bytes_per_step": 4, "steps": n_e2e,
-               "how": "every step: host->device copy of its 64 target images from pinned memory (copy stream, "
-                      "double-buffered, overlapping the previous step) + the step + its loss read back to the host"}
+        views_e2e = sum_over_ranks(V * K, dev)
+        assert len(losses) == K and all(math.isfinite(x) for x in losses)
+        e2e = {"value": round(views_e2e / t_e2e, 3), "unit": UNIT, "h2d_bytes_per_step": int(npix * 4),
+               "d2h_bytes_per_step": 4, "steps": K,
+               "how": "every step: host->device copy of its %d target images from pinned memory (copy stream, "
+                      "double-buffered, overlapping the previous step) + one replay of the captured step + its loss "
+                      "read back to the host" % V}
+        del graphs
 
     if rank != 0:
         return None
 
-    # ---- roofline of the dominant kernel (live per-stage CUDA-event times)
+    # ---- roofline of the dominant kernel (stage events of the timed replay)
     peaks, peak_src = measured_peaks()
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    stage_ms = {k: (ms / max(n, 1), n) for k, (ms, n) in prof.items()}
+    stage_ms = {k: ms / max(n, 1) for k, (ms, n) in prof.items()}
     dom = max(prof, key=lambda k: prof[k][0])
-    ms_launch, nl = stage_ms[dom]
     share = {k: round(prof[k][0] / max(sum(x[0] for x in prof.values()), 1e-9), 4) for k in prof}
     sm_max = float(peaks.get("sm_max_mhz", 2032.0))
+    raster = raster_roofline(stage_ms, pairs, sms, sm_max, rates)
+    peak = alu_peak_tops(sms, sm_max)
     if dom in ALG_OPS:
-        fp, mu = ALG_OPS[dom]
-        ops = pairs[PLANE[dom]] * (fp + 8 * mu)
-        achieved = ops / (ms_launch / 1e3) / 1e12
-        peak = alu_peak_tops(sms, sm_max)
-        roof = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 3), "unit": "Tops/s",
-                "frac": round(achieved / peak, 4), "traffic": kernel_traffic(dom), "kernel": KERNEL_NAME[dom],
-                "peak_source": "SMs x 128 FP32 lanes x %.0f MHz (sm_max_mhz, %s)" % (sm_max, peak_src),
-                "ops_per_pair": fp + 8 * mu, "pairs_per_launch": pairs[PLANE[dom]],
-                "ms_per_launch": round(ms_launch, 4)}
+        rk = raster[KERNEL_NAME[dom]]
+        roof = {"bound": "alu", "achieved": rk["achieved"], "peak": round(peak, 3), "unit": "Tops/s",
+                "frac": rk["frac"], "traffic": kernel_traffic(dom), "kernel": KERNEL_NAME[dom],
+                "peak_source": "SMs x 128 lane-issue slots (= FP32 lanes) x %.0f MHz (sm_max_mhz, %s)"
+                               % (sm_max, peak_src),
+                "instr_per_pair": rk["instr_per_pair"], "slots_per_pair": rk["slots_per_pair"],
+                "sfu_slot_cost": {k: round(v, 3) for k, v in sfu_slot_cost(rates).items()},
+                "pairs_per_launch": pairs[PLANE[dom]],
+                "ms_per_launch": round(stage_ms[dom], 4), "binds": rk["binds"]}
         if clocks and clocks.get("sm_mhz"):
-            roof["frac_at_measured_clock"] = round(achieved / alu_peak_tops(sms, clocks["sm_mhz"]), 4)
+            roof["frac_at_measured_clock"] = round(rk["frac"] * sm_max / clocks["sm_mhz"], 4)
     else:
         roof = {"bound": "hbm", "achieved": None, "peak": peaks.get("hbm_gbs"), "unit": "GB/s", "frac": None,
                 "traffic": kernel_traffic(dom), "kernel": KERNEL_NAME.get(dom, dom)}
-    roof["stage_ms_per_step"] = {k: round(prof[k][0] / max(args.steps, 1), 4) for k in prof}
+    roof["stage_ms_per_step"] = {k: round(prof[k][0] / max(K, 1), 4) for k in prof}
     roof["stage_share"] = share
-    # every raster kernel against the same FP32-pipe peak (algorithmic ops per in-cutoff pair)
-    alu_peak = alu_peak_tops(sms, sm_max)
-    roof["raster_kernels"] = {}
-    for k, (fp, mu) in ALG_OPS.items():
-        if k in stage_ms and stage_ms[k][0] > 0:
-            ach = pairs[PLANE[k]] * (fp + 8 * mu) / (stage_ms[k][0] / 1e3) / 1e12
-            roof["raster_kernels"][KERNEL_NAME[k]] = {"ms_per_launch": round(stage_ms[k][0], 4),
-                                                      "ops_per_pair": fp + 8 * mu, "achieved": round(ach, 3),
-                                                      "frac": round(ach / alu_peak, 4)}
+    roof["raster_kernels"] = raster
+    roof["pipe_rates_per_sm_cycle"] = rates
 
     out = {
-        "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": K,
         "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": desc, "gaussians": int(params.shape[0]), "views_per_step": V,
                    "image": [views[0]["NR"], views[0]["NA"]], "parallelism": "replicas" if world > 1 else "single",
-                   "l2": "inputs larger than L2 (workspace %.1f GB per step)" % (r.workspace_bytes() / 1e9),
+                   "form": "batched: the K timed steps are one replay of a captured CUDA graph of K fused steps",
+                   "l2": "inputs larger than L2 (workspace %.1f GB per step)" % (fs.r.workspace_bytes() / 1e9),
                    "pairs_per_step": {"computation_plane": pairs[0], "imaging_plane": pairs[1]},
-                   "instances_per_step": int(r.n_inst), "schedule": r.schedule,
-                   "schedule_ms_per_step": schedule_ms, "stage_batch": stage_batches(r),
+                   "instances_per_step": int(fs.r.n_inst), "schedule": fs.r.schedule,
+                   "schedule_ms_per_step": schedule_ms, "stage_batch": stage_batches(fs.r),
                    "stage_batch_ms_per_launch": stage_batch_ms},
-        "gaussian_pixel_evals_per_s": round((pairs[0] + pairs[1]) * world * args.steps / (ms_max / 1e3), 1),
+        "gaussian_pixel_evals_per_s": round((pairs[0] + pairs[1]) * world * K / (ms_max / 1e3), 1),
         "plain": plain, "e2e": e2e, "roofline": roof, "gpu_launches": int(launches), "clocks": clocks,
     }
     return out, params, start, views
-
 
 def stage_batches(r):
     """Staging batch of each raster kernel in use (chosen, else the default)."""
@@ -526,19 +561,21 @@ def run_reference(args):
             "e2e": {"value": round(value, 5), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
-def run_uneven(args):
+def run_uneven(args, steps=None, warmup=None, autotune=None):
     """Uneven batch: 256 scenes (log-uniform 1k-500k Gaussians, vehicle boxes
     and buildings alternating), image sizes 256/512/1024, 8 views each; the
     whole batch is one graph-captured step, against plain per-view calls."""
     import numpy as np
     import torch
     import sdgr_scenes as sc
-    from paper_2506_21633_b300 import _lib
     from paper_2506_21633_b300.batch import FusedStep, plain_step
     from paper_2506_21633_b300.render import Renderer, views_npix
     rank, world, local = rank_info()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    steps = args.steps if steps is None else steps
+    warmup = args.warmup if warmup is None else warmup
+    autotune = (args.schedule == "auto") if autotune is None else autotune
     scenes, views = sc.uneven_batch(seed=4 + rank)
     offs = [0]
     for p in scenes:
@@ -554,26 +591,27 @@ def run_uneven(args):
     fs = FusedStep(p, views, targets, offs)
     fs.capture()
     schedule_ms = None
-    if args.schedule == "auto":
+    if autotune:
         _, schedule_ms = fs.autotune(steps=2)
-    elif args.schedule != fs.r.schedule:
+    elif args.schedule not in ("auto", fs.r.schedule):
         fs.r.set_schedule(args.schedule)
-        fs.graph = None
         fs.capture()
-    for _ in range(max(args.warmup, 1)):
-        fs.step()
-    fs.check()
+    for attempt in range(3):
+        for _ in range(max(warmup, 1)):
+            fs.step()
+        if fs.check():
+            break
     pairs = fs.r.count_pairs()
     stream = torch.cuda.current_stream(dev)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize(dev)
     ev0.record(stream)
-    for _ in range(args.steps):
+    for _ in range(steps):
         fs.step()
     ev1.record(stream)
     torch.cuda.synchronize(dev)
     assert fs.check()
-    ms = ev0.elapsed_time(ev1) / args.steps
+    ms = ev0.elapsed_time(ev1) / steps
     # plain: one view at a time, stream sync after each
     rp = Renderer(device=dev)
     rp.prepare(p[offs[0]:offs[1]], [dict(views[0], scene=0)], [0, offs[1]], instances=fs.r.n_inst)
@@ -587,10 +625,12 @@ def run_uneven(args):
     torch.cuda.synchronize(dev)
     t_plain = time.perf_counter() - t0
     sizes = sorted({v["NA"] for v in views})
+    evals = pairs[0] + pairs[1]
     return {"metric": "uneven-batch fwd+bwd views/s (batched graph-captured step vs plain per-view calls)",
-            "value": round(V / (ms / 1e3), 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": True, "dtype": "f32",
+            "value": round(V / (ms / 1e3), 3), "unit": UNIT, "n_gpus": world, "steps": steps,
+            "warmup": warmup, "ms_per_step": round(ms, 3), "higher_is_better": True, "dtype": "f32",
             "data": "synthetic",
+            "pair_evals_per_s": round(evals / (ms / 1e3), 1),
             "config": {"workload": "uneven batch: %d scenes, %d..%d Gaussians (total %d), images %s, %d views"
                                    % (len(scenes), min(s.shape[0] for s in scenes), max(s.shape[0] for s in scenes),
                                       offs[-1], sizes, V),
@@ -601,21 +641,18 @@ def run_uneven(args):
                        "stage_batch_ms_per_launch": {k: {nb: round(ms, 3) for nb, ms in d.items()}
                                                      for k, (_, d) in getattr(fs, "stage_batch_ms", {}).items()}
                        or None},
-            "plain": {"value": round(V / t_plain, 3), "unit": UNIT, "s_per_step": round(t_plain, 3)},
-            "gpu_launches": int(fs.graph_launches) * args.steps,
+            "plain": {"value": round(V / t_plain, 3), "unit": UNIT, "s_per_step": round(t_plain, 3),
+                      "pair_evals_per_s": round(evals / t_plain, 1)},
+            "gpu_launches": int(fs.graph_launches) * steps,
             "gpu_launches_how": "kernel launches captured in the step's graph x steps"}
 
 
-def run_serving(args):
-    """Serving: Poisson arrivals (mean 2 ms apart) of render and gradient
-    requests over 32 resident scenes of 10k-1M Gaussians; 1-16 views per
-    request, images of 256..2048 pixels, half render, half gradient."""
+def serving_scenes(rank):
+    """32 resident scenes, log-uniform 10k-1M Gaussians: vehicle boxes (scaled
+    to the count) and buildings alternating; per scene the frame and centre of
+    its views."""
     import numpy as np
-    import torch
     import sdgr_scenes as sc
-    from paper_2506_21633_b300.serve import Server
-    rank, world, local = rank_info()
-    torch.cuda.set_device(local)
     rng = np.random.default_rng(5 + rank)
     scenes, meta = [], []
     for s in range(32):
@@ -629,6 +666,35 @@ def run_serving(args):
             r2 = np.random.default_rng(500 + s)
             scenes.append(sc.box_surface_scene(n, sc._place_boxes(r2, 3, 60.0, 5.0, 20.0), r2))
             meta.append((76.8, (30.0, 30.0, 5.0)))
+    return scenes, meta
+
+
+def count_request_pairs(params, offs, reqs, dev):
+    """In-cutoff pairs (both planes) of each request's views, counted on the
+    device after the run (untimed)."""
+    from paper_2506_21633_b300.render import Renderer
+    r = Renderer(device=dev)
+    out = []
+    for views in reqs:
+        r.prepare(params, views, offs)
+        a, b = r.count_pairs()
+        out.append(a + b)
+    return out
+
+
+def run_serving(args, n_spec=None, n_sus=None, warm_spec=50, warm_sus=20):
+    """Serving: Poisson arrivals (mean 2 ms apart) of render and gradient
+    requests over 32 resident scenes of 10k-1M Gaussians; 1-16 views per
+    request, images of 256..2048 pixels, half render, half gradient."""
+    import numpy as np
+    import torch
+    import sdgr_scenes as sc
+    from paper_2506_21633_b300.serve import Server
+    rank, world, local = rank_info()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    n_spec = args.requests if n_spec is None else n_spec
+    scenes, meta = serving_scenes(rank)
     sizes = (256, 512, 1024, 2048)
     pool = {sz: np.random.default_rng(sz).uniform(0.0, 0.05, size=(sz, sz)).astype(np.float32) for sz in sizes}
     budget = int(torch.cuda.get_device_properties(local).total_memory * 0.6)
@@ -639,7 +705,7 @@ def run_serving(args):
         g = np.random.default_rng(seed)
         srv = Server(scenes, hbm_budget_bytes=budget, n_slots=3, max_batch_views=64, max_batch_pixels=1 << 26)
         futs, t_sched = [], time.perf_counter()
-        nviews, t_sub = [], []
+        nviews, t_sub, reqs, kinds = [], [], [], []
         for k in range(n_warm + n_meas):
             t_sched += g.exponential(mean_s)
             dt = t_sched - time.perf_counter()
@@ -653,39 +719,52 @@ def run_serving(args):
             vs = sc.random_views(nv, seed=10000 + k, size=sz, res=frame / sz, center=center)
             if g.uniform() < 0.5:
                 futs.append(srv.submit(s, vs, "render"))
+                kinds.append("render")
             else:
                 futs.append(srv.submit(s, vs, "gradient", [pool[sz]] * nv))
+                kinds.append("gradient")
             nviews.append(nv)
+            reqs.append([dict(v, scene=s) for v in vs])
         res = [f.result(timeout=3600) for f in futs]
         srv.close(timeout=600)
         meas = res[n_warm:]
         lat = np.array([r.latency_s for r in meas]) * 1e3
         done_views = sum(nviews[n_warm:])
         window = max(t + r.latency_s for t, r in zip(t_sub[n_warm:], meas)) - t_sub[n_warm]
-        return {"p50_ms": round(float(np.percentile(lat, 50)), 3), "p99_ms": round(float(np.percentile(lat, 99)), 3),
-                "mean_ms": round(float(lat.mean()), 3), "views_per_s": round(done_views / window, 2),
-                "views": done_views, "requests": n_meas, "warmup_requests": n_warm, "window_s": round(window, 3),
-                "offered_views_per_s": round(8.5 / mean_s, 1), "arrival_mean_ms": round(mean_s * 1e3, 3),
-                "batches": srv.stats["batches"], "mean_batch": round(float(np.mean(srv.stats["batch_sizes"])), 2),
-                "max_inflight": srv.stats["max_inflight"], "requeued": srv.stats["requeued"]}
+        pairs = count_request_pairs(srv.params, srv.offs, reqs[n_warm:], dev)
+        # a gradient request evaluates its pairs twice (pass and adjoint) on each plane
+        evals = sum(pr * (2 if kd == "gradient" else 1) for pr, kd in zip(pairs, kinds[n_warm:]))
+        out = {"p50_ms": round(float(np.percentile(lat, 50)), 3), "p99_ms": round(float(np.percentile(lat, 99)), 3),
+               "mean_ms": round(float(lat.mean()), 3), "views_per_s": round(done_views / window, 2),
+               "pair_evals_per_s": round(evals / window, 1), "pairs_per_view": round(sum(pairs) / done_views, 1),
+               "views": done_views, "requests": n_meas, "warmup_requests": n_warm, "window_s": round(window, 3),
+               "offered_views_per_s": round(8.5 / mean_s, 1), "arrival_mean_ms": round(mean_s * 1e3, 3),
+               "batches": srv.stats["batches"], "mean_batch": round(float(np.mean(srv.stats["batch_sizes"])), 2),
+               "max_inflight": srv.stats["max_inflight"], "requeued": srv.stats["requeued"]}
+        for k in ("host_stage_s", "gpu_busy_s"):
+            if k in srv.stats:
+                out[k] = round(float(srv.stats[k]), 3)
+        del srv
+        torch.cuda.empty_cache()
+        return out
 
-    spec = drive(0.002, 50, args.requests, 5 + rank)
+    spec = drive(0.002, warm_spec, n_spec, 5 + rank)
     # second run at 70 % of the throughput the first one sustained (1-16 views
     # per request: 8.5 on average): latency without a growing queue
     mean_s = 8.5 / (0.7 * spec["views_per_s"])
-    sus = drive(mean_s, 20, max(100, min(args.requests, int(20.0 / mean_s))), 7 + rank)
+    n_sus = max(100, min(args.requests, int(20.0 / mean_s))) if n_sus is None else n_sus
+    sus = drive(mean_s, warm_sus, n_sus, 7 + rank)
     return {"metric": "serving p50/p99 ms and views/s (continuous batching, Poisson arrivals mean 2 ms)",
             "value": spec["p50_ms"], "unit": "ms (p50)", "p99_ms": spec["p99_ms"], "mean_ms": spec["mean_ms"],
-            "views_per_s": spec["views_per_s"], "views": spec["views"], "requests": spec["requests"],
+            "views_per_s": spec["views_per_s"], "pair_evals_per_s": spec["pair_evals_per_s"],
+            "views": spec["views"], "requests": spec["requests"],
             "warmup_requests": spec["warmup_requests"], "window_s": spec["window_s"],
             "higher_is_better": False, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "32 resident scenes, %d..%d Gaussians; requests 1-16 views, images 256..2048, "
                                    "render/gradient 1:1, Poisson arrivals mean 2 ms" %
                                    (min(s.shape[0] for s in scenes), max(s.shape[0] for s in scenes)),
                        "hbm_budget_bytes": budget, "slots": 3},
-            "batches": spec["batches"], "mean_batch": spec["mean_batch"], "max_inflight": spec["max_inflight"],
-            "requeued": spec["requeued"],
-            "at_70pct_load": sus}
+            "at_spec_rate": spec, "at_70pct_load": sus}
 
 
 def main():
@@ -716,6 +795,36 @@ def main():
         out["cpu_baseline"] = cpu_baseline(start, views)
     else:
         out["cpu_baseline"] = None
+    # the rest of the metric at N = 1 (shortened runs; the full ones are
+    # --workload config4 / --workload serve)
+    if world == 1 and args.workload == "config3" and not args.no_config4:
+        import torch
+        torch.cuda.empty_cache()
+        t0 = time.perf_counter()
+        c4 = run_uneven(args, steps=5, warmup=3, autotune=False)
+        out["config4"] = {"batched_views_s": c4["value"], "plain_views_s": c4["plain"]["value"],
+                          "ms_per_step": c4["ms_per_step"], "pair_evals_per_s": c4["pair_evals_per_s"],
+                          "plain_pair_evals_per_s": c4["plain"]["pair_evals_per_s"], "steps": c4["steps"],
+                          "warmup": c4["warmup"], "workload": c4["config"]["workload"],
+                          "pairs_per_step": c4["config"]["pairs_per_step"], "schedule": c4["config"]["schedule"],
+                          "gpu_launches": c4["gpu_launches"],
+                          "how": "5 replays of the captured step (default schedule and staging batches, no tuning) "
+                                 "after 3 warm-up replays; plain = one pass over the 2048 views, one call sequence "
+                                 "and stream sync per view",
+                          "wall_s": round(time.perf_counter() - t0, 1)}
+    if world == 1 and args.workload == "config3" and not args.no_serving:
+        import torch
+        torch.cuda.empty_cache()
+        t0 = time.perf_counter()
+        sv = run_serving(args, n_spec=300, n_sus=100, warm_spec=30, warm_sus=10)
+        out["serving"] = {"p50_ms": sv["value"], "p99_ms": sv["p99_ms"], "views_s": sv["views_per_s"],
+                          "pair_evals_per_s": sv["pair_evals_per_s"],
+                          "offered_views_s": sv["at_spec_rate"]["offered_views_per_s"],
+                          "arrivals": "Poisson, mean 2 ms", "requests": sv["requests"],
+                          "at_spec_rate": sv["at_spec_rate"], "at_70pct_load": sv["at_70pct_load"],
+                          "how": "300 measured requests after 30 (spec rate), then 100 after 10 at 70 % of the "
+                                 "sustained rate; the full run is --workload serve (1000 requests)",
+                          "wall_s": round(time.perf_counter() - t0, 1)}
     print(json.dumps(out), flush=True)
     return 0
 

@@ -250,6 +250,21 @@ int32_t sdgr_stage_batch_options(int32_t kernel, int32_t *sizes, int32_t max_siz
  * SDGR_ERR_INVALID (NULL or misaligned flags), SDGR_ERR_CUDA (launch). */
 #define SDGR_SELFCHECK_ALL 1u
 sdgr_status sdgr_device_selfcheck(uint32_t *flags, void *stream);
+
+/* Diagnostic: the sustained per-SM rate of the instruction kinds the raster
+ * kernels are built from, measured on the current device -- the
+ * denominators of their arithmetic roofline.  Writes rates[0..4], each in
+ * thread-instructions per SM per SM clock cycle (read from the SM's cycle
+ * counter, so independent of the clock frequency): [0] fma.rn.f32,
+ * [1] ex2.approx.ftz.f32, [2] rcp.approx.ftz.f32, [3] a stream of one ex2
+ * per seven fma and [4] one rcp per seven fma (all instructions counted;
+ * 8 rates[0] / rates[3] - 7 is what one ex2 costs inside an FP32 stream, in
+ * fma issue slots).
+ * scratch: caller-owned device memory of at least SDGR_PIPE_RATES_SCRATCH
+ * bytes, 16-byte aligned.  Synchronous (waits for `stream`; a few ms).
+ * Errors: SDGR_ERR_INVALID (NULL or misaligned arguments), SDGR_ERR_CUDA. */
+#define SDGR_PIPE_RATES_SCRATCH 8192
+sdgr_status sdgr_pipe_rates(void *scratch, double *rates, void *stream);
 sdgr_status sdgr_set_stage_batch(sdgr_ws *ws, int32_t kernel, int32_t records);
 
 /* Densification and pruning (the "Densification and Pruning Operation" of
@@ -302,9 +317,12 @@ sdgr_status sdgr_densify(const float *params, const float *grads, const float *a
                          float *out_params, float *out_m, float *out_v, float *out_sh, int64_t out_capacity,
                          void *scratch, int64_t *new_N, void *stream);
 
-/* Step a13: one Adam step (Kingma & Ba; bias-corrected, eps added to the
- * square root of the corrected second moment, torch.optim.Adam semantics,
- * no weight decay) over N Gaussians.  params, grads, m, v: device
+/* Step a13: the optimiser step of the training loop (Section II: the
+ * Gaussians' parameters are updated by gradient descent on the loss; the
+ * paper names no optimiser, so the update is read as Adam -- Kingma & Ba,
+ * bias-corrected, eps added to the square root of the corrected second
+ * moment, torch.optim.Adam semantics, no weight decay -- as in the 3D
+ * Gaussian splatting training the paper builds on).  Over N Gaussians.  params, grads, m, v: device
  * [N][12] float32, 16-byte aligned; params, m, v updated in place.  lr: host
  * [5] learning rates for the groups {means, log-scales, quaternions,
  * opacity logit, P}.  step: 1-based step count.
@@ -348,6 +366,11 @@ sdgr_status sdgr_read_status(sdgr_ws *ws, int64_t *required_instances);
  * allocated).  sdgr_profile_read waits for the recorded events, and adds
  * up, per stage, the elapsed milliseconds and the number of launches since
  * the last reset.  ms and launches: host arrays of SDGR_NUM_STAGES entries.
+ * Calls enqueued on a stream that is being captured into a CUDA graph record
+ * their events as event-record nodes of the graph: every replay records
+ * them again, and sdgr_profile_read, called after a replay has finished,
+ * adds that replay's stage times (read once: the read resets the record of
+ * which events are pending).
  * Errors: SDGR_ERR_INVALID (NULL ws / arrays), SDGR_ERR_CUDA. */
 enum {
     SDGR_STAGE_PREPROCESS = 0,   /* step a1-a5 */
@@ -393,11 +416,12 @@ int64_t sdgr_launch_count(void);
  * The first call on a device looks up the scratch array's device address
  * (once per device, with that device current), so make that first call
  * before any stream capture.  The call waits for `stream` before it returns
- * (it reads the device status word).  Every call reuses the same scratch,
- * which keeps the previous call's contents (everything that must start at
- * zero is cleared by the call); host threads are serialised by a lock, but
- * work that overlaps on the GPU -- e.g. a second process context or replayed
- * launches touching this scratch -- races. */
+ * (it reads the device status word); a `stream` in capture mode is refused
+ * with SDGR_ERR_INVALID before anything is enqueued.  Every call reuses the
+ * same scratch, which keeps the previous call's contents (everything that
+ * must start at zero is cleared by the call); host threads are serialised by
+ * a lock, but calls whose work overlaps on the GPU (e.g. from two processes
+ * sharing the device) race on the scratch. */
 #define SDGR_NOALLOC_SCRATCH_BYTES (32u << 20)
 #define SDGR_NOALLOC_MAX_GAUSSIANS 16384
 #define SDGR_NOALLOC_MAX_VIEWS 4

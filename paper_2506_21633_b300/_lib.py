@@ -25,7 +25,7 @@ EXPORTS = (
     "sdgr_count_pairs", "sdgr_launch_count", "sdgr_render_fwd_noalloc", "sdgr_adam_step_device",
     "sdgr_copy_status_async", "sdgr_set_sh", "sdgr_set_densify_stats", "sdgr_densify_scratch_bytes",
     "sdgr_densify", "sdgr_set_schedule", "sdgr_adam_step_flat", "sdgr_stage_batch_options",
-    "sdgr_set_stage_batch", "sdgr_device_selfcheck",
+    "sdgr_set_stage_batch", "sdgr_device_selfcheck", "sdgr_pipe_rates",
 )
 
 SELFCHECK_ALL = 1  # every bit sdgr_device_selfcheck defines
@@ -115,6 +115,7 @@ def lib():
         L.sdgr_stage_batch_options.restype = i32
         L.sdgr_set_stage_batch.argtypes = [vp, i32, i32]
         L.sdgr_device_selfcheck.argtypes = [vp, vp]
+        L.sdgr_pipe_rates.argtypes = [vp, P(ctypes.c_double), vp]
         L.sdgr_densify_scratch_bytes.argtypes = [i64]
         L.sdgr_densify.argtypes = [vp, vp, vp, vp, vp, vp, vp, i64, P(SdgrDensifyCfg), vp, vp, vp, vp, i64, vp,
                                    P(ctypes.c_int64), vp]
@@ -272,6 +273,19 @@ def sdgr_device_selfcheck(flags_ptr, stream=None):
     """Enqueue the device self-check; it writes its bit mask to the device
     word at flags_ptr (uint32)."""
     _check("sdgr_device_selfcheck", lib().sdgr_device_selfcheck(ctypes.c_void_p(flags_ptr), stream))
+
+
+PIPE_RATES_SCRATCH = 8192
+PIPE_RATE_KINDS = ("ffma", "ex2", "rcp", "ex2_in_ffma_stream", "rcp_in_ffma_stream")
+
+
+def sdgr_pipe_rates(scratch_ptr, stream=None):
+    """Measured per-SM rates (thread-instructions per SM cycle) of fma, ex2,
+    rcp, and of streams of one ex2 (rcp) per seven fma; synchronous.
+    scratch_ptr: device memory of PIPE_RATES_SCRATCH bytes."""
+    out = (ctypes.c_double * 5)()
+    _check("sdgr_pipe_rates", lib().sdgr_pipe_rates(ctypes.c_void_p(scratch_ptr), out, ctypes.c_void_p(stream)))
+    return dict(zip(PIPE_RATE_KINDS, (float(x) for x in out)))
 
 
 def sdgr_densify_scratch_bytes(N):

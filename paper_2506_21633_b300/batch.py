@@ -74,6 +74,23 @@ class FusedStep:
     def capture(self):
         """Capture one step into a CUDA graph (the step's launches, memsets
         and plan uploads become graph nodes); replaying it runs the step."""
+        self.graph = self.capture_graph()
+        return self
+
+    def capture_graph(self, steps=1, targets=None, profile=False):
+        """A new CUDA graph of `steps` consecutive optimisation steps (one
+        replay runs them all, back to back, with no host work between).
+
+        targets: flat target images this graph's L1 reads (default: the
+        current ones); the graph keeps their address, so two graphs over two
+        target buffers let a caller refill one buffer while the other is in
+        use.  profile=True: the stage events of the captured calls become
+        graph nodes; once a replay has finished, `self.r.profile_read()`
+        returns that replay's per-stage times.  Sets `self.graph_launches`
+        to the kernel launches one replay runs."""
+        if targets is not None:
+            assert targets.numel() == self.targets.numel() and targets.device == self.targets.device
+            self.targets = targets
         side = torch.cuda.Stream(device=self.p.device)
         side.wait_stream(torch.cuda.current_stream(self.p.device))
         # one step on a side stream before capture (library set-up, lazy module
@@ -89,12 +106,17 @@ class FusedStep:
             t.copy_(s0)
         torch.cuda.synchronize(self.p.device)
         g = torch.cuda.CUDAGraph()
+        if profile:
+            self.r.profile(True)
+            self.r.profile_read(reset=True)  # nothing pending but the captured steps' events
         l0 = L.sdgr_launch_count()
         with torch.cuda.graph(g):
-            self.enqueue()
+            for _ in range(int(steps)):
+                self.enqueue()
         self.graph_launches = L.sdgr_launch_count() - l0  # kernel launches captured = launches per replay
-        self.graph = g
-        return self
+        if profile:
+            self.r.profile(False)  # later eager calls record nothing; the captured events stay pending
+        return g
 
     def autotune(self, schedules=("tiles", "ordered", "persistent"), steps=3, stage_batches=True):
         """Pick the raster schedule (whole steps timed under each, re-capturing

@@ -173,18 +173,33 @@ cudaError_t prof_harvest(sdgr_ws *ws) {
     return cudaSuccess;
 }
 
+bool capturing(cudaStream_t s) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    return cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone;
+}
+
+// Stage events.  On a stream that is being captured into a CUDA graph they
+// become event-record nodes of the graph (recorded again by every replay),
+// so the stage times of a replay are read after it has run.
+void prof_record(cudaEvent_t e, cudaStream_t s) {
+    if (capturing(s))
+        cudaEventRecordWithFlags(e, s, cudaEventRecordExternal);
+    else
+        cudaEventRecord(e, s);
+}
+
 // Records the start event of a stage; returns the pair index or -1.
 int prof_begin(sdgr_ws *ws, int stage, cudaStream_t s) {
     if (!ws->prof_on) return -1;
-    if (ws->prof_used == PROF_PAIRS && prof_harvest(ws) != cudaSuccess) return -1;
+    if (ws->prof_used == PROF_PAIRS && (capturing(s) || prof_harvest(ws) != cudaSuccess)) return -1;
     const int k = ws->prof_used++;
     ws->prof_stage[k] = stage;
-    cudaEventRecord(ws->prof_ev[2 * k], s);
+    prof_record(ws->prof_ev[2 * k], s);
     return k;
 }
 
 void prof_end(sdgr_ws *ws, int k, cudaStream_t s) {
-    if (k >= 0) cudaEventRecord(ws->prof_ev[2 * k + 1], s);
+    if (k >= 0) prof_record(ws->prof_ev[2 * k + 1], s);
 }
 
 }  // namespace
@@ -552,6 +567,27 @@ sdgr_status sdgr_set_schedule(sdgr_ws *ws, int32_t mode) {
 sdgr_status sdgr_device_selfcheck(uint32_t *flags, void *stream) {
     if (!flags || ((uintptr_t)flags) % 4 != 0) return SDGR_ERR_INVALID;
     return launch_selfcheck(flags, static_cast<cudaStream_t>(stream)) == cudaSuccess ? SDGR_OK : SDGR_ERR_CUDA;
+}
+
+sdgr_status sdgr_pipe_rates(void *scratch, double *rates, void *stream) {
+    if (!scratch || !rates || ((uintptr_t)scratch) % 16 != 0) return SDGR_ERR_INVALID;
+    int dev = 0, sms = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    float *sink = static_cast<float *>(scratch);
+    unsigned long long *cyc = reinterpret_cast<unsigned long long *>(static_cast<char *>(scratch) + 4096);
+    static const int iters[5] = {4096, 1024, 1024, 2048, 2048};
+    for (int op = 0; op < 5; ++op) {
+        CK(cudaMemsetAsync(cyc, 0, sizeof(*cyc), s));
+        int bps = 0;
+        CK(launch_pipe_rate(op, iters[op], sink, cyc, &bps, sms, s));
+        CK(cudaStreamSynchronize(s));
+        unsigned long long c = 0;
+        CK(cudaMemcpy(&c, cyc, sizeof(c), cudaMemcpyDeviceToHost));
+        rates[op] = c ? (double)bps * 1024.0 * iters[op] * 8.0 / (double)c : 0.0;
+    }
+    return SDGR_OK;
 }
 
 int32_t sdgr_stage_batch_options(int32_t kernel, int32_t *sizes, int32_t max_sizes) {

@@ -248,6 +248,9 @@ cudaError_t launch_count_pairs(const uint2 *ranges, const uint32_t *vals, const 
                                const ViewDev *views, int V, int tiles, float cut, StatusDev *st, cudaStream_t s);
 cudaError_t launch_intensity_out(const CompRec *comp, const float *A, int64_t VG, float *I, int sms, cudaStream_t s);
 cudaError_t launch_selfcheck(uint32_t *flags, cudaStream_t s);
+// sink: 1024 floats; cycles: one counter, zeroed by the caller.
+cudaError_t launch_pipe_rate(int op, int iters, float *sink, unsigned long long *cycles, int *blocks_per_sm,
+                             int sms, cudaStream_t s);
 
 // parameter adjoint, optimiser, loss
 cudaError_t launch_param_bwd(const float4 *params, const ViewDev *views, const SceneDev *scenes,

@@ -54,6 +54,9 @@ class Renderer:
         self.n_inst = None
         self.schedule = "persistent"
         self.stage_batch = {}  # raster kernel name -> staging batch (absent: the kernel's default)
+        # bumped by every prepare(): the workspace then holds another scene or
+        # view set, and an adjoint of an earlier forward is no longer possible
+        self.generation = 0
 
     def __del__(self):
         try:
@@ -102,6 +105,7 @@ class Renderer:
         offs = L.make_offsets(scene_offsets)
         n_scenes = len(scene_offsets) - 1
         s = _stream_handle(stream)
+        self.generation += 1
         guess = instances if instances is not None else (self.n_inst if self.n_inst is not None else None)
         if guess is None:
             base = L.sdgr_caps_for(vs, len(views), offs, n_scenes, 0)
@@ -212,21 +216,42 @@ class Renderer:
                    for v in self.views)
 
 
+class StaleRendererError(RuntimeError):
+    """The renderer of an SDGRRender node was prepared again (other
+    parameters or views) before that node's backward ran."""
+
+
 class SDGRRender(torch.autograd.Function):
     """images (flat, views concatenated) = SDGR(params); backward = the
-    hand-written adjoint (saves nothing but the renderer, which holds params,
-    the sorted lists and per-ray end state in its workspace)."""
+    hand-written adjoint of Section II-B (dL/dS from autograd, then the
+    splat, intensity and projection adjoints in libsdgr.so).
+
+    The sorted lists and per-ray end state the adjoint needs stay in the
+    renderer's workspace (per-tile visibility is recomputed, not stored), so
+    the renderer must not be prepared again between this forward and its
+    backward: a generation count taken at the forward is checked in the
+    backward, which raises StaleRendererError instead of differentiating
+    another scene.  params are saved, so autograd's version check refuses a
+    backward after they were modified in place (e.g. by an optimiser step)."""
 
     @staticmethod
     def forward(ctx, params, renderer, views, scene_offsets=None):
         renderer.prepare(params.detach().contiguous(), views, scene_offsets)
         images = renderer.forward()
         ctx.renderer = renderer
+        ctx.generation = renderer.generation
+        ctx.save_for_backward(params)
         return images
 
     @staticmethod
     def backward(ctx, dL_dimages):
-        grads = ctx.renderer.backward(dL_dimages.contiguous())
+        ctx.saved_tensors  # raises if params changed in place since the forward
+        r = ctx.renderer
+        if r.generation != ctx.generation:
+            raise StaleRendererError("SDGRRender: the renderer was prepared again (generation %d, forward at %d); "
+                                     "run backward before the next forward on the same renderer, or use one "
+                                     "renderer per graph" % (r.generation, ctx.generation))
+        grads = r.backward(dL_dimages.contiguous())
         return grads, None, None, None
 
 

@@ -36,10 +36,10 @@ def _noalloc(params32, views, cfg):
     return code, images.cpu().numpy(), inten.cpu().numpy()[:len(views) * params32.shape[0]]
 
 
-def _workspace_path(params32, views):
+def _workspace_path(params32, views, **cfg):
     import torch
     from paper_2506_21633_b300.render import Renderer
-    r = Renderer()
+    r = Renderer(**cfg)
     p = torch.from_numpy(params32).cuda().contiguous()
     r.prepare(p, views)
     inten = torch.zeros(max(1, len(views) * params32.shape[0]), dtype=torch.float32, device="cuda")
@@ -82,3 +82,32 @@ def test_noalloc_rejects_oversize():
     small = sc.random_cube_scene(10, seed=64).astype(np.float32)
     code, _, _ = _noalloc(small, [sc.make_view(0.0, 45.0, 0.1, 0.1, 1024, 1024)], cfg)
     assert code == L.SDGR_ERR_INVALID
+
+
+def test_noalloc_capacity_exceeded_gives_zeros():
+    """A dense scene inside the N, V and pixel limits whose tile instances do
+    not fit the scratch: SDGR_ERR_CAPACITY and all-zero images."""
+    from paper_2506_21633_b300 import _lib as L
+    cfg = L.make_cfg()
+    dense = sc.random_cube_scene(16384, half=1.0, s_lo=0.2, s_hi=0.4, seed=65)
+    views = [sc.make_view(45.0 + 80.0 * k, 40.0 + 5.0 * k, 0.02, 0.02, 256, 256) for k in range(4)]
+    code, img, _ = _noalloc(np.ascontiguousarray(dense, dtype=np.float32), views, cfg)
+    assert code == L.SDGR_ERR_CAPACITY, L.status_string(code)
+    assert np.all(img == 0.0)
+
+
+@pytest.mark.parametrize("opts", [dict(norm_mode=1), dict(alpha_mode=1)])
+def test_noalloc_other_options(opts):
+    """A call with other renderer options rebuilds the scratch's workspace
+    binding; the result still matches the workspace-based path."""
+    from paper_2506_21633_b300 import _lib as L
+    cfg = L.make_cfg(norm_mode=opts.get("norm_mode", 0), alpha_mode=opts.get("alpha_mode", 0))
+    params = sc.vehicle_box_scene(3000, seed=66, extent=(2.0, 1.5, 1.0), log_s_mean=math.log(0.06),
+                                  center=(0.0, 0.0, 0.5))
+    views = sc.random_views(2, seed=67, size=128, res=0.03, center=(0.0, 0.0, 0.5))
+    p32 = np.ascontiguousarray(params, dtype=np.float32)
+    code, img, inten = _noalloc(p32, views, cfg)
+    assert code == L.SDGR_OK, L.status_string(code)
+    ref_img, ref_inten = _workspace_path(p32, views, **opts)
+    assert np.abs(img - ref_img).max() <= IMG_TOL * np.abs(ref_img).max()
+    assert np.abs(inten - ref_inten).max() <= IMG_TOL * np.abs(ref_inten).max()
