@@ -706,12 +706,14 @@ def run_serving(args, n_spec=None, n_sus=None, warm_spec=50, warm_sus=20):
         srv = Server(scenes, hbm_budget_bytes=budget, n_slots=3, max_batch_views=64, max_batch_pixels=1 << 26)
         futs, t_sched = [], time.perf_counter()
         nviews, t_sub, reqs, kinds = [], [], [], []
+        t_submit_total = 0.0
         for k in range(n_warm + n_meas):
             t_sched += g.exponential(mean_s)
             dt = t_sched - time.perf_counter()
             if dt > 0:
                 time.sleep(dt)
             t_sub.append(time.perf_counter())
+            ts0 = time.perf_counter()
             s = int(g.integers(0, 32))
             nv = int(g.integers(1, 17))
             sz = int(g.choice(sizes))
@@ -723,6 +725,7 @@ def run_serving(args, n_spec=None, n_sus=None, warm_spec=50, warm_sus=20):
             else:
                 futs.append(srv.submit(s, vs, "gradient", [pool[sz]] * nv))
                 kinds.append("gradient")
+            t_submit_total += time.perf_counter() - ts0
             nviews.append(nv)
             reqs.append([dict(v, scene=s) for v in vs])
         res = [f.result(timeout=3600) for f in futs]
@@ -732,18 +735,23 @@ def run_serving(args, n_spec=None, n_sus=None, warm_spec=50, warm_sus=20):
         done_views = sum(nviews[n_warm:])
         window = max(t + r.latency_s for t, r in zip(t_sub[n_warm:], meas)) - t_sub[n_warm]
         pairs = count_request_pairs(srv.params, srv.offs, reqs[n_warm:], dev)
-        # a gradient request evaluates its pairs twice (pass and adjoint) on each plane
-        evals = sum(pr * (2 if kd == "gradient" else 1) for pr, kd in zip(pairs, kinds[n_warm:]))
+        # in-cutoff pairs of the served views (both planes), once per view as
+        # for the batched step; a render request runs only the forward passes
+        evals = sum(pairs)
+        grad_share = sum(pr for pr, kd in zip(pairs, kinds[n_warm:]) if kd == "gradient") / max(evals, 1)
         out = {"p50_ms": round(float(np.percentile(lat, 50)), 3), "p99_ms": round(float(np.percentile(lat, 99)), 3),
                "mean_ms": round(float(lat.mean()), 3), "views_per_s": round(done_views / window, 2),
                "pair_evals_per_s": round(evals / window, 1), "pairs_per_view": round(sum(pairs) / done_views, 1),
+               "gradient_share_of_pairs": round(grad_share, 3),
                "views": done_views, "requests": n_meas, "warmup_requests": n_warm, "window_s": round(window, 3),
                "offered_views_per_s": round(8.5 / mean_s, 1), "arrival_mean_ms": round(mean_s * 1e3, 3),
                "batches": srv.stats["batches"], "mean_batch": round(float(np.mean(srv.stats["batch_sizes"])), 2),
                "max_inflight": srv.stats["max_inflight"], "requeued": srv.stats["requeued"]}
-        for k in ("host_stage_s", "gpu_busy_s"):
-            if k in srv.stats:
-                out[k] = round(float(srv.stats[k]), 3)
+        # where the scheduler thread's time went, and the GPU time of the
+        # batches (summed over slots: overlapping batches count twice)
+        out["scheduler_s"] = {k: round(float(srv.stats[k]), 3)
+                              for k in ("host_form_s", "host_launch_s", "host_retire_s", "gpu_batch_s")}
+        out["client_submit_s"] = round(t_submit_total, 3)
         del srv
         torch.cuda.empty_cache()
         return out

@@ -26,7 +26,9 @@
 //
 // Exponent: in a tile, a pixel's exponent of Gaussian i is a quadratic in the
 // pixel's tile-local coordinates (X, Y); the six coefficients are formed when
-// the batch is staged, so a pair costs five FMAs on per-thread constants.
+// the batch is staged, so a pair costs five FMAs on per-thread constants
+// (Horner form, column part first: the two rays of a lane share a column, so
+// the intensity pass and the splat pay seven FMAs for two).
 //
 // Sums over the tile's pixels per Gaussian.  The intensity pass needs only
 // sum_rays alpha T (non-negative, each term <= 1): one redux.sync per hit on
@@ -102,9 +104,9 @@ __device__ __forceinline__ TileCtx tile_ctx(const ViewDev *views, int V, int til
 // conversion instruction.
 __device__ __forceinline__ float small_u2f(uint32_t n) { return __fsub_rn(__uint_as_float(0x4B000000u | n), 8388608.f); }
 
-// Tile-local pixel coordinates of the thread and their products.
+// Tile-local pixel coordinates of the thread.
 struct LaneXY {
-    float X, Y, X2, XY, Y2;
+    float X, Y;
 };
 
 __device__ __forceinline__ LaneXY lane_xy() {
@@ -112,9 +114,6 @@ __device__ __forceinline__ LaneXY lane_xy() {
     LaneXY L;
     L.X = (float)(8 * (w & 1) + (l & 7));
     L.Y = (float)(4 * (w >> 1) + (l >> 3));
-    L.X2 = L.X * L.X;
-    L.XY = L.X * L.Y;
-    L.Y2 = L.Y * L.Y;
     return L;
 }
 
@@ -133,12 +132,28 @@ __device__ __forceinline__ void poly_coeffs(float u, float v, float qa, float qb
     Q = make_float2(l2, c0);
 }
 
+// The exponent in Horner form, column part first: with
+// bx = (qa X + l1) X + c0 and my = qb X + l2 (the column's part, which the
+// rays of one column share), q = (qc Y + my) Y + bx -- five FMAs for one
+// ray, three plus two per ray for rays of one column.  Every kernel that
+// decides a pair's cutoff evaluates it in exactly this order.
+struct ColQ {
+    float bx, my;
+};
+
+__device__ __forceinline__ ColQ poly_col(const float4 &P, float l2, float c0, float X) {
+    ColQ c;
+    c.bx = __fmaf_rn(__fmaf_rn(P.x, X, P.w), X, c0);
+    c.my = __fmaf_rn(P.y, X, l2);
+    return c;
+}
+
+__device__ __forceinline__ float poly_row(const float4 &P, const ColQ &c, float Y) {
+    return __fmaf_rn(__fmaf_rn(P.z, Y, c.my), Y, c.bx);
+}
+
 __device__ __forceinline__ float poly_q(const float4 &P, float l2, float c0, const LaneXY &L) {
-    float q = __fmaf_rn(l2, L.Y, c0);
-    q = __fmaf_rn(P.w, L.X, q);
-    q = __fmaf_rn(P.z, L.Y2, q);
-    q = __fmaf_rn(P.y, L.XY, q);
-    return __fmaf_rn(P.x, L.X2, q);
+    return poly_row(P, poly_col(P, l2, c0, L.X), L.Y);
 }
 
 // Tile-local rows [x, y] that the K-ellipse of a Gaussian centred at row uy
@@ -382,7 +397,8 @@ constexpr uint32_t S23_BITS = 0x4B000000u;  // bit pattern of 2^23
 // TfloorS: the transmittance floor times 2^23.  Four warps per tile, each on
 // an 8 x 8 block of rays with two rays per lane (rows r and r + 4 of the
 // block); each ray's exponent is the same five-FMA quadratic, in the same
-// tile-local coordinates, as the adjoint evaluates for it.  A lane adds its
+// tile-local coordinates and order, as the adjoint evaluates for it (the
+// column part computed once for both rays).  A lane adds its
 // two rays' fixed-point weights before the warp's redux: 64 patterns of
 // 2^23 + k sum to 64 x 0x4B000000 = 0xC0000000 (mod 2^32) plus the warp's
 // sum, at most 2^29.
@@ -423,15 +439,7 @@ intensity_fwd_tile(const int tile, const StatusDev *st, const uint2 *__restrict_
     const int X = 8 * (w & 1) + (lane & 7), Y = 8 * (w >> 1) + (lane >> 3);
     const int px = c.x0 + X, py0 = c.y0 + Y, py1 = py0 + 4;
     const bool in0 = px < vd.NA && py0 < vd.NR, in1 = px < vd.NA && py1 < vd.NR;
-    LaneXY L0, L1;
-    L0.X = L1.X = (float)X;
-    L0.Y = (float)Y;
-    L1.Y = (float)(Y + 4);
-    L0.X2 = L1.X2 = L0.X * L0.X;
-    L0.XY = L0.X * L0.Y;
-    L1.XY = L1.X * L1.Y;
-    L0.Y2 = L0.Y * L0.Y;
-    L1.Y2 = L1.Y * L1.Y;
+    const float fX = (float)X, fY0 = (float)Y, fY1 = (float)(Y + 4);
     const uint2 r = ranges[tile];
     const float cutm = cut_margin(cut);
     constexpr uint32_t WARP_BIAS = 0xC0000000u;  // 64 x bits(2^23), mod 2^32
@@ -443,8 +451,9 @@ intensity_fwd_tile(const int tile, const StatusDev *st, const uint2 *__restrict_
     const auto alphas = [&](uint32_t off, float &a0, float &a1) {
         const float4 P = *reinterpret_cast<const float4 *>(reinterpret_cast<const char *>(sP) + off);
         const float4 Q = *reinterpret_cast<const float4 *>(reinterpret_cast<const char *>(sQ) + off);
-        const float q0 = poly_q(P, Q.x, Q.y, L0);
-        const float q1 = poly_q(P, Q.x, Q.y, L1);
+        const ColQ cq = poly_col(P, Q.x, Q.y, fX);
+        const float q0 = poly_row(P, cq, fY0);
+        const float q1 = poly_row(P, cq, fY1);
         a0 = alpha_of<AM>(Q.z, q0 >= cut ? ex2_approx(q0) : 0.f);
         a1 = alpha_of<AM>(Q.z, q1 >= cut ? ex2_approx(q1) : 0.f);
     };
@@ -608,9 +617,8 @@ __device__ __forceinline__ void stage_img(const ImgRec *__restrict__ img, uint32
 // Each pixel gathers over its warp's hit list; no reduction is needed.  Unlike
 // the other raster kernels the splat runs four warps per tile, each on an
 // 8 x 8 pixel block with two pixels per lane (rows r and r + 4 of the block):
-// the second pixel's exponent follows from the first's by
-// q(X, Y + 4) - q(X, Y) = qb (4X) + qc (8Y + 16) + 4 l2 (two FMAs and an add
-// instead of five FMAs), the per-hit record loads and list walk serve two
+// the two pixels share the column part of the exponent (seven FMAs for both
+// instead of ten), the per-hit record loads and list walk serve two
 // pixels, and four warps wait at a barrier instead of eight (-10 % against
 // eight warps on 8 x 4 blocks, despite the coarser blocks).  A block's mask
 // bit is the union of its two 8 x 4 halves.  Every pixel is written: with a
@@ -624,7 +632,7 @@ splat_fwd_tile(const int tile, const StatusDev *st, const uint2 *__restrict__ ra
     constexpr int NT = 128;
     constexpr int PER = NB / NT;  // records staged per thread
     __shared__ float4 sP[NB];  // (qa, qb, qc, l1)
-    __shared__ float4 sQ[NB];  // (l2, c0, c I, 4 l2)
+    __shared__ float4 sQ[NB];  // (l2, c0, c I, -)
     __shared__ uint32_t sM[NB];
     __shared__ uint16_t sHL[4 * 32];  // per warp: its hit list of the current slice
     const int t = threadIdx.x, w = t >> 5, l = t & 31;
@@ -646,13 +654,7 @@ splat_fwd_tile(const int tile, const StatusDev *st, const uint2 *__restrict__ ra
     const int X = 8 * (w & 1) + (l & 7), Y = 8 * (w >> 1) + (l >> 3);
     const int px = c.x0 + X, py0 = c.y0 + Y, py1 = py0 + 4;
     const bool in0 = px < vd.NA && py0 < vd.NR, in1 = px < vd.NA && py1 < vd.NR;
-    LaneXY L;
-    L.X = (float)X;
-    L.Y = (float)Y;
-    L.X2 = L.X * L.X;
-    L.XY = L.X * L.Y;
-    L.Y2 = L.Y * L.Y;
-    const float X4 = 4.f * L.X, Yt = fmaf(8.f, L.Y, 16.f);
+    const float fX = (float)X, fY0 = (float)Y, fY1 = (float)(Y + 4);
     const uint2 r = ok ? rangesI[tile] : make_uint2(0u, 0u);
     const float cutm = cut_margin(cut);
     float acc0 = 0.f, acc1 = 0.f;
@@ -672,7 +674,7 @@ splat_fwd_tile(const int tile, const StatusDev *st, const uint2 *__restrict__ ra
                     stage_img(img, vg, c, cutm, G, uv, cn, m);
                     poly_coeffs(uv.x, uv.y, G.x, G.y, G.z, P, Q);
                     sP[k] = P;
-                    sQ[k] = make_float4(Q.x, Q.y, cn * comp[vg].P * A[vg], 4.f * Q.x);
+                    sQ[k] = make_float4(Q.x, Q.y, cn * comp[vg].P * A[vg], 0.f);
                     const uint32_t h = m | (m >> 2);  // 8 x 8 block 2 RB + cb: 8 x 4 blocks 4 RB + cb, 4 RB + 2 + cb
                     sM[k] = (h & 3u) | ((h >> 2) & 0xcu);
                 } else {
@@ -695,8 +697,9 @@ splat_fwd_tile(const int tile, const StatusDev *st, const uint2 *__restrict__ ra
                 const uint32_t off = wl[i];
                 const float4 P0 = *reinterpret_cast<const float4 *>(reinterpret_cast<const char *>(sP) + off);
                 const float4 Q0 = *reinterpret_cast<const float4 *>(reinterpret_cast<const char *>(sQ) + off);
-                const float q0 = poly_q(P0, Q0.x, Q0.y, L);
-                const float q1 = q0 + fmaf(P0.y, X4, fmaf(P0.z, Yt, Q0.w));
+                const ColQ cq = poly_col(P0, Q0.x, Q0.y, fX);
+                const float q0 = poly_row(P0, cq, fY0);
+                const float q1 = poly_row(P0, cq, fY1);
                 if (q0 >= cut) acc0 = fmaf(Q0.z, ex2_approx(q0), acc0);
                 if (q1 >= cut) acc1 = fmaf(Q0.z, ex2_approx(q1), acc1);
             }

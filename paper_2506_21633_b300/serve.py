@@ -47,7 +47,8 @@ class AdmissionError(RuntimeError):
 
 
 class Request:
-    __slots__ = ("rid", "scene", "views", "kind", "target", "npix", "t_submit", "t_done", "future", "attempts")
+    __slots__ = ("rid", "scene", "views", "kind", "target", "npix", "t_submit", "t_done", "future", "attempts",
+                 "sums")
 
     def __init__(self, rid, scene, views, kind, target):
         self.rid, self.scene, self.views, self.kind, self.target = rid, scene, views, kind, target
@@ -56,6 +57,10 @@ class Request:
         self.t_done = None
         self.future = concurrent.futures.Future()
         self.attempts = 0
+        # this request's share of a batch's workspace capacities (views,
+        # view-Gaussian slots, pixels, tiles; they add up over a batch), set
+        # by the server on first use
+        self.sums = None
 
 
 class Result:
@@ -94,7 +99,8 @@ class _Slot:
         self.grads = None
         self.h_images = self.h_targets = self.h_grads = self.h_loss = None
         self.h_status = torch.zeros(4, dtype=torch.int32, pin_memory=True)
-        self.event = torch.cuda.Event()
+        self.event = torch.cuda.Event(enable_timing=True)
+        self.ev_start = torch.cuda.Event(enable_timing=True)
         self.batch = None
         self.footprint = 0
         self.seg = None
@@ -122,7 +128,8 @@ class Server:
         self._next_id = 0
         self.inflight_bytes = 0
         self.stats = {"batches": 0, "requests": 0, "refused": 0, "invalid": 0, "requeued": 0, "batch_sizes": [],
-                      "max_inflight": 0}
+                      "max_inflight": 0, "host_form_s": 0.0, "host_launch_s": 0.0, "host_retire_s": 0.0,
+                      "gpu_batch_s": 0.0}
         self._thread = threading.Thread(target=self._loop, name="sdgr-server", daemon=True)
         self._thread.start()
 
@@ -138,13 +145,15 @@ class Server:
         try:
             if kind not in ("render", "gradient") or not (0 <= req.scene < len(self.offs) - 1) or not views:
                 raise ValueError("bad request")
-            L.sdgr_caps_for(L.make_views(views), len(views), L.make_offsets(self.offs), len(self.offs) - 1, 0)
+            self._sums(req)  # validates the views
             if kind == "gradient":
-                t = np.concatenate([np.asarray(x, dtype=np.float32).ravel() for x in
-                                    (target if isinstance(target, (list, tuple)) else [target])])
-                if t.size != req.npix:
+                # kept as the caller's arrays (no copy here); staged into
+                # page-locked memory when the request's batch is launched
+                parts = [np.asarray(x, dtype=np.float32) for x in
+                         (target if isinstance(target, (list, tuple)) else [target])]
+                if sum(x.size for x in parts) != req.npix:
                     raise ValueError("target size does not match the views")
-                req.target = t
+                req.target = parts
         except (ValueError, L.SdgrError, TypeError) as e:
             with self._cv:
                 self.stats["invalid"] += 1
@@ -174,10 +183,19 @@ class Server:
             est += len(r.views) * n * self.inst_ratio[r.scene]
         return int(est * 1.25) + 4096
 
+    def _sums(self, r):
+        if r.sums is None:
+            c = L.sdgr_caps_for(L.make_views(r.views), len(r.views), L.make_offsets(self.offs), len(self.offs) - 1, 0)
+            r.sums = (c.max_views, c.max_view_gauss, c.max_pixels, c.max_tiles)
+        return r.sums
+
     def _footprint(self, reqs):
-        views = [v for r in reqs for v in r.views]
-        caps = L.sdgr_caps_for(L.make_views(views), len(views), L.make_offsets(self.offs), len(self.offs) - 1,
-                               min(self._inst_estimate(reqs), 0x7fffffff))
+        caps = L.SdgrCaps()
+        caps.max_views, caps.max_view_gauss, caps.max_pixels, caps.max_tiles = (
+            sum(x) for x in zip(*(self._sums(r) for r in reqs)))
+        caps.max_scenes = len(self.offs) - 1
+        caps.max_gaussians = self.n_total
+        caps.max_instances = min(self._inst_estimate(reqs), 0x7fffffff)
         ws = L.sdgr_workspace_size(self.cfg, caps)
         npix = sum(r.npix for r in reqs)
         grad = any(r.kind == "gradient" for r in reqs)
@@ -224,6 +242,7 @@ class Server:
         s = slot.stream
         sh = _stream_handle(s)
         with torch.cuda.stream(s):
+            slot.ev_start.record(s)
             slot.images = _grow(slot.images, npix, torch.float32, dev)
             slot.h_images = _grow(slot.h_images, npix, torch.float32, pinned=True)
             r = slot.renderer
@@ -241,8 +260,11 @@ class Server:
                 slot.h_loss = _grow(slot.h_loss, len(batch), torch.float32, pinned=True)
                 slot.grads = _grow(slot.grads, self.n_total * 12, torch.float32, dev)
                 slot.h_grads = _grow(slot.h_grads, self.n_total * 12, torch.float32, pinned=True)
-                for q, (o, n) in zip(batch, seg):
-                    slot.h_targets[o:o + n].numpy()[:] = q.target
+                for q, (o, n) in zip(batch, seg):  # multi-threaded host copies (torch), no GIL held
+                    p = o
+                    for part in q.target:
+                        slot.h_targets[p:p + part.size].copy_(torch.from_numpy(part.reshape(-1)))
+                        p += part.size
                 slot.targets[:npix].copy_(slot.h_targets[:npix], non_blocking=True)
                 for k, (o, n) in enumerate(seg):
                     l1_loss(slot.images[o:o + n], slot.targets[o:o + n], slot.dLdS[o:o + n], slot.loss[k:k + 1],
@@ -266,6 +288,7 @@ class Server:
     def _retire(self, slot):
         batch, seg = slot.batch, slot.seg
         slot.batch = None
+        self.stats["gpu_batch_s"] += slot.ev_start.elapsed_time(slot.event) / 1e3
         self.inflight_bytes -= slot.footprint
         slot.footprint = 0
         code = int(slot.h_status[0])
@@ -287,19 +310,23 @@ class Server:
         ratio = required / max(vg, 1)
         for q in batch:  # running estimate of instances per view-Gaussian slot
             self.inst_ratio[q.scene] = 0.7 * self.inst_ratio[q.scene] + 0.3 * max(ratio, 1.0)
-        now = time.perf_counter()
         for k, (q, (o, n)) in enumerate(zip(batch, seg)):
-            flat = slot.h_images[o:o + n].numpy()
+            # the request's own arrays, filled by multi-threaded copies out of
+            # the slot's page-locked buffers (which the next batch reuses)
+            flat = np.empty(n, dtype=np.float32)
+            torch.from_numpy(flat).copy_(slot.h_images[o:o + n])
             imgs, p = [], 0
             for v in q.views:
                 m = int(v["NA"]) * int(v["NR"])
-                imgs.append(flat[p:p + m].reshape(int(v["NR"]), int(v["NA"])).copy())
+                imgs.append(flat[p:p + m].reshape(int(v["NR"]), int(v["NA"])))
                 p += m
             grads, loss = None, None
             if q.kind == "gradient":
                 a, b = self.offs[q.scene] * 12, self.offs[q.scene + 1] * 12
-                grads = slot.h_grads[a:b].numpy().reshape(-1, 12).copy()
+                grads = np.empty(((b - a) // 12, 12), dtype=np.float32)
+                torch.from_numpy(grads).view(-1).copy_(slot.h_grads[a:b])
                 loss = float(slot.h_loss[k])
+            now = time.perf_counter()
             q.t_done = now
             _resolve(q.future, Result(imgs, grads, loss, now - q.t_submit, len(batch)))
         with self._cv:
@@ -317,12 +344,17 @@ class Server:
             progressed = False
             for sl in self.slots:
                 if sl.batch is not None and sl.event.query():
+                    t0 = time.perf_counter()
                     self._retire(sl)
+                    self.stats["host_retire_s"] += time.perf_counter() - t0
                     progressed = True
             for sl in self.slots:
                 if sl.batch is None:
+                    t0 = time.perf_counter()
                     with self._cv:
                         batch = self._form_batch()
+                    t1 = time.perf_counter()
+                    self.stats["host_form_s"] += t1 - t0
                     if batch:
                         try:
                             self._launch(sl, batch)
@@ -330,6 +362,7 @@ class Server:
                             sl.batch = None
                             for q in batch:
                                 _resolve(q.future, exc=e)
+                        self.stats["host_launch_s"] += time.perf_counter() - t1
                         progressed = True
             if not progressed:
                 time.sleep(0.0002)
