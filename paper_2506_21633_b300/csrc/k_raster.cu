@@ -897,7 +897,8 @@ __device__ __forceinline__ void
 intensity_bwd_tile(const int tile, const StatusDev *st, const uint2 *__restrict__ ranges, const uint32_t *__restrict__ vals,
                    const CompRec *__restrict__ comp, const ImgRec *__restrict__ img, const float4 *__restrict__ accI,
                    const float *__restrict__ Tend, const int32_t *__restrict__ last,
-                   const ViewDev *__restrict__ views, int V, float cut, float4 *__restrict__ accC, const uint32_t *sBL) {
+                   const ViewDev *__restrict__ views, int V, float cut, float4 *__restrict__ accC, const uint32_t *sBL,
+                   const float2 *sBO) {
     __shared__ float4 sP[BATCH];  // (qa, qb, qc, l1)
     __shared__ float4 sQ[BATCH];  // (l2, c0, o, chat)
     __shared__ float2 sU[BATCH];  // tile-local centre
@@ -905,13 +906,13 @@ intensity_bwd_tile(const int tile, const StatusDev *st, const uint2 *__restrict_
     __shared__ uint32_t sid[BATCH];
     __shared__ uint8_t sperm[BATCH];
     __shared__ __align__(16) float W[SUB * WSTRIDE];
-    __shared__ __align__(16) float zero4[4];
+    __shared__ __align__(16) float zero12[12];  // reads at offsets -4 .. 7 from zero12 + 4
     __shared__ __align__(4) uint16_t sHL[8 * 32];  // per warp: its hit list of the current slice
     __shared__ int smax;
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
     uint16_t *const wl = sHL + 32 * warp;
     int nh = 0;
-    if (t < 4) zero4[t] = 0.f;
+    if (t < 12) zero12[t] = 0.f;
     const TileCtx c = tile_ctx(views, V, tile);
     const LaneXY L = lane_xy();
     const uint2 r = ranges[tile];
@@ -1046,22 +1047,33 @@ intensity_bwd_tile(const int tile, const StatusDev *st, const uint2 *__restrict_
             else
                 walk(std::false_type{});
             __syncthreads();
+            // eight threads per Gaussian: thread cc takes the column pair cp
+            // (columns 2 cp and 2 cp + 1) of every other block of the
+            // Gaussian's list, from list position hb: the per-block work is
+            // shared by two columns, and each thread walks half the blocks.
+            // It reads column 2 cp + hb first, so that the two halves of a
+            // group load disjoint banks.
             const int j = sperm[sl * SUB + (t >> 3)], cc = t & 7;
+            const int cp = cc & 3, hb = cc >> 2;
             const uint32_t mb = j < ns ? sM[sub + j] : 0u;
-            uint32_t bl = sBL[mb];
-            const int cnt = __popc(mb);
+            uint32_t bl = sBL[mb] >> (4 * hb);
+            const int cnt = (__popc(mb) + 1 - hb) >> 1;  // list positions hb, hb + 2, ...
             const float2 uv = sU[sub + (j < ns ? j : 0)];
-            const float dx0 = (float)cc - uv.x, dy00 = -uv.y;
-            const float *wr = W + j * WSTRIDE + 4 * cc;
+            const float dxa = (float)(2 * cp + hb) - uv.x, dxb = (float)(2 * cp + 1 - hb) - uv.x, dy00 = -uv.y;
+            const float *wr = W + j * WSTRIDE + 8 * cp + 4 * hb;
+            const int o2 = 4 - 8 * hb;  // the second column, relative to the first
             float m[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-            const float dx1 = dx0 + 8.f;
             const int rounds = __reduce_max_sync(0xffffffffu, cnt);
             for (int i = 0; i < rounds; ++i) {
                 const int b = (int)(bl & 7u);
-                bl >>= 4;
-                const float *src = i < cnt ? wr + 32 * b : zero4;
-                const float4 w4 = *reinterpret_cast<const float4 *>(src);
-                block_moments(w4, (b & 1) ? dx1 : dx0, fmaf(4.f, small_u2f((uint32_t)b >> 1), dy00), m);
+                bl >>= 8;
+                const float *src = i < cnt ? wr + 32 * b : zero12 + 4;
+                const float4 wa = *reinterpret_cast<const float4 *>(src);
+                const float4 wc = *reinterpret_cast<const float4 *>(src + o2);
+                const float2 o = sBO[b];  // the block's offset from the tile origin
+                const float dy = dy00 + o.y;
+                block_moments(wa, dxa + o.x, dy, m);
+                block_moments(wc, dxb + o.x, dy, m);
             }
             // the group's table row is free after the reads above: scratch, at
             // an offset that puts the four groups of the warp on disjoint banks
@@ -1074,17 +1086,19 @@ intensity_bwd_tile(const int tile, const StatusDev *st, const uint2 *__restrict_
 }
 
 template <int AM>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 4)
 k_intensity_bwd(const uint2 *__restrict__ ranges, const uint32_t *__restrict__ vals, const CompRec *__restrict__ comp,
                 const ImgRec *__restrict__ img, const float4 *__restrict__ accI, const float *__restrict__ Tend,
                 const int32_t *__restrict__ last, const ViewDev *__restrict__ views, int V, float cut,
                 const StatusDev *st, float4 *__restrict__ accC, const TileSched sc) {
     if (st->code != SDGR_OK) return;
     __shared__ uint32_t sBL[256];
+    __shared__ float2 sBO[8];  // pixel block b's offset from the tile origin: (8 (b & 1), 4 (b >> 1))
     sBL[threadIdx.x] = block_list(threadIdx.x);
+    if (threadIdx.x < 8) sBO[threadIdx.x] = make_float2((float)(8 * (threadIdx.x & 1)), (float)(4 * (threadIdx.x >> 1)));
     __syncthreads();
     for_tiles(sc, st, [&](int tile) {
-        intensity_bwd_tile<AM>(tile, st, ranges, vals, comp, img, accI, Tend, last, views, V, cut, accC, sBL);
+        intensity_bwd_tile<AM>(tile, st, ranges, vals, comp, img, accI, Tend, last, views, V, cut, accC, sBL, sBO);
     });
 }
 
