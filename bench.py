@@ -50,10 +50,10 @@ UNIT = "views/s"
 # live) and also occupies the SFU pipe at its measured rate.  Derivation in
 # the design notes.
 ALG_OPS = {
-    "intensity_fwd": (11, 1, 0),
+    "intensity_fwd": (10, 1, 0),
     "splat_fwd": (7, 1, 0),
     "splat_bwd": (18, 1, 0),
-    "intensity_bwd": (26, 1, 1),
+    "intensity_bwd": (25, 1, 1),
 }
 PLANE = {"intensity_fwd": 0, "splat_fwd": 1, "splat_bwd": 1, "intensity_bwd": 0}
 KERNEL_NAME = {"intensity_fwd": "k_intensity_fwd", "splat_fwd": "k_splat_fwd", "splat_bwd": "k_splat_bwd",

@@ -44,9 +44,14 @@ k_param_bwd(const float4 *__restrict__ params, const ViewDev *__restrict__ views
         const float qn = 1.0f / sqrtf(p2.x * p2.x + p2.y * p2.y + p2.z * p2.z + p2.w * p2.w);
         const float w = p2.x * qn, x = p2.y * qn, y = p2.z * qn, z = p2.w * qn;
         const float osig = 1.0f / (1.0f + expf(-p0.w));
-        // factor of the computation-plane geometry: d alpha / d G is o (default)
-        // or tau (1 - alpha) with the (1 - alpha) already inside the moments
-        const float o = alpha_mode ? softplus(p0.w) : osig;
+        // factor of the computation-plane geometry: d alpha / d G is o (default;
+        // the intensity adjoint's moments carry it: they are of dL/dalpha
+        // alpha = o dL/dalpha G) or tau (1 - alpha) with the (1 - alpha)
+        // already inside the moments
+        const float o = alpha_mode ? softplus(p0.w) : 1.f;
+        // dL/do from the moments of dL/dalpha alpha (default: divided by o;
+        // o = 0 leaves alpha = 0 and d o / d logit = 0) or dL/dtau
+        const float go_scale = alpha_mode ? 1.f : (osig > 0.f ? 1.f / osig : 0.f);
         // d o / d logit = o (1 - o); d tau / d logit = sigmoid(logit)
         const float dlogit = alpha_mode ? osig : osig * (1.f - osig);
         float R[3][3];
@@ -113,7 +118,7 @@ k_param_bwd(const float4 *__restrict__ params, const ViewDev *__restrict__ views
                 dacc += sqrtf(guIx * guIx + guIy * guIy);
                 dcnt += 1.f;
             }
-            go += n0.x;
+            go += n0.x * go_scale;
             const float dLdP = dLdI * Av;  // dL/dP of this view (P depends on the view through SH)
             gP += dLdP;
             if (dsh) {

@@ -313,6 +313,19 @@ __device__ __forceinline__ float alpha_of(float o, float e) {
     return y < 0.125f ? series : direct;
 }
 
+// Opacity folded into the exponent (alpha_mode 0): alpha = o exp2(q) =
+// exp2(q + log2 o), so the staged record carries c0 + log2 o in place of c0
+// and the pair's cutoff q >= cut becomes q + log2 o >= cut + log2 o.  The
+// intensity pass and its adjoint stage the same record bits (the same
+// instructions on the same inputs), so they take the same cutoff decisions
+// and the same alpha bits.  o = 0 gives log2 o = -inf: the cutoff test
+// passes and alpha = exp2(-inf) = 0.
+__device__ __forceinline__ void fold_opacity(float o, float cut, float &c0, float &cutq) {
+    const float lo = __log2f(o);
+    c0 = __fadd_rn(c0, lo);
+    cutq = __fadd_rn(cut, lo);
+}
+
 // Calls f(0), ..., f(N - 1) as straight-line code.  (A `for` loop over a
 // compile-time trip count, even with `#pragma unroll`, costs the staging code
 // six registers here.)
@@ -410,7 +423,7 @@ intensity_fwd_tile(const int tile, const StatusDev *st, const uint2 *__restrict_
     constexpr int NT = 128;
     constexpr int PER = NB / NT;  // records staged per thread
     __shared__ float4 sP[NB];  // (qa, qb, qc, l1)
-    __shared__ float4 sQ[NB];  // (l2, c0, o, -)
+    __shared__ float4 sQ[NB];  // (l2, c0 + log2 o, cut + log2 o, -); alpha_mode 1: (l2, c0, tau, -)
     __shared__ uint32_t sM[NB];
     __shared__ uint32_t sid[NB];
     __shared__ uint32_t sAcc[NB];  // sum of alpha T over the tile's 256 rays, in units of 2^-23 (< 2^31)
@@ -454,8 +467,13 @@ intensity_fwd_tile(const int tile, const StatusDev *st, const uint2 *__restrict_
         const ColQ cq = poly_col(P, Q.x, Q.y, fX);
         const float q0 = poly_row(P, cq, fY0);
         const float q1 = poly_row(P, cq, fY1);
-        a0 = alpha_of<AM>(Q.z, q0 >= cut ? ex2_approx(q0) : 0.f);
-        a1 = alpha_of<AM>(Q.z, q1 >= cut ? ex2_approx(q1) : 0.f);
+        if constexpr (AM == 0) {  // Q.z: the folded cutoff; the exponent includes log2 o
+            a0 = q0 >= Q.z ? ex2_approx(q0) : 0.f;
+            a1 = q1 >= Q.z ? ex2_approx(q1) : 0.f;
+        } else {  // Q.z: the optical depth
+            a0 = alpha_of<AM>(Q.z, q0 >= cut ? ex2_approx(q0) : 0.f);
+            a1 = alpha_of<AM>(Q.z, q1 >= cut ? ex2_approx(q1) : 0.f);
+        }
     };
     int nb = 0;  // Gaussians staged in the current batch
     uint32_t vnext[PER];  // next batch's list entries, loaded one batch ahead
@@ -471,9 +489,14 @@ intensity_fwd_tile(const int tile, const StatusDev *st, const uint2 *__restrict_
                 float4 P;
                 float2 Q, uv, oP;
                 uint32_t m = 0;
-                if (vg_ok(st, vd, vg)) stage_comp(comp, vg, c, cutm, P, Q, m, uv, oP);
+                float oz = 0.f;
+                if (vg_ok(st, vd, vg)) {
+                    stage_comp(comp, vg, c, cutm, P, Q, m, uv, oP);
+                    oz = oP.x;
+                    if constexpr (AM == 0) fold_opacity(oP.x, cut, Q.y, oz);
+                }
                 sP[k] = P;
-                sQ[k] = make_float4(Q.x, Q.y, oP.x, 0.f);
+                sQ[k] = make_float4(Q.x, Q.y, oz, 0.f);
                 const uint32_t h = m | (m >> 2);  // 8 x 8 block 2 RB + cb: 8 x 4 blocks 4 RB + cb, 4 RB + 2 + cb
                 sM[k] = (h & 3u) | ((h >> 2) & 0xcu);
                 sid[k] = vg;
@@ -900,7 +923,7 @@ intensity_bwd_tile(const int tile, const StatusDev *st, const uint2 *__restrict_
                    const ViewDev *__restrict__ views, int V, float cut, float4 *__restrict__ accC, const uint32_t *sBL,
                    const float2 *sBO) {
     __shared__ float4 sP[BATCH];  // (qa, qb, qc, l1)
-    __shared__ float4 sQ[BATCH];  // (l2, c0, o, chat)
+    __shared__ float4 sQ[BATCH];  // (l2, c0 + log2 o, cut + log2 o, chat); alpha_mode 1: (l2, c0, tau, chat)
     __shared__ float2 sU[BATCH];  // tile-local centre
     __shared__ uint32_t sM[BATCH];
     __shared__ uint32_t sid[BATCH];
@@ -941,12 +964,15 @@ intensity_bwd_tile(const int tile, const StatusDev *st, const uint2 *__restrict_
             float2 Q, uv, oP;
             uint32_t m = 0;
             float dLdI = 0.f;
+            float oz = 0.f;
             if (vg_ok(st, views[c.v], vg)) {
                 stage_comp(comp, vg, c, cutm, P, Q, m, uv, oP);
                 dLdI = accI[2 * (size_t)vg].x * img[vg].cn;
+                oz = oP.x;
+                if constexpr (AM == 0) fold_opacity(oP.x, cut, Q.y, oz);
             }
             sP[t] = P;
-            sQ[t] = make_float4(Q.x, Q.y, oP.x, dLdI * oP.y);
+            sQ[t] = make_float4(Q.x, Q.y, oz, dLdI * oP.y);
             sU[t] = uv;
             sM[t] = m;
             sid[t] = vg;
@@ -982,7 +1008,8 @@ intensity_bwd_tile(const int tile, const StatusDev *st, const uint2 *__restrict_
             // and no stopped ray ahead of its stopping pair in the warp
             const auto hit = [&](auto fast, uint32_t off, float q, const float4 &Q) {
                 constexpr bool F = decltype(fast)::value;
-                const bool in = F ? q >= cut : (q >= cut) & ((int)(off >> 4) < lim);
+                const float cq = AM == 0 ? Q.z : cut;  // the folded cutoff (alpha_mode 0)
+                const bool in = F ? q >= cq : (q >= cq) & ((int)(off >> 4) < lim);
                 float *const wp = reinterpret_cast<float *>(reinterpret_cast<char *>(W) + (int)(off * 66u) + wb);
                 const float e = in ? ex2_approx(q) : 0.f;
                 // T in front of the pair: T behind it / (1 - alpha), relative
@@ -999,13 +1026,13 @@ intensity_bwd_tile(const int tile, const StatusDev *st, const uint2 *__restrict_
                     }
                 };
                 if constexpr (AM == 0) {
-                    // alpha = o e: 1 - alpha in one rounding, and B += alpha d
-                    // as o (e d), e d being the weight's factor as well
-                    rebuild(__fmaf_rn(-Q.z, e, 1.f));
-                    const float ed = e * (Q.w - B);
-                    B = fmaf(Q.z, ed, B);
-                    // weight of the profile: d alpha / d G = o
-                    *wp = T * ed;
+                    // e is alpha itself (the exponent includes log2 o)
+                    rebuild(__fsub_rn(1.f, e));
+                    const float ad = e * (Q.w - B);
+                    B += ad;
+                    // weight: dL/dalpha alpha = o dL/dalpha G (the parameter
+                    // adjoint divides the moments by o)
+                    *wp = T * ad;
                 } else {
                     const float alpha = alpha_of<AM>(Q.z, e);
                     const float om = __fsub_rn(1.f, alpha);
