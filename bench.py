@@ -749,8 +749,7 @@ def run_serving(args, n_spec=None, n_sus=None, warm_spec=50, warm_sus=20):
                "max_inflight": srv.stats["max_inflight"], "requeued": srv.stats["requeued"]}
         # where the scheduler thread's time went, and the GPU time of the
         # batches (summed over slots: overlapping batches count twice)
-        out["scheduler_s"] = {k: round(float(srv.stats[k]), 3)
-                              for k in ("host_form_s", "host_launch_s", "host_retire_s", "gpu_batch_s")}
+        out["scheduler_s"] = {k: round(float(v), 3) for k, v in srv.stats.items() if k.endswith("_s")}
         out["client_submit_s"] = round(t_submit_total, 3)
         del srv
         torch.cuda.empty_cache()

@@ -815,11 +815,13 @@ splat_bwd_tile(const int tile, const StatusDev *st, const uint2 *__restrict__ ra
         __syncthreads();
         // two threads per Gaussian, each four columns (c2, c2 + 2, c2 + 4,
         // c2 + 6) of every block; 128 Gaussians at a time, a warp's sixteen
-        // in one 32-entry window
+        // in one 32-entry window (sorted by block count).  The two warps of a
+        // window swap halves every other round, so that neither takes the
+        // heavier half every time and waits at the next barrier are even.
         for (int j0 = 0; j0 < nb; j0 += 128) {
             const int g = t >> 1, c2 = t & 1;
             const int w0 = j0 + (g & 96);
-            const int k = w0 < nb ? w0 + sperm[w0 + (g & 31)] : nb;
+            const int k = w0 < nb ? w0 + sperm[w0 + ((g & 31) ^ (((j0 >> 7) & 1) << 4))] : nb;
             const int ks = k < nb ? k : 0;
             const uint32_t mb = k < nb ? sM[k] : 0u;
             uint32_t bl = sBL[mb];

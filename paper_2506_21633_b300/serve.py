@@ -128,8 +128,8 @@ class Server:
         self._next_id = 0
         self.inflight_bytes = 0
         self.stats = {"batches": 0, "requests": 0, "refused": 0, "invalid": 0, "requeued": 0, "batch_sizes": [],
-                      "max_inflight": 0, "host_form_s": 0.0, "host_launch_s": 0.0, "host_retire_s": 0.0,
-                      "gpu_batch_s": 0.0}
+                      "max_inflight": 0, "host_form_s": 0.0, "host_launch_s": 0.0, "host_stage_targets_s": 0.0,
+                      "host_retire_s": 0.0, "gpu_batch_s": 0.0}
         self._thread = threading.Thread(target=self._loop, name="sdgr-server", daemon=True)
         self._thread.start()
 
@@ -260,11 +260,13 @@ class Server:
                 slot.h_loss = _grow(slot.h_loss, len(batch), torch.float32, pinned=True)
                 slot.grads = _grow(slot.grads, self.n_total * 12, torch.float32, dev)
                 slot.h_grads = _grow(slot.h_grads, self.n_total * 12, torch.float32, pinned=True)
+                t0 = time.perf_counter()
                 for q, (o, n) in zip(batch, seg):  # multi-threaded host copies (torch), no GIL held
                     p = o
                     for part in q.target:
                         slot.h_targets[p:p + part.size].copy_(torch.from_numpy(part.reshape(-1)))
                         p += part.size
+                self.stats["host_stage_targets_s"] += time.perf_counter() - t0
                 slot.targets[:npix].copy_(slot.h_targets[:npix], non_blocking=True)
                 for k, (o, n) in enumerate(seg):
                     l1_loss(slot.images[o:o + n], slot.targets[o:o + n], slot.dLdS[o:o + n], slot.loss[k:k + 1],
