@@ -241,13 +241,14 @@ def workload(name, rank):
 
 def sfu_slot_cost(rates):
     """Issue-slot cost of one ex2 and one rcp inside an FP32 stream, from the
-    measured rates of streams with one SFU instruction per seven fma: eight
-    instructions take 8 r_fma / r_mix slots, seven of them fma."""
+    measured rates of streams with one SFU instruction per seven (ex2) or
+    eight (rcp) fma: n instructions take n r_fma / r_mix slots, n - 1 of them
+    fma."""
     out = {}
-    for k in ("ex2", "rcp"):
+    for k, n in (("ex2", 8.0), ("rcp", 9.0)):
         mix = (rates or {}).get(k + "_in_ffma_stream")
         fma = (rates or {}).get("ffma")
-        out[k] = max(1.0, 8.0 * fma / mix - 7.0) if mix and fma else 8.0  # no measurement: SFU lanes 16 of 128
+        out[k] = max(1.0, n * fma / mix - (n - 1.0)) if mix and fma else 8.0  # no measurement: SFU lanes 16 of 128
     return out
 
 

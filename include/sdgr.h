@@ -256,10 +256,11 @@ sdgr_status sdgr_device_selfcheck(uint32_t *flags, void *stream);
  * denominators of their arithmetic roofline.  Writes rates[0..4], each in
  * thread-instructions per SM per SM clock cycle (read from the SM's cycle
  * counter, so independent of the clock frequency): [0] fma.rn.f32,
- * [1] ex2.approx.ftz.f32, [2] rcp.approx.ftz.f32, [3] a stream of one ex2
- * per seven fma and [4] one rcp per seven fma (all instructions counted;
- * 8 rates[0] / rates[3] - 7 is what one ex2 costs inside an FP32 stream, in
- * fma issue slots).
+ * [1] ex2.approx.ftz.f32, [2] rcp.approx.ftz.f32 (each followed by a
+ * dependent fma, which is not counted), [3] a stream of one ex2 per seven fma
+ * and [4] one rcp per eight fma (all instructions counted; 8 rates[0] /
+ * rates[3] - 7 and 9 rates[0] / rates[4] - 8 are what one ex2 and one rcp
+ * cost inside an FP32 stream, in fma issue slots).
  * scratch: caller-owned device memory of at least SDGR_PIPE_RATES_SCRATCH
  * bytes, 16-byte aligned.  Synchronous (waits for `stream`; a few ms).
  * Errors: SDGR_ERR_INVALID (NULL or misaligned arguments), SDGR_ERR_CUDA. */

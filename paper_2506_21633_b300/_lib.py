@@ -281,7 +281,8 @@ PIPE_RATE_KINDS = ("ffma", "ex2", "rcp", "ex2_in_ffma_stream", "rcp_in_ffma_stre
 
 def sdgr_pipe_rates(scratch_ptr, stream=None):
     """Measured per-SM rates (thread-instructions per SM cycle) of fma, ex2,
-    rcp, and of streams of one ex2 (rcp) per seven fma; synchronous.
+    rcp, and of streams of one ex2 per seven fma and one rcp per eight fma;
+    synchronous.
     scratch_ptr: device memory of PIPE_RATES_SCRATCH bytes."""
     out = (ctypes.c_double * 5)()
     _check("sdgr_pipe_rates", lib().sdgr_pipe_rates(ctypes.c_void_p(scratch_ptr), out, ctypes.c_void_p(stream)))

@@ -585,7 +585,10 @@ sdgr_status sdgr_pipe_rates(void *scratch, double *rates, void *stream) {
         CK(cudaStreamSynchronize(s));
         unsigned long long c = 0;
         CK(cudaMemcpy(&c, cyc, sizeof(c), cudaMemcpyDeviceToHost));
-        rates[op] = c ? (double)bps * 1024.0 * iters[op] * 8.0 / (double)c : 0.0;
+        // instructions counted per thread and iteration: 8, or 9 for the rcp
+        // stream (its rcp's fma included)
+        const double per_iter = op == 4 ? 9.0 : 8.0;
+        rates[op] = c ? (double)bps * 1024.0 * iters[op] * per_iter / (double)c : 0.0;
     }
     return SDGR_OK;
 }

@@ -1206,9 +1206,11 @@ cudaError_t launch_selfcheck(uint32_t *flags, cudaStream_t s) {
 // chains of iters x 8 dependent instructions between two reads of the SM's
 // cycle counter; the instructions are volatile asm, so none moves across the
 // counter reads.  OP 0: fma.rn.f32; 1: ex2.approx.ftz.f32; 2:
-// rcp.approx.ftz.f32; 3: one ex2 and seven fma per eight; 4: one rcp and
-// seven fma per eight (what an SFU instruction costs inside an FP32 stream:
-// one issue slot if the pipes overlap perfectly, more otherwise).
+// rcp.approx.ftz.f32, each followed by an fma (rcp of rcp is the identity,
+// which the assembler may fold away; only the rcp are counted); 3: one ex2
+// and seven fma per eight; 4: one rcp (with its fma) and seven fma per
+// nine (what an SFU instruction costs inside an FP32 stream: one issue slot
+// if the pipes overlap perfectly, more otherwise).
 __device__ __forceinline__ float probe_fma(float a) {
     float y;
     asm volatile("fma.rn.f32 %0, %1, 0f3F7FBE77, 0f3A03126F;" : "=f"(y) : "f"(a));  // a * 0.999 + 0.0005
@@ -1237,7 +1239,7 @@ __global__ void __launch_bounds__(1024) k_pipe_rate(int iters, float *sink, unsi
         for (int j = 0; j < 8; ++j) {
             if (OP == 0 || (OP >= 3 && j >= 1)) a[j] = probe_fma(a[j]);
             else if (OP == 1 || OP == 3) a[j] = probe_ex2(a[j]);
-            else a[j] = probe_rcp(a[j]);
+            else a[j] = probe_fma(probe_rcp(a[j]));
         }
     }
     const long long t1 = clock64();
