@@ -1201,72 +1201,6 @@ cudaError_t launch_selfcheck(uint32_t *flags, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-// Diagnostic: sustained per-SM rate of one instruction kind, the denominators
-// of the raster kernels' roofline.  Every thread runs eight independent
-// chains of iters x 8 dependent instructions between two reads of the SM's
-// cycle counter; the instructions are volatile asm, so none moves across the
-// counter reads.  OP 0: fma.rn.f32; 1: ex2.approx.ftz.f32; 2:
-// rcp.approx.ftz.f32, each followed by an fma (rcp of rcp is the identity,
-// which the assembler may fold away; only the rcp are counted); 3: one ex2
-// and seven fma per eight; 4: one rcp (with its fma) and seven fma per
-// nine (what an SFU instruction costs inside an FP32 stream: one issue slot
-// if the pipes overlap perfectly, more otherwise).
-__device__ __forceinline__ float probe_fma(float a) {
-    float y;
-    asm volatile("fma.rn.f32 %0, %1, 0f3F7FBE77, 0f3A03126F;" : "=f"(y) : "f"(a));  // a * 0.999 + 0.0005
-    return y;
-}
-__device__ __forceinline__ float probe_ex2(float a) {
-    float y;
-    asm volatile("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(-a));
-    return y;
-}
-__device__ __forceinline__ float probe_rcp(float a) {
-    float y;
-    asm volatile("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(a));
-    return y;
-}
-
-template <int OP>
-__global__ void __launch_bounds__(1024) k_pipe_rate(int iters, float *sink, unsigned long long *cycles) {
-    float a[8];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) a[j] = 0.5f + 0.01f * (float)(threadIdx.x & 7) + 0.001f * (float)j;
-    __syncthreads();
-    const long long t0 = clock64();
-    for (int i = 0; i < iters; ++i) {
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            if (OP == 0 || (OP >= 3 && j >= 1)) a[j] = probe_fma(a[j]);
-            else if (OP == 1 || OP == 3) a[j] = probe_ex2(a[j]);
-            else a[j] = probe_fma(probe_rcp(a[j]));
-        }
-    }
-    const long long t1 = clock64();
-    __syncthreads();
-    float s = 0.f;
-#pragma unroll
-    for (int j = 0; j < 8; ++j) s += a[j];
-    if (s == -1.f) sink[threadIdx.x] = s;  // never true: keeps the chains alive
-    if (threadIdx.x == 0) atomicMax(cycles, (unsigned long long)(t1 - t0));
-}
-
-cudaError_t launch_pipe_rate(int op, int iters, float *sink, unsigned long long *cycles, int *blocks_per_sm,
-                             int sms, cudaStream_t s) {
-    static void (*const kern[5])(int, float *, unsigned long long *) = {k_pipe_rate<0>, k_pipe_rate<1>,
-                                                                         k_pipe_rate<2>, k_pipe_rate<3>,
-                                                                         k_pipe_rate<4>};
-    if (op < 0 || op > 4) return cudaErrorInvalidValue;
-    int n = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern[op], 1024, 0);
-    if (e != cudaSuccess) return e;
-    if (n < 1) return cudaErrorInvalidConfiguration;
-    *blocks_per_sm = n;
-    kern[op]<<<(unsigned)(sms * n), 1024, 0, s>>>(iters, sink, cycles);
-    note_launch();
-    return cudaGetLastError();
-}
-
 // Diagnostic: in-cutoff (pixel, Gaussian) pairs of every tile of one plane.
 template <typename Rec>
 __global__ void __launch_bounds__(256)
