@@ -62,6 +62,42 @@ def test_graph_replay_matches_eager():
     assert np.abs(runs[0] - runs[1]).max() <= 1e-3 * moved
 
 
+def test_multi_step_graph_with_stage_events():
+    """One graph of K consecutive steps (the bench's timed form): a replay
+    advances the optimisation like K one-step replays, and the stage events
+    captured as graph nodes give that replay's per-stage times (K launches
+    of every stage, positive times)."""
+    import torch
+    from paper_2506_21633_b300 import _lib as L
+    from paper_2506_21633_b300.batch import FusedStep
+    params, offs, views = _batch()
+    start32 = sc.perturb(params, seed=5).astype(np.float32)
+    tg = _targets(params.astype(np.float32), views, offs)
+    K = 3
+    runs = []
+    for multi in (False, True):
+        p = torch.from_numpy(start32.copy()).cuda()
+        fs = FusedStep(p, views, tg, offs)
+        if multi:
+            g = fs.capture_graph(steps=K, profile=True)
+            g.replay()
+            torch.cuda.synchronize()
+            prof = fs.r.profile_read(reset=True)
+            for stage in L.STAGES:
+                ms, n = prof[stage]
+                assert n == K and ms > 0.0, (stage, ms, n)
+            assert fs.graph_launches > 0
+        else:
+            fs.capture()
+            for _ in range(K):
+                fs.step()
+        assert fs.check()
+        runs.append(p.cpu().numpy().astype(np.float64))
+    moved = np.abs(runs[0] - start32).max()
+    assert moved > 0
+    assert np.abs(runs[0] - runs[1]).max() <= 1e-3 * moved
+
+
 def test_first_step_gradient_multiscene():
     """Seeded targets far above every rendered value: sign(S - S*) = -1 on
     both sides, so the fused step's L1 upstream gradient is exactly -1/npix
