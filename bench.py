@@ -704,7 +704,8 @@ def run_serving(args, n_spec=None, n_sus=None, warm_spec=50, warm_sus=20):
         """Submit n_warm + n_meas requests with exponential inter-arrival
         times of mean `mean_s`; latency and throughput of the measured ones."""
         g = np.random.default_rng(seed)
-        srv = Server(scenes, hbm_budget_bytes=budget, n_slots=3, max_batch_views=64, max_batch_pixels=1 << 26)
+        srv = Server(scenes, hbm_budget_bytes=budget, n_slots=3, max_batch_views=64, max_batch_pixels=1 << 26,
+                     preallocate=True)
         futs, t_sched = [], time.perf_counter()
         nviews, t_sub, reqs, kinds = [], [], [], []
         t_submit_total = 0.0

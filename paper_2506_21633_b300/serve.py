@@ -105,10 +105,27 @@ class _Slot:
         self.footprint = 0
         self.seg = None
 
+    def preallocate(self, npix, nreq, ngrad, device):
+        f = torch.float32
+        self.images = _grow(None, npix, f, device)
+        self.dLdS = _grow(None, npix, f, device)
+        self.targets = _grow(None, npix, f, device)
+        self.loss = _grow(None, nreq, f, device)
+        self.grads = _grow(None, ngrad, f, device)
+        self.h_images = _grow(None, npix, f, pinned=True)
+        self.h_targets = _grow(None, npix, f, pinned=True)
+        self.h_loss = _grow(None, nreq, f, pinned=True)
+        self.h_grads = _grow(None, ngrad, f, pinned=True)
+
 
 class Server:
     def __init__(self, scenes, hbm_budget_bytes, n_slots=3, max_batch_views=64, max_batch_pixels=1 << 26,
-                 device=None, inst_per_slot=16.0):
+                 device=None, inst_per_slot=16.0, preallocate=False):
+        """preallocate: size every slot's image, target and gradient buffers
+        (device and page-locked host) for the largest batch at start-up, so
+        that no buffer grows while requests are served (page-locked
+        allocations are slow; growing them inside the scheduler thread stalls
+        every request queued behind)."""
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
         offs = [0]
         for s in scenes:
@@ -122,6 +139,9 @@ class Server:
         self.inst_ratio = [float(inst_per_slot)] * len(scenes)
         self.cfg = L.make_cfg()
         self.slots = [_Slot(self.device) for _ in range(n_slots)]
+        if preallocate:
+            for sl in self.slots:
+                sl.preallocate(self.max_pixels, self.max_views, self.n_total * 12, self.device)
         self._pending = collections.deque()
         self._cv = threading.Condition()
         self._stop = False
@@ -129,7 +149,7 @@ class Server:
         self.inflight_bytes = 0
         self.stats = {"batches": 0, "requests": 0, "refused": 0, "invalid": 0, "requeued": 0, "batch_sizes": [],
                       "max_inflight": 0, "host_form_s": 0.0, "host_launch_s": 0.0, "host_stage_targets_s": 0.0,
-                      "host_retire_s": 0.0, "gpu_batch_s": 0.0}
+                      "host_prepare_s": 0.0, "host_grow_s": 0.0, "host_retire_s": 0.0, "gpu_batch_s": 0.0}
         self._thread = threading.Thread(target=self._loop, name="sdgr-server", daemon=True)
         self._thread.start()
 
@@ -145,6 +165,9 @@ class Server:
         try:
             if kind not in ("render", "gradient") or not (0 <= req.scene < len(self.offs) - 1) or not views:
                 raise ValueError("bad request")
+            if len(views) > self.max_views or req.npix > self.max_pixels:
+                raise ValueError("request larger than a batch (%d views, %d pixels; limits %d, %d)"
+                                 % (len(views), req.npix, self.max_views, self.max_pixels))
             self._sums(req)  # validates the views
             if kind == "gradient":
                 # kept as the caller's arrays (no copy here); staged into
@@ -243,16 +266,21 @@ class Server:
         sh = _stream_handle(s)
         with torch.cuda.stream(s):
             slot.ev_start.record(s)
+            t0 = time.perf_counter()
             slot.images = _grow(slot.images, npix, torch.float32, dev)
             slot.h_images = _grow(slot.h_images, npix, torch.float32, pinned=True)
+            self.stats["host_grow_s"] += time.perf_counter() - t0
             r = slot.renderer
+            t0 = time.perf_counter()
             r.prepare(self.params, views, self.offs, stream=s, check=False, instances=self._inst_estimate(batch))
+            self.stats["host_prepare_s"] += time.perf_counter() - t0
             r.forward(images=slot.images, stream=s)
             seg, off = [], 0
             for q in batch:
                 seg.append((off, q.npix))
                 off += q.npix
             if grad:
+                t0 = time.perf_counter()
                 slot.dLdS = _grow(slot.dLdS, npix, torch.float32, dev)
                 slot.targets = _grow(slot.targets, npix, torch.float32, dev)
                 slot.h_targets = _grow(slot.h_targets, npix, torch.float32, pinned=True)
@@ -260,6 +288,7 @@ class Server:
                 slot.h_loss = _grow(slot.h_loss, len(batch), torch.float32, pinned=True)
                 slot.grads = _grow(slot.grads, self.n_total * 12, torch.float32, dev)
                 slot.h_grads = _grow(slot.h_grads, self.n_total * 12, torch.float32, pinned=True)
+                self.stats["host_grow_s"] += time.perf_counter() - t0
                 t0 = time.perf_counter()
                 for q, (o, n) in zip(batch, seg):  # multi-threaded host copies (torch), no GIL held
                     p = o

@@ -4,9 +4,10 @@
   (1e-3 per parameter group) alone and in the middle of a burst of mixed
   render and gradient requests that the scheduler batches and overlaps.
 - A served render matches the FP64 oracle.
-- Host-side failures stay local: an invalid request fails alone, a request
-  above the HBM budget is refused, a cancelled request is dropped, and the
-  other requests complete."""
+- Host-side failures stay local: an invalid request (bad geometry, a
+  target of the wrong size, more views than a batch holds) fails alone, a
+  request above the HBM budget is refused, a cancelled request is dropped,
+  and the other requests complete."""
 import math
 
 import numpy as np
@@ -95,8 +96,11 @@ def test_failures_stay_local():
         bad = srv.submit(0, [bad_view], "render")
         wrong_target = srv.submit(0, _views(8, 1), "gradient", [np.zeros((3, 3), np.float32)])
         huge = srv.submit(0, [sc.make_view(0.0, 45.0, 0.001, 0.001, 2048, 2048, center=(0, 0, 0.5))] * 8, "render")
+        too_many = srv.submit(0, _views(11, 2) * 40, "render")  # more views than a batch holds
         cancelled = srv.submit(1, _views(10, 2), "render")
         cancelled.cancel()
+        with pytest.raises(ValueError):
+            too_many.result(timeout=60)
         with pytest.raises(ValueError):
             bad.result(timeout=60)
         with pytest.raises(ValueError):
@@ -105,7 +109,7 @@ def test_failures_stay_local():
             huge.result(timeout=60)
         for f in good:
             assert len(f.result(timeout=120).images) == 2
-        assert srv.stats["invalid"] == 2 and srv.stats["refused"] == 1
+        assert srv.stats["invalid"] == 3 and srv.stats["refused"] == 1
         assert cancelled.cancelled() or cancelled.done()
     finally:
         srv.close(timeout=60)
