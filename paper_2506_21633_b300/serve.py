@@ -22,9 +22,11 @@ thread owns the GPU:
   slot, learned from the device status of earlier batches); a batch that
   overflows is re-queued at the head with a larger estimate.
 - Results (images, and gradients of the request's scene w.r.t. its own L1
-  loss) are copied to page-locked host memory on the slot's stream; the
-  request's latency runs from submit() to the moment its result is
-  host-visible.
+  loss) are copied to page-locked host memory on the slot's stream (two
+  buffer sets per slot, used in turn); a second host thread copies them into
+  the request's own arrays and resolves its future, so the scheduler thread
+  only forms, launches and retires batches.  The request's latency runs
+  from submit() to the moment its result is host-visible.
 
 All arithmetic runs in libsdgr.so; this module only schedules.
 """
@@ -32,6 +34,7 @@ from __future__ import annotations
 
 import collections
 import concurrent.futures
+import queue
 import threading
 import time
 
@@ -90,6 +93,17 @@ def _grow(buf, n, dtype, device=None, pinned=False):
     return torch.empty(int(n * 1.25), dtype=dtype, device=device)
 
 
+class _HostSet:
+    """Page-locked result buffers of one batch.  A slot has two, used in
+    turn: the finisher thread copies one batch's results out of one set
+    while the slot's next batch writes into the other."""
+
+    def __init__(self):
+        self.h_images = self.h_grads = self.h_loss = None
+        self.free = threading.Event()
+        self.free.set()
+
+
 class _Slot:
     def __init__(self, device):
         self.stream = torch.cuda.Stream(device=device)
@@ -97,7 +111,10 @@ class _Slot:
         self.device = device
         self.images = self.dLdS = self.targets = self.loss = None
         self.grads = None
-        self.h_images = self.h_targets = self.h_grads = self.h_loss = None
+        self.h_targets = None
+        self.sets = [_HostSet(), _HostSet()]
+        self.flip = 0
+        self.hs = None  # the host set of the batch in flight
         self.h_status = torch.zeros(4, dtype=torch.int32, pin_memory=True)
         self.event = torch.cuda.Event(enable_timing=True)
         self.ev_start = torch.cuda.Event(enable_timing=True)
@@ -112,10 +129,11 @@ class _Slot:
         self.targets = _grow(None, npix, f, device)
         self.loss = _grow(None, nreq, f, device)
         self.grads = _grow(None, ngrad, f, device)
-        self.h_images = _grow(None, npix, f, pinned=True)
         self.h_targets = _grow(None, npix, f, pinned=True)
-        self.h_loss = _grow(None, nreq, f, pinned=True)
-        self.h_grads = _grow(None, ngrad, f, pinned=True)
+        for hs in self.sets:
+            hs.h_images = _grow(None, npix, f, pinned=True)
+            hs.h_loss = _grow(None, nreq, f, pinned=True)
+            hs.h_grads = _grow(None, ngrad, f, pinned=True)
 
 
 class Server:
@@ -149,7 +167,13 @@ class Server:
         self.inflight_bytes = 0
         self.stats = {"batches": 0, "requests": 0, "refused": 0, "invalid": 0, "requeued": 0, "batch_sizes": [],
                       "max_inflight": 0, "host_form_s": 0.0, "host_launch_s": 0.0, "host_stage_targets_s": 0.0,
-                      "host_prepare_s": 0.0, "host_grow_s": 0.0, "host_retire_s": 0.0, "gpu_batch_s": 0.0}
+                      "host_prepare_s": 0.0, "host_grow_s": 0.0, "host_retire_s": 0.0, "host_finish_s": 0.0,
+                      "gpu_batch_s": 0.0}
+        # results are copied out and futures resolved by a second thread, so
+        # that the scheduler thread only forms, launches and retires batches
+        self._done = queue.SimpleQueue()
+        self._finisher = threading.Thread(target=self._finish_loop, name="sdgr-finisher", daemon=True)
+        self._finisher.start()
         self._thread = threading.Thread(target=self._loop, name="sdgr-server", daemon=True)
         self._thread.start()
 
@@ -197,6 +221,8 @@ class Server:
             self._stop = True
             self._cv.notify()
         self._thread.join(timeout)
+        self._done.put(None)
+        self._finisher.join(timeout)
 
     # -- accounting ----------------------------------------------------------
     def _inst_estimate(self, reqs):
@@ -264,11 +290,16 @@ class Server:
         npix = sum(r.npix for r in batch)
         s = slot.stream
         sh = _stream_handle(s)
+        hs = slot.sets[slot.flip]
+        slot.flip ^= 1
+        hs.free.wait()  # the finisher is done with this set's previous batch
+        hs.free.clear()
+        slot.hs = hs
         with torch.cuda.stream(s):
             slot.ev_start.record(s)
             t0 = time.perf_counter()
             slot.images = _grow(slot.images, npix, torch.float32, dev)
-            slot.h_images = _grow(slot.h_images, npix, torch.float32, pinned=True)
+            hs.h_images = _grow(hs.h_images, npix, torch.float32, pinned=True)
             self.stats["host_grow_s"] += time.perf_counter() - t0
             r = slot.renderer
             t0 = time.perf_counter()
@@ -285,9 +316,9 @@ class Server:
                 slot.targets = _grow(slot.targets, npix, torch.float32, dev)
                 slot.h_targets = _grow(slot.h_targets, npix, torch.float32, pinned=True)
                 slot.loss = _grow(slot.loss, len(batch), torch.float32, dev)
-                slot.h_loss = _grow(slot.h_loss, len(batch), torch.float32, pinned=True)
+                hs.h_loss = _grow(hs.h_loss, len(batch), torch.float32, pinned=True)
                 slot.grads = _grow(slot.grads, self.n_total * 12, torch.float32, dev)
-                slot.h_grads = _grow(slot.h_grads, self.n_total * 12, torch.float32, pinned=True)
+                hs.h_grads = _grow(hs.h_grads, self.n_total * 12, torch.float32, pinned=True)
                 self.stats["host_grow_s"] += time.perf_counter() - t0
                 t0 = time.perf_counter()
                 for q, (o, n) in zip(batch, seg):  # multi-threaded host copies (torch), no GIL held
@@ -303,9 +334,9 @@ class Server:
                 r.backward(slot.dLdS[:npix], slot.grads[:self.n_total * 12].view(-1, 12), stream=s)
                 for q in batch:
                     a, b = self.offs[q.scene] * 12, self.offs[q.scene + 1] * 12
-                    slot.h_grads[a:b].copy_(slot.grads[a:b], non_blocking=True)
-                slot.h_loss[:len(batch)].copy_(slot.loss[:len(batch)], non_blocking=True)
-            slot.h_images[:npix].copy_(slot.images[:npix], non_blocking=True)
+                    hs.h_grads[a:b].copy_(slot.grads[a:b], non_blocking=True)
+                hs.h_loss[:len(batch)].copy_(slot.loss[:len(batch)], non_blocking=True)
+            hs.h_images[:npix].copy_(slot.images[:npix], non_blocking=True)
             L.sdgr_copy_status_async(r.ws, slot.h_status.data_ptr(), sh)
             slot.event.record(s)
         slot.batch = batch
@@ -317,8 +348,9 @@ class Server:
         self.stats["max_inflight"] = max(self.stats["max_inflight"], sum(sl.batch is not None for sl in self.slots))
 
     def _retire(self, slot):
-        batch, seg = slot.batch, slot.seg
+        batch, seg, hs = slot.batch, slot.seg, slot.hs
         slot.batch = None
+        slot.hs = None
         self.stats["gpu_batch_s"] += slot.ev_start.elapsed_time(slot.event) / 1e3
         self.inflight_bytes -= slot.footprint
         slot.footprint = 0
@@ -333,19 +365,39 @@ class Server:
             with self._cv:
                 self.stats["requeued"] += len(batch)
                 self._pending.extendleft(reversed(batch))
+            hs.free.set()
             return
         if code != L.SDGR_OK:
             for q in batch:
                 _resolve(q.future, exc=L.SdgrError("device status", code))
+            hs.free.set()
             return
         ratio = required / max(vg, 1)
         for q in batch:  # running estimate of instances per view-Gaussian slot
             self.inst_ratio[q.scene] = 0.7 * self.inst_ratio[q.scene] + 0.3 * max(ratio, 1.0)
+        self._done.put((batch, seg, hs))
+
+    def _finish_loop(self):
+        while True:
+            job = self._done.get()
+            if job is None:
+                return
+            t0 = time.perf_counter()
+            try:
+                self._finish(*job)
+            except Exception as e:  # host-side failure: fail these requests, keep serving
+                for q in job[0]:
+                    _resolve(q.future, exc=e)
+            finally:
+                job[2].free.set()
+            self.stats["host_finish_s"] += time.perf_counter() - t0
+
+    def _finish(self, batch, seg, hs):
         for k, (q, (o, n)) in enumerate(zip(batch, seg)):
             # the request's own arrays, filled by multi-threaded copies out of
             # the slot's page-locked buffers (which the next batch reuses)
             flat = np.empty(n, dtype=np.float32)
-            torch.from_numpy(flat).copy_(slot.h_images[o:o + n])
+            torch.from_numpy(flat).copy_(hs.h_images[o:o + n])
             imgs, p = [], 0
             for v in q.views:
                 m = int(v["NA"]) * int(v["NR"])
@@ -355,8 +407,8 @@ class Server:
             if q.kind == "gradient":
                 a, b = self.offs[q.scene] * 12, self.offs[q.scene + 1] * 12
                 grads = np.empty(((b - a) // 12, 12), dtype=np.float32)
-                torch.from_numpy(grads).view(-1).copy_(slot.h_grads[a:b])
-                loss = float(slot.h_loss[k])
+                torch.from_numpy(grads).view(-1).copy_(hs.h_grads[a:b])
+                loss = float(hs.h_loss[k])
             now = time.perf_counter()
             q.t_done = now
             _resolve(q.future, Result(imgs, grads, loss, now - q.t_submit, len(batch)))
