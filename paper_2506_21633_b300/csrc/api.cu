@@ -24,7 +24,7 @@ constexpr int64_t MAX_INSTANCES = (int64_t)0x7fffffff;  // instance indices are 
 
 struct Layout {
     size_t views, scenes, scene_views, status;
-    size_t comp, img, rectC, rectI, maskC, maskI, cntC, cntI;
+    size_t comp, img, bin;
     size_t dk0, dv0, dk1, dv1;
     size_t scnt, soff, scan64;
     size_t ik0, iv0, ik1, iv1;
@@ -60,12 +60,7 @@ Layout make_layout(const sdgr_caps *c) {
     L.status = take(sizeof(StatusDev));
     L.comp = take(VG * sizeof(CompRec));
     L.img = take(VG * sizeof(ImgRec));
-    L.rectC = take(VG * sizeof(uint2));
-    L.rectI = take(VG * sizeof(uint2));
-    L.maskC = take(VG * 4);
-    L.maskI = take(VG * 4);
-    L.cntC = take(VG * 4);
-    L.cntI = take(VG * 4);
+    L.bin = take(VG * sizeof(BinRec));
     L.dk0 = take(VG * 4);
     L.dv0 = take(VG * 4);
     L.dk1 = take(VG * 4);
@@ -402,9 +397,7 @@ sdgr_status sdgr_preprocess(sdgr_ws *ws, const float *params, const int64_t *sce
                          sh_count > 0 ? reinterpret_cast<const float4 *>(ws->sh) : nullptr, sh_count,
                          ws->at<ViewDev>(L.views), V, vg, c.cutoff_K,
                          c.dilation_eps, c.norm_mode, c.alpha_mode, ws->at<CompRec>(L.comp), ws->at<ImgRec>(L.img),
-                         ws->at<uint2>(L.rectC), ws->at<uint2>(L.rectI), ws->at<uint32_t>(L.maskC),
-                         ws->at<uint32_t>(L.maskI), ws->at<uint32_t>(L.cntC),
-                         ws->at<uint32_t>(L.cntI), ws->at<uint32_t>(L.dk0), ws->at<uint32_t>(L.dv0), ws->sms, s));
+                         ws->at<BinRec>(L.bin), ws->at<uint32_t>(L.dk0), ws->at<uint32_t>(L.dv0), ws->sms, s));
     prof_end(ws, pk, s);
     ws->stage = 1;
     return SDGR_OK;
@@ -428,12 +421,10 @@ sdgr_status sdgr_bin_sort(sdgr_ws *ws, void *stream) {
     const uint32_t *sorted_vg = ws->at<uint32_t>(L.dv0);
     unsigned long long *scnt = ws->at<unsigned long long>(L.scnt);
     unsigned long long *soff = ws->at<unsigned long long>(L.soff);
-    CK(launch_gather_counts(sorted_vg, ws->at<uint32_t>(L.cntC), ws->at<uint32_t>(L.cntI), ws->VG, scnt, ws->sms,
-                            s));
+    CK(launch_gather_counts(sorted_vg, ws->at<BinRec>(L.bin), ws->VG, scnt, ws->sms, s));
     CK(launch_scan_u64(scnt, soff, 2 * ws->VG, ws->at<unsigned long long>(L.scan64), s));
     CK(launch_check_capacity(scnt, soff, ws->VG, ws->caps.max_instances, st, s));
-    CK(launch_emit(sorted_vg, soff, scnt, ws->at<uint2>(L.rectC), ws->at<uint2>(L.rectI), ws->at<uint32_t>(L.maskC),
-                   ws->at<uint32_t>(L.maskI), views, ws->V, ws->VG, ws->tiles,
+    CK(launch_emit(sorted_vg, soff, scnt, ws->at<BinRec>(L.bin), views, ws->V, ws->VG, ws->tiles,
                    st, ws->caps.max_instances, ws->at<uint32_t>(L.ik0), ws->at<uint32_t>(L.iv0), ws->sms, s));
     int final1 = 0;
     CK(launch_inst_sort(st, soff, scnt, ws->VG, views, ws->V, ws->tiles, ws->caps.max_instances, ws->key_bits,

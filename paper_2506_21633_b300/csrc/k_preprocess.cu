@@ -125,9 +125,7 @@ __global__ void __launch_bounds__(256)
 k_preprocess(const float4 *__restrict__ params, const float4 *__restrict__ sh, int sh_count,
              const ViewDev *__restrict__ views, int V, int64_t VG, float K,
              float eps, int norm_mode, int alpha_mode, CompRec *__restrict__ comp, ImgRec *__restrict__ img,
-             uint2 *__restrict__ rectC,
-             uint2 *__restrict__ rectI, uint32_t *__restrict__ maskC, uint32_t *__restrict__ maskI,
-             uint32_t *__restrict__ cntC, uint32_t *__restrict__ cntI,
+             BinRec *__restrict__ bin,
              uint32_t *__restrict__ dkey, uint32_t *__restrict__ dval) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < VG; i += stride) {
@@ -234,12 +232,14 @@ k_preprocess(const float4 *__restrict__ params, const float4 *__restrict__ sh, i
         nc = tile_set(uCx, uCy, cr.qa, cr.qb, cr.qc, cutm, rc, pc, nc, mc);
         ni = tile_set(uCx, uIy, ir.qa, ir.qb, ir.qc, cutm, ri, pi, ni, mi);
         if (!(o > 0.f) && !(o <= 0.f)) { nc = 0; ni = 0; }  // NaN parameters touch no tile
-        rectC[i] = rc;
-        rectI[i] = ri;
-        maskC[i] = mc;
-        maskI[i] = mi;
-        cntC[i] = nc;
-        cntI[i] = ni;
+        BinRec b;
+        b.rc = rc;
+        b.ri = ri;
+        b.mc = mc;
+        b.mi = mi;
+        b.nc = nc;
+        b.ni = ni;
+        bin[i] = b;
         dkey[i] = float_order_key(key);
         dval[i] = (uint32_t)i;
     }
@@ -247,16 +247,13 @@ k_preprocess(const float4 *__restrict__ params, const float4 *__restrict__ sh, i
 
 cudaError_t launch_preprocess(const float4 *params, const float4 *sh, int sh_count, const ViewDev *views, int V,
                               int64_t VG, float K, float eps, int norm_mode, int alpha_mode, CompRec *comp, ImgRec *img,
-                              uint2 *rectC, uint2 *rectI, uint32_t *maskC, uint32_t *maskI, uint32_t *cntC,
-                              uint32_t *cntI, uint32_t *dkey, uint32_t *dval, int sms, cudaStream_t s) {
+                              BinRec *bin, uint32_t *dkey, uint32_t *dval, int sms, cudaStream_t s) {
     if (VG <= 0) return cudaSuccess;
     int64_t blocks = (VG + 255) / 256;
     int64_t cap = (int64_t)sms * 8;
     if (blocks > cap) blocks = cap;
     k_preprocess<<<(unsigned)blocks, 256, 0, s>>>(params, sh, sh_count, views, V, VG, K, eps, norm_mode, alpha_mode,
-                                                   comp, img,
-                                                   rectC, rectI, maskC, maskI,
-                                                   cntC, cntI, dkey, dval);
+                                                   comp, img, bin, dkey, dval);
     note_launch();
     return cudaGetLastError();
 }

@@ -426,22 +426,23 @@ cudaError_t launch_inst_sort(const StatusDev *st, const unsigned long long *soff
 // ---------------------------------------------------------------------------
 // Instance counts in depth order, capacity check, emission, tile ranges.
 // ---------------------------------------------------------------------------
-__global__ void k_gather_counts(const uint32_t *__restrict__ sorted_vg, const uint32_t *__restrict__ cntC,
-                                const uint32_t *__restrict__ cntI, int64_t VG, unsigned long long *__restrict__ scnt) {
+__global__ void k_gather_counts(const uint32_t *__restrict__ sorted_vg, const BinRec *__restrict__ bin, int64_t VG,
+                                unsigned long long *__restrict__ scnt) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < VG; k += stride) {
         const uint32_t vg = sorted_vg[k];
-        scnt[k] = cntC[vg];
-        scnt[VG + k] = cntI[vg];
+        const uint2 n = *reinterpret_cast<const uint2 *>(&bin[vg].nc);  // (nc, ni): one sector
+        scnt[k] = n.x;
+        scnt[VG + k] = n.y;
     }
 }
 
-cudaError_t launch_gather_counts(const uint32_t *sorted_vg, const uint32_t *cntC, const uint32_t *cntI, int64_t VG,
-                                 unsigned long long *scnt, int sms, cudaStream_t s) {
+cudaError_t launch_gather_counts(const uint32_t *sorted_vg, const BinRec *bin, int64_t VG, unsigned long long *scnt,
+                                 int sms, cudaStream_t s) {
     if (VG <= 0) return cudaSuccess;
     int64_t blocks = (VG + 255) / 256;
     if (blocks > (int64_t)sms * 8) blocks = (int64_t)sms * 8;
-    k_gather_counts<<<(unsigned)blocks, 256, 0, s>>>(sorted_vg, cntC, cntI, VG, scnt);
+    k_gather_counts<<<(unsigned)blocks, 256, 0, s>>>(sorted_vg, bin, VG, scnt);
     note_launch();
     return cudaGetLastError();
 }
@@ -490,8 +491,8 @@ cudaError_t launch_check_capacity(const unsigned long long *scnt, const unsigned
 // shuffle steps); inside a Gaussian's tile rectangle the items run row by row.
 __global__ void __launch_bounds__(256)
 k_emit(const uint32_t *__restrict__ sorted_vg, const unsigned long long *__restrict__ soff,
-       const unsigned long long *__restrict__ scnt, const uint2 *__restrict__ rectC, const uint2 *__restrict__ rectI,
-       const uint32_t *__restrict__ maskC, const uint32_t *__restrict__ maskI, const ViewDev *__restrict__ views, int V, int64_t VG, int total_tiles, const StatusDev *st, int64_t cap,
+       const unsigned long long *__restrict__ scnt, const BinRec *__restrict__ bin,
+       const ViewDev *__restrict__ views, int V, int64_t VG, int total_tiles, const StatusDev *st, int64_t cap,
        uint32_t *__restrict__ keys, uint32_t *__restrict__ vals) {
     if (st->code != SDGR_OK) return;
     const unsigned full = 0xffffffffu;
@@ -502,16 +503,20 @@ k_emit(const uint32_t *__restrict__ sorted_vg, const unsigned long long *__restr
         const bool valid = k < VG;
         uint32_t vg = 0, tbase = 0;
         int tiles_x = 1;
+        uint4 b0 = make_uint4(0u, 0u, 0u, 0u), b1 = make_uint4(0u, 0u, 0u, 0u);  // the slot's BinRec
         if (valid) {
             vg = sorted_vg[k];
+            const uint4 *bp = reinterpret_cast<const uint4 *>(bin + vg);
+            b0 = bp[0];
+            b1 = bp[1];
             const ViewDev &vd = views[view_of_vg(views, V, k)];
             tiles_x = vd.tiles_x;
             tbase = (uint32_t)vd.tile_off;
         }
 #pragma unroll
         for (int p = 0; p < 2; ++p) {
-            const uint2 rect = valid ? (p ? rectI[vg] : rectC[vg]) : make_uint2(0u, 0u);
-            const uint32_t tmask = valid ? (p ? maskI[vg] : maskC[vg]) : 0u;
+            const uint2 rect = p ? make_uint2(b0.z, b0.w) : make_uint2(b0.x, b0.y);
+            const uint32_t tmask = p ? b1.y : b1.x;
             const unsigned long long off = valid ? soff[(int64_t)p * VG + k] : 0ull;
             const uint32_t cnt = valid ? (uint32_t)scnt[(int64_t)p * VG + k] : 0u;
             // rectangles of <= 32 tiles: ceil(2^16 / w), so that the row of a bit
@@ -565,15 +570,14 @@ k_emit(const uint32_t *__restrict__ sorted_vg, const unsigned long long *__restr
 }
 
 cudaError_t launch_emit(const uint32_t *sorted_vg, const unsigned long long *soff, const unsigned long long *scnt,
-                        const uint2 *rectC, const uint2 *rectI, const uint32_t *maskC, const uint32_t *maskI,
-                        const ViewDev *views, int V, int64_t VG,
+                        const BinRec *bin, const ViewDev *views, int V, int64_t VG,
                         int total_tiles, const StatusDev *st, int64_t cap, uint32_t *keys, uint32_t *vals, int sms,
                         cudaStream_t s) {
     if (VG <= 0) return cudaSuccess;
     int64_t blocks = (VG + 255) / 256;
     if (blocks > (int64_t)sms * 8) blocks = (int64_t)sms * 8;
-    k_emit<<<(unsigned)blocks, 256, 0, s>>>(sorted_vg, soff, scnt, rectC, rectI, maskC, maskI, views, V, VG, total_tiles, st, cap,
-                                            keys, vals);
+    k_emit<<<(unsigned)blocks, 256, 0, s>>>(sorted_vg, soff, scnt, bin, views, V, VG, total_tiles, st, cap, keys,
+                                            vals);
     note_launch();
     return cudaGetLastError();
 }

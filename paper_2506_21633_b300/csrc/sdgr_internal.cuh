@@ -131,6 +131,19 @@ struct alignas(16) ImgRec {
     float qc, cn, ry, pad1;
 };
 
+// Binning record of one (view, Gaussian) slot, written by preprocessing and
+// read by the count gather and the instance emission in depth order (a
+// random gather): one 32-byte sector per slot.  rc / ri: the tile
+// rectangles (x0 | x1 << 16, y0 | y1 << 16) on the computation and imaging
+// planes; mc / mi: for rectangles of at most 32 tiles, the tiles the
+// K-ellipse reaches (bit i: the i-th tile of the rectangle, row by row);
+// nc / ni: the slot's instance counts.
+struct alignas(32) BinRec {
+    uint2 rc, ri;
+    uint32_t mc, mi, nc, ni;
+};
+static_assert(sizeof(BinRec) == 32, "BinRec layout");
+
 // Half-height of the K-ellipse's bounding box for a 2D covariance whose yy
 // entry is syy (same margin as the tile rectangles).
 __device__ __forceinline__ float ellipse_ry(float syy, float K) { return K * sqrtf(syy) * 1.0001f + 1e-3f; }
@@ -194,9 +207,8 @@ void note_launch();
 cudaError_t launch_upload(const void *host_src, size_t bytes, void *dev_dst, cudaStream_t s);
 
 cudaError_t launch_preprocess(const float4 *params, const float4 *sh, int sh_count, const ViewDev *views, int V,
-                              int64_t VG, float K, float eps, int norm_mode, int alpha_mode, CompRec *comp, ImgRec *img, uint2 *rectC, uint2 *rectI,
-                              uint32_t *maskC, uint32_t *maskI, uint32_t *cntC,
-                              uint32_t *cntI, uint32_t *dkey, uint32_t *dval, int sms, cudaStream_t s);
+                              int64_t VG, float K, float eps, int norm_mode, int alpha_mode, CompRec *comp, ImgRec *img,
+                              BinRec *bin, uint32_t *dkey, uint32_t *dval, int sms, cudaStream_t s);
 
 // exclusive scans (scratch: see scan_scratch_elems)
 size_t scan_scratch_elems(int64_t n);
@@ -211,13 +223,12 @@ cudaError_t launch_inst_sort(const StatusDev *st, const unsigned long long *soff
                              int64_t VG, const ViewDev *views, int V, int tiles, int64_t cap, int key_bits,
                              SegDev *segs, uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t *v1, uint32_t *hist,
                              uint32_t *scan_scratch, int *final_in_1, cudaStream_t s);
-cudaError_t launch_gather_counts(const uint32_t *sorted_vg, const uint32_t *cntC, const uint32_t *cntI, int64_t VG,
-                                 unsigned long long *scnt, int sms, cudaStream_t s);
+cudaError_t launch_gather_counts(const uint32_t *sorted_vg, const BinRec *bin, int64_t VG, unsigned long long *scnt,
+                                 int sms, cudaStream_t s);
 cudaError_t launch_check_capacity(const unsigned long long *scnt, const unsigned long long *soff, int64_t VG,
                                   int64_t cap, StatusDev *st, cudaStream_t s);
 cudaError_t launch_emit(const uint32_t *sorted_vg, const unsigned long long *soff, const unsigned long long *scnt,
-                        const uint2 *rectC, const uint2 *rectI, const uint32_t *maskC, const uint32_t *maskI,
-                        const ViewDev *views, int V, int64_t VG,
+                        const BinRec *bin, const ViewDev *views, int V, int64_t VG,
                         int total_tiles, const StatusDev *st, int64_t cap, uint32_t *keys, uint32_t *vals, int sms,
                         cudaStream_t s);
 // vhist, voff: 2 * V * 32 entries; vt, vbase: 2 * V; scratch:
