@@ -417,8 +417,7 @@ int64_t sdgr_launch_count(void);
  * The first call on a device looks up the scratch array's device address
  * (once per device, with that device current), so make that first call
  * before any stream capture.  The call waits for `stream` before it returns
- * (it reads the device status word); a `stream` in capture mode is refused
- * with SDGR_ERR_INVALID before anything is enqueued.  Every call reuses the
+ * (it reads the device status word).  Every call reuses the
  * same scratch, which keeps the previous call's contents (everything that
  * must start at zero is cleared by the call); host threads are serialised by
  * a lock, but calls whose work overlaps on the GPU (e.g. from two processes

@@ -58,11 +58,6 @@ extern "C" sdgr_status sdgr_render_fwd_noalloc(const float *params, int64_t N, c
         N > SDGR_NOALLOC_MAX_GAUSSIANS)
         return SDGR_ERR_INVALID;
     if (N > 0 && (!params || ((uintptr_t)params) % 16 != 0)) return SDGR_ERR_INVALID;
-    // the call waits for its stream below: refuse a stream in capture mode
-    // before anything is enqueued, so that the caller's capture stays intact
-    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-    if (cudaStreamIsCapturing(static_cast<cudaStream_t>(stream), &cs) != cudaSuccess) return SDGR_ERR_CUDA;
-    if (cs != cudaStreamCaptureStatusNone) return SDGR_ERR_INVALID;
     const int64_t offsets[2] = {0, N};
     sdgr_caps need;
     if (sdgr_caps_for(views, V, offsets, 1, 0, &need) != SDGR_OK) return SDGR_ERR_INVALID;
