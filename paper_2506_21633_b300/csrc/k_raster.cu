@@ -16,10 +16,11 @@
 // Culling: when a batch is staged, each Gaussian gets the set of the tile's
 // eight 8x4 pixel blocks that its K-ellipse reaches (found from the ellipse's
 // exact horizontal extent over each band of four rows; an 8x8 block is the
-// union of two).  A warp walks only
-// the Gaussians whose set holds its block: per 32 staged Gaussians one ballot
-// gives the warp its hit list, which it visits in list order (front to back
-// for the intensity pass, back to front for its adjoint).  The intensity pass
+// union of two; the splat tests the sixteen 4x4 sub-blocks instead).  A warp
+// walks only the Gaussians whose set holds its block: per 32 staged Gaussians
+// one ballot gives the warp its hit list (the splat: one per half-warp), which
+// it visits in list order (front to back for the intensity pass, back to
+// front for its adjoint).  The intensity pass
 // and its adjoint first write the list out as byte indices (one popc per lane)
 // and walk that: a shared load per hit instead of a bit scan and a mask
 // update (-7 % and -5 % of their time).
@@ -209,6 +210,34 @@ __device__ __forceinline__ uint32_t block_mask(float u, float v, float qa, float
         const float xa = -u, xb = 8.f - u;
         if (xmax >= xa && xmin <= xa + 7.f) m |= 1u << (2 * rb);
         if (xmax >= xb && xmin <= xb + 7.f) m |= 2u << (2 * rb);
+    }
+    return m;
+}
+
+// The same test on the tile's sixteen 4 x 4 sub-blocks: bit 4 rb + cb for
+// rows 4 rb .. 4 rb + 3 and columns 4 cb .. 4 cb + 3.
+__device__ __forceinline__ uint32_t subblock_mask(float u, float v, float qa, float qb, float qc, float cutm,
+                                                  int2 rows) {
+    const float kx = -0.5f * __fdividef(qb, qa);
+    const float ky = -0.5f * __fdividef(qb, qc);
+    const float qs = fmaf(0.5f * qb, kx, qc);
+    const float qt = fmaf(0.5f * qb, ky, qa);
+    const float dyR = ky * sqrt_approx(fmaxf(0.f, __fdividef(cutm, qt)));
+    const float iqa = __fdividef(1.f, qa);
+    uint32_t m = 0;
+#pragma unroll
+    for (int rb = 0; rb < 4; ++rb) {
+        if (rows.x > 4 * rb + 3 || rows.y < 4 * rb) continue;
+        const float ya = (float)(4 * rb) - v, yb = ya + 3.f;
+        const float tR = fminf(fmaxf(dyR, ya), yb), tL = fminf(fmaxf(-dyR, ya), yb);
+        const float hR = sqrt_approx(fmaxf(0.f, (cutm - qs * tR * tR) * iqa));
+        const float hL = sqrt_approx(fmaxf(0.f, (cutm - qs * tL * tL) * iqa));
+        const float xmax = fmaf(kx, tR, hR), xmin = fmaf(kx, tL, -hL);
+#pragma unroll
+        for (int cb = 0; cb < 4; ++cb) {
+            const float xa = (float)(4 * cb) - u;
+            if (xmax >= xa && xmin <= xa + 3.f) m |= 1u << (4 * rb + cb);
+        }
     }
     return m;
 }
@@ -624,6 +653,9 @@ cudaError_t launch_intensity_fwd(const uint2 *ranges, const uint32_t *vals, cons
 }
 
 // Stage one imaging-plane record.
+// SUBBLOCKS: the 16-bit set of 4 x 4 sub-blocks (without the image-edge
+// mask) in place of the 8-bit set of 8 x 4 blocks.
+template <bool SUBBLOCKS = false>
 __device__ __forceinline__ void stage_img(const ImgRec *__restrict__ img, uint32_t vg, const TileCtx &c, float cutm,
                                           float4 &G, float2 &uv, float &cn, uint32_t &mask) {
     const float4 *ip = reinterpret_cast<const float4 *>(img + vg);
@@ -632,20 +664,28 @@ __device__ __forceinline__ void stage_img(const ImgRec *__restrict__ img, uint32
     G = make_float4(i0.z, i0.w, i1.x, 0.f);
     uv = make_float2(u, v);
     cn = i1.y;
-    mask = block_mask(u, v, i0.z, i0.w, i1.x, cutm, tile_rows(i0.y, i1.z, c.y0f)) & c.valid;
+    if constexpr (SUBBLOCKS)
+        mask = subblock_mask(u, v, i0.z, i0.w, i1.x, cutm, tile_rows(i0.y, i1.z, c.y0f));
+    else
+        mask = block_mask(u, v, i0.z, i0.w, i1.x, cutm, tile_rows(i0.y, i1.z, c.y0f)) & c.valid;
 }
 
 // ---------------------------------------------------------------------------
 // a8: imaging splat.  S[pixel] = sum_i c_i exp(-delta_I/2) I_i, I_i = P_i A_i.
-// Each pixel gathers over its warp's hit list; no reduction is needed.  Unlike
-// the other raster kernels the splat runs four warps per tile, each on an
-// 8 x 8 pixel block with two pixels per lane (rows r and r + 4 of the block):
-// the two pixels share the column part of the exponent (seven FMAs for both
-// instead of ten), the per-hit record loads and list walk serve two
-// pixels, and four warps wait at a barrier instead of eight (-10 % against
-// eight warps on 8 x 4 blocks, despite the coarser blocks).  A block's mask
-// bit is the union of its two 8 x 4 halves.  Every pixel is written: with a
-// work list (non-empty tiles only) the caller zeroes the images first.
+// Each pixel gathers over its hit list; no reduction is needed.  The splat
+// runs four warps per tile, each on an 8 x 8 pixel block with two pixels per
+// lane (rows r and r + 4 of one column): the two pixels share the column part
+// of the exponent (seven FMAs for both instead of ten), the per-hit record
+// loads and list walk serve two pixels, and four warps wait at a barrier
+// instead of eight (-10 % against eight warps on 8 x 4 blocks).  No pixel
+// depends on another, so the two 4 x 8 halves of a warp's block (its left and
+// right four columns) walk hit lists of their own, culled on the tile's 4 x 4
+// sub-blocks, side by side: the shorter list is padded with a null record.
+// Left and right, not top and bottom: on the imaging plane the rows run along
+// the slant range, which is the depth order of the list, so within 32 staged
+// Gaussians the hits of a top and a bottom half come one after the other
+// rather than side by side.  Every pixel is written: with a work list
+// (non-empty tiles only) the caller zeroes the images first.
 // ---------------------------------------------------------------------------
 template <int NB>
 __device__ __forceinline__ void
@@ -654,12 +694,16 @@ splat_fwd_tile(const int tile, const StatusDev *st, const uint2 *__restrict__ ra
                 const ViewDev *__restrict__ views, int V, float cut, bool ok, float *__restrict__ images) {
     constexpr int NT = 128;
     constexpr int PER = NB / NT;  // records staged per thread
-    __shared__ float4 sP[NB];  // (qa, qb, qc, l1)
-    __shared__ float4 sQ[NB];  // (l2, c0, c I, -)
+    __shared__ float4 sP[NB + 1];  // (qa, qb, qc, l1); entry NB: the null record
+    __shared__ float4 sQ[NB + 1];  // (l2, c0, c I, -)
     __shared__ uint32_t sM[NB];
-    __shared__ uint16_t sHL[4 * 32];  // per warp: its hit list of the current slice
-    const int t = threadIdx.x, w = t >> 5, l = t & 31;
-    uint16_t *const wl = sHL + 32 * w;
+    __shared__ uint16_t sHL[4 * 64];  // per warp: the hit lists of its two halves in the current slice
+    const int t = threadIdx.x, w = t >> 5, l = t & 31, h = l >> 4, j = l & 15;
+    uint16_t *const wl = sHL + 64 * w;  // half h walks wl[32 h ..]
+    if (t == 0) {  // no pixel is inside its cutoff: exponent -inf
+        sP[NB] = make_float4(0.f, 0.f, 0.f, 0.f);
+        sQ[NB] = make_float4(0.f, __int_as_float(0xff800000), 0.f, 0.f);
+    }
     TileCtx c;
     c.v = view_of_tile(views, V, tile);
     const ViewDev &vd = views[c.v];
@@ -674,10 +718,15 @@ splat_fwd_tile(const int tile, const StatusDev *st, const uint2 *__restrict__ ra
         for (int b = 0; b < 8; ++b)
             if (c.x0 + 8 * (b & 1) < vd.NA && c.y0 + 4 * (b >> 1) < vd.NR) c.valid |= 1u << b;
     }
-    const int X = 8 * (w & 1) + (l & 7), Y = 8 * (w >> 1) + (l >> 3);
+    // half h of warp w: the 4 x 8 block of columns 8 (w & 1) + 4 h .. + 3; its
+    // lanes take rows r and r + 4 of one column
+    const int X = 8 * (w & 1) + 4 * h + (j & 3), Y = 8 * (w >> 1) + (j >> 2);
     const int px = c.x0 + X, py0 = c.y0 + Y, py1 = py0 + 4;
     const bool in0 = px < vd.NA && py0 < vd.NR, in1 = px < vd.NA && py1 < vd.NR;
     const float fX = (float)X, fY0 = (float)Y, fY1 = (float)(Y + 4);
+    // sub-block bits of the warp's left half (rows 8 (w >> 1) .. + 7, two row
+    // bands); the right half's are the next ones
+    const uint32_t left = 0x11u << (8 * (w >> 1) + 2 * (w & 1)), right = left << 1;
     const uint2 r = ok ? rangesI[tile] : make_uint2(0u, 0u);
     const float cutm = cut_margin(cut);
     float acc0 = 0.f, acc1 = 0.f;
@@ -694,12 +743,11 @@ splat_fwd_tile(const int tile, const StatusDev *st, const uint2 *__restrict__ ra
                 float cn;
                 uint32_t m;
                 if (vg_ok(st, vd, vg)) {
-                    stage_img(img, vg, c, cutm, G, uv, cn, m);
+                    stage_img<true>(img, vg, c, cutm, G, uv, cn, m);
                     poly_coeffs(uv.x, uv.y, G.x, G.y, G.z, P, Q);
                     sP[k] = P;
                     sQ[k] = make_float4(Q.x, Q.y, cn * comp[vg].P * A[vg], 0.f);
-                    const uint32_t h = m | (m >> 2);  // 8 x 8 block 2 RB + cb: 8 x 4 blocks 4 RB + cb, 4 RB + 2 + cb
-                    sM[k] = (h & 3u) | ((h >> 2) & 0xcu);
+                    sM[k] = m;
                 } else {
                     sM[k] = 0;
                 }
@@ -709,15 +757,25 @@ splat_fwd_tile(const int tile, const StatusDev *st, const uint2 *__restrict__ ra
         __syncthreads();
         const int nb = min(NB, (int)(r.y - base));
         for (int k0 = 0; k0 < nb; k0 += 32) {
-            // this warp's hits in list order, as byte offsets of the staged records
-            const uint32_t hm = warp_hits(sM, k0, min(32, nb - k0));
-            __syncwarp();  // every lane has read the previous slice's list
-            if ((hm >> l) & 1u) wl[__popc(hm & ((1u << l) - 1u))] = (uint16_t)(16 * (k0 + l));
-            const int nh = __popc(hm);
+            // the two halves' hits in list order, as byte offsets of the staged
+            // records; the shorter list is padded with the null record, so that
+            // both halves walk max(n0, n1) entries in lockstep
+            const uint32_t mk = l < nb - k0 ? sM[k0 + l] : 0u;
+            const uint32_t hm0 = __ballot_sync(0xffffffffu, (mk & left) != 0u);
+            const uint32_t hm1 = __ballot_sync(0xffffffffu, (mk & right) != 0u);
+            const int n0 = __popc(hm0), n1 = __popc(hm1), nh = max(n0, n1);
+            const uint32_t lt = (1u << l) - 1u;
+            const uint16_t me = (uint16_t)(16 * (k0 + l));
+            __syncwarp();  // every lane has read the previous slice's lists
+            if ((hm0 >> l) & 1u) wl[__popc(hm0 & lt)] = me;
+            if ((hm1 >> l) & 1u) wl[32 + __popc(hm1 & lt)] = me;
+            if (l >= n0 && l < nh) wl[l] = (uint16_t)(16 * NB);
+            if (l >= n1 && l < nh) wl[32 + l] = (uint16_t)(16 * NB);
             __syncwarp();
+            const uint16_t *const hl = wl + 32 * h;
 #pragma unroll 8
             for (int i = 0; i < nh; ++i) {
-                const uint32_t off = wl[i];
+                const uint32_t off = hl[i];
                 const float4 P0 = *reinterpret_cast<const float4 *>(reinterpret_cast<const char *>(sP) + off);
                 const float4 Q0 = *reinterpret_cast<const float4 *>(reinterpret_cast<const char *>(sQ) + off);
                 const ColQ cq = poly_col(P0, Q0.x, Q0.y, fX);
