@@ -105,6 +105,39 @@ __device__ __forceinline__ TileCtx tile_ctx(const ViewDev *views, int V, int til
 // conversion instruction.
 __device__ __forceinline__ float small_u2f(uint32_t n) { return __fsub_rn(__uint_as_float(0x4B000000u | n), 8388608.f); }
 
+// Packed FP32 pairs: Blackwell's two-wide FP32 instructions (fma/add/mul
+// .rn.f32x2) do two IEEE round-to-nearest operations in one issue slot, on a
+// pair held in a 64-bit register (element 0 in the low half).  Each result
+// equals that of the scalar instruction on each element.
+struct F2 {
+    uint64_t v;
+};
+__device__ __forceinline__ F2 pk(float lo, float hi) {
+    F2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r.v) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ float2 unpk(F2 a) {
+    float2 r;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(a.v));
+    return r;
+}
+__device__ __forceinline__ F2 fma2(F2 a, F2 b, F2 c) {
+    F2 r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r.v) : "l"(a.v), "l"(b.v), "l"(c.v));
+    return r;
+}
+__device__ __forceinline__ F2 add2(F2 a, F2 b) {
+    F2 r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+    return r;
+}
+__device__ __forceinline__ F2 mul2(F2 a, F2 b) {
+    F2 r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+    return r;
+}
+
 // Tile-local pixel coordinates of the thread.
 struct LaneXY {
     float X, Y;
@@ -257,6 +290,26 @@ __device__ __forceinline__ void block_moments(const float4 &w, float dx, float d
     m[3] = fmaf(px, dx, m[3]);
     m[4] = fmaf(py, dx, m[4]);
     m[5] += pyy;
+}
+
+// The same for two columns at once, as pairs: W0..W3 the weights of rows
+// dy .. dy + 3 of both columns, DX their column offsets; adds into pair
+// accumulators (element i: column i's share).
+__device__ __forceinline__ void block_moments2(F2 W0, F2 W1, F2 W2, F2 W3, F2 DX, F2 DY, F2 M[6]) {
+    const F2 a = add2(W2, W3), b = add2(W1, a);
+    const F2 sw = add2(W0, b);                 // sum w_i
+    const F2 s1 = add2(add2(b, a), W3);        // sum w_i i
+    const F2 t = add2(a, add2(W3, W3));        // w_2 + 3 w_3
+    const F2 s2 = add2(s1, add2(t, t));        // sum w_i i^2
+    const F2 py = fma2(DY, sw, s1);            // sum w_i (dy + i)
+    const F2 pyy = fma2(DY, add2(py, s1), s2); // sum w_i (dy + i)^2
+    const F2 px = mul2(sw, DX);
+    M[0] = add2(M[0], sw);
+    M[1] = add2(M[1], px);
+    M[2] = add2(M[2], py);
+    M[3] = fma2(px, DX, M[3]);
+    M[4] = fma2(py, DX, M[4]);
+    M[5] = add2(M[5], pyy);
 }
 
 // Block list of an 8-bit block set m: the indices of its set bits in
@@ -820,10 +873,14 @@ cudaError_t launch_splat_fwd(const uint2 *rangesI, const uint32_t *vals, const I
 // dL/dI = c M0, dL/du_I, dL/dconic_I and dL/dc.  No pixel depends on
 // another here, so the kernel is Gaussian-parallel: two threads per
 // Gaussian walk its hit blocks, each thread four columns (four rows each) per
-// block, with dL/dS read from shared memory as one float4 per column; the two
-// partial moments meet by one shuffle each, and each thread issues three of
-// the six atomics.  (Against eight threads of one column each, the per-block
-// and per-Gaussian work is shared by four times the pixels: -13 %.)
+// block; the two partial moments meet by one shuffle each, and each thread
+// issues three of the six atomics.  (Against eight threads of one column each,
+// the per-block and per-Gaussian work is shared by four times the pixels:
+// -13 %.)  A thread's four columns form two pairs (c, c + 2) that run through
+// packed FP32 pair instructions -- the exponent's steps down the columns, the
+// weights and the moment sums -- two columns per issue slot (-10 %); the
+// dL/dS table interleaves the two columns of a pair, so that one float4 load
+// holds two rows of both.
 // ---------------------------------------------------------------------------
 template <int NB>
 __device__ __forceinline__ void
@@ -836,14 +893,19 @@ splat_bwd_tile(const int tile, const StatusDev *st, const uint2 *__restrict__ ra
     __shared__ uint32_t sM[NB];
     __shared__ uint32_t sid[NB];
     __shared__ uint8_t sperm[NB];
-    // dL/dS of the tile's pixels in table layout, then a block of zeros (block
-    // index 8 of the padded block lists)
+    // dL/dS of the tile's pixels, then a block of zeros (block index 8 of the
+    // padded block lists).  Per 8 x 4 block 32 entries: columns c and c + 2
+    // (c = 0, 1, 4, 5) interleaved as pairs, row by row, so that a float4 holds
+    // two rows of two columns and its halves are the pairs of the packed loop
     __shared__ __align__(16) float sg[TILE_PIX + 32];
     const int t = threadIdx.x, warp = t >> 5;
     const TileCtx c = tile_ctx(views, V, tile);
     const uint2 r = rangesI[tile];
     const float g = c.inside ? dLdS[c.pix] : 0.f;
-    sg[c.toff] = g;
+    {
+        const int col = t & 7, row = (t >> 3) & 3;
+        sg[32 * warp + 8 * (((col >> 2) << 1) | (col & 1)) + 2 * row + ((col >> 1) & 1)] = g;
+    }
     if (t < 32) sg[TILE_PIX + t] = 0.f;
     if (__syncthreads_count(g != 0.f) == 0) return;
     const float cutm = cut_margin(cut);
@@ -885,42 +947,63 @@ splat_bwd_tile(const int tile, const StatusDev *st, const uint2 *__restrict__ ra
             uint32_t bl = sBL[mb];
             const int cnt = __popc(mb);
             const float4 G = sG[ks];
-            const float qc2 = 2.f * G.z;
+            const F2 QC2 = pk(2.f * G.z, 2.f * G.z);
+            const float gy2 = 2.f * G.y, gx4 = 4.f * G.x, qc2s = 2.f * G.z;
             const float2 uv = sU[ks];
             const float dxa0 = (float)c2 - uv.x, dy00 = -uv.y;
-            float m[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            F2 M[6];
+#pragma unroll
+            for (int q = 0; q < 6; ++q) M[q] = pk(0.f, 0.f);
             const int rounds = __reduce_max_sync(0xffffffffu, cnt);
             for (int i = 0; i < rounds; ++i) {
                 const int b = (int)(bl & 15u);  // 8 past the Gaussian's blocks: zeros
                 bl >>= 4;
-                const float *src = sg + 32 * b + 4 * c2;
-                constexpr int step = 8;
+                const float *src = sg + 32 * b + 8 * c2;
                 const float dxa = (b & 1) ? dxa0 + 8.f : dxa0;
                 const float dy0 = fmaf(4.f, small_u2f((uint32_t)b >> 1), dy00);
+                const F2 DY = pk(dy0, dy0);
+                // columns c2 + 4 hp and c2 + 4 hp + 2 as one pair; down each
+                // column the exponent by differences
 #pragma unroll
-                for (int h = 0; h < 4; ++h) {
-                    const float dx = dxa + 2.f * (float)h;
-                    const float4 g4 = *reinterpret_cast<const float4 *>(src + step * h);
-                    const float Aq = G.x * dx * dx, Bq = G.y * dx;
-                    float4 w;
-                    float q = fmaf(fmaf(G.z, dy0, Bq), dy0, Aq);
-                    float dq = fmaf(qc2, dy0, G.z + Bq);
-                    w.x = q >= cut ? g4.x * ex2_approx(q) : 0.f;
-                    q += dq;
-                    dq += qc2;
-                    w.y = q >= cut ? g4.y * ex2_approx(q) : 0.f;
-                    q += dq;
-                    dq += qc2;
-                    w.z = q >= cut ? g4.z * ex2_approx(q) : 0.f;
-                    q += dq;
-                    w.w = q >= cut ? g4.w * ex2_approx(q) : 0.f;
-                    block_moments(w, dx, dy0, m);
+                for (int hp = 0; hp < 2; ++hp) {
+                    const float4 ga = *reinterpret_cast<const float4 *>(src + 16 * hp);      // rows 0, 1
+                    const float4 gb = *reinterpret_cast<const float4 *>(src + 16 * hp + 4);  // rows 2, 3
+                    const float dx = dxa + 4.f * (float)hp;  // the pair's first column; the second: dx + 2
+                    const F2 DX = pk(dx, dx + 2.f);
+                    // first column: q = qa dx^2 + qb dx dy + qc dy^2, dq its step
+                    // to the next row; second column: + qa (4 dx + 4) + 2 qb dy
+                    // and + 2 qb
+                    const float Bq = G.y * dx;
+                    const float q0 = fmaf(fmaf(G.z, dy0, Bq), dy0, G.x * dx * dx);
+                    const float dq0 = fmaf(qc2s, dy0, G.z + Bq);
+                    F2 q = pk(q0, q0 + fmaf(gx4, dx + 1.f, gy2 * dy0));
+                    F2 dq = pk(dq0, dq0 + gy2);
+                    const auto wts = [&](F2 qq, float g0, float g1) {
+                        const float2 e = unpk(qq);
+                        return mul2(pk(g0, g1), pk(e.x >= cut ? ex2_approx(e.x) : 0.f, e.y >= cut ? ex2_approx(e.y) : 0.f));
+                    };
+                    const F2 W0 = wts(q, ga.x, ga.y);
+                    q = add2(q, dq);
+                    dq = add2(dq, QC2);
+                    const F2 W1 = wts(q, ga.z, ga.w);
+                    q = add2(q, dq);
+                    dq = add2(dq, QC2);
+                    const F2 W2 = wts(q, gb.x, gb.y);
+                    q = add2(q, dq);
+                    const F2 W3 = wts(q, gb.z, gb.w);
+                    block_moments2(W0, W1, W2, W3, DX, DY, M);
                 }
             }
-            // the pair's partial moments: add across the two lanes, then lane c2
-            // issues the atomics of moments c2, c2 + 2, c2 + 4
+            // the thread's two columns of each pair, then the Gaussian's two
+            // threads: one shuffle each; lane c2 issues the atomics of moments
+            // c2, c2 + 2, c2 + 4
+            float m[6];
 #pragma unroll
-            for (int q = 0; q < 6; ++q) m[q] += __shfl_xor_sync(0xffffffffu, m[q], 1);
+            for (int q = 0; q < 6; ++q) {
+                const float2 h = unpk(M[q]);
+                m[q] = h.x + h.y;
+                m[q] += __shfl_xor_sync(0xffffffffu, m[q], 1);
+            }
             if (k < nb) {
                 float *dst = reinterpret_cast<float *>(accI + 2 * (size_t)sid[ks]);
 #pragma unroll
@@ -933,10 +1016,11 @@ splat_bwd_tile(const int tile, const StatusDev *st, const uint2 *__restrict__ ra
     }
 }
 
-// Held to five resident CTAs per SM (48 registers, no spills): -3 % against
-// the unbounded build's 64 registers and four CTAs.
+// Four resident CTAs per SM (64 registers; the 1024-record build spills a
+// few words): the packed pairs need the registers, and three CTAs per SM (no
+// spills) or scalar moment sums (no spills at 64) were 4 % and 2 % slower.
 template <int NB>
-__global__ void __launch_bounds__(256, 5)
+__global__ void __launch_bounds__(256, 4)
 k_splat_bwd(const uint2 *__restrict__ rangesI, const uint32_t *__restrict__ vals, const ImgRec *__restrict__ img,
             const float *__restrict__ dLdS, const ViewDev *__restrict__ views, int V, float cut, const StatusDev *st,
             float4 *__restrict__ accI, const TileSched sc) {
