@@ -190,6 +190,19 @@ __device__ __forceinline__ float poly_q(const float4 &P, float l2, float c0, con
     return poly_row(P, poly_col(P, l2, c0, L.X), L.Y);
 }
 
+// The same from a record laid out as R = (qa, qb, l1, l2) with qc apart (the
+// intensity pass's staging layout, which needs fewer registers there).
+__device__ __forceinline__ ColQ poly_col_r(const float4 &R, float c0, float X) {
+    ColQ c;
+    c.bx = __fmaf_rn(__fmaf_rn(R.x, X, R.z), X, c0);
+    c.my = __fmaf_rn(R.y, X, R.w);
+    return c;
+}
+
+__device__ __forceinline__ float poly_row_q(float qc, const ColQ &c, float Y) {
+    return __fmaf_rn(__fmaf_rn(qc, Y, c.my), Y, c.bx);
+}
+
 // Tile-local rows [x, y] that the K-ellipse of a Gaussian centred at row uy
 // with bounding-box half-height ry can reach (empty when x > y).
 __device__ __forceinline__ int2 tile_rows(float uy, float ry, float y0) {
@@ -504,8 +517,8 @@ intensity_fwd_tile(const int tile, const StatusDev *st, const uint2 *__restrict_
                    float *__restrict__ A, float *__restrict__ Tend, int32_t *__restrict__ last) {
     constexpr int NT = 128;
     constexpr int PER = NB / NT;  // records staged per thread
-    __shared__ float4 sP[NB];  // (qa, qb, qc, l1)
-    __shared__ float4 sQ[NB];  // (l2, c0 + log2 o, cut + log2 o, -); alpha_mode 1: (l2, c0, tau, -)
+    __shared__ float4 sP[NB];  // (qa, qb, l1, l2)
+    __shared__ float4 sQ[NB];  // (qc, c0 + log2 o, cut + log2 o, -); alpha_mode 1: (qc, c0, tau, -)
     __shared__ uint32_t sM[NB];
     __shared__ uint32_t sid[NB];
     __shared__ uint32_t sAcc[NB];  // sum of alpha T over the tile's 256 rays, in units of 2^-23 (< 2^31)
@@ -535,6 +548,7 @@ intensity_fwd_tile(const int tile, const StatusDev *st, const uint2 *__restrict_
     const int px = c.x0 + X, py0 = c.y0 + Y, py1 = py0 + 4;
     const bool in0 = px < vd.NA && py0 < vd.NR, in1 = px < vd.NA && py1 < vd.NR;
     const float fX = (float)X, fY0 = (float)Y, fY1 = (float)(Y + 4);
+    const F2 S23P = pk(S23, S23);
     const uint2 r = ranges[tile];
     const float cutm = cut_margin(cut);
     constexpr uint32_t WARP_BIAS = 0xC0000000u;  // 64 x bits(2^23), mod 2^32
@@ -546,9 +560,9 @@ intensity_fwd_tile(const int tile, const StatusDev *st, const uint2 *__restrict_
     const auto alphas = [&](uint32_t off, float &a0, float &a1) {
         const float4 P = *reinterpret_cast<const float4 *>(reinterpret_cast<const char *>(sP) + off);
         const float4 Q = *reinterpret_cast<const float4 *>(reinterpret_cast<const char *>(sQ) + off);
-        const ColQ cq = poly_col(P, Q.x, Q.y, fX);
-        const float q0 = poly_row(P, cq, fY0);
-        const float q1 = poly_row(P, cq, fY1);
+        const ColQ cq = poly_col_r(P, Q.y, fX);
+        const float q0 = poly_row_q(Q.x, cq, fY0);
+        const float q1 = poly_row_q(Q.x, cq, fY1);
         if constexpr (AM == 0) {  // Q.z: the folded cutoff; the exponent includes log2 o
             a0 = q0 >= Q.z ? ex2_approx(q0) : 0.f;
             a1 = q1 >= Q.z ? ex2_approx(q1) : 0.f;
@@ -577,8 +591,8 @@ intensity_fwd_tile(const int tile, const StatusDev *st, const uint2 *__restrict_
                     oz = oP.x;
                     if constexpr (AM == 0) fold_opacity(oP.x, cut, Q.y, oz);
                 }
-                sP[k] = P;
-                sQ[k] = make_float4(Q.x, Q.y, oz, 0.f);
+                sP[k] = make_float4(P.x, P.y, P.w, Q.x);
+                sQ[k] = make_float4(P.z, Q.y, oz, 0.f);
                 const uint32_t h = m | (m >> 2);  // 8 x 8 block 2 RB + cb: 8 x 4 blocks 4 RB + cb, 4 RB + 2 + cb
                 sM[k] = (h & 3u) | ((h >> 2) & 0xcu);
                 sid[k] = vg;
@@ -610,7 +624,10 @@ intensity_fwd_tile(const int tile, const StatusDev *st, const uint2 *__restrict_
                 const uint32_t off = wl[i];
                 float a0, a1;
                 alphas(off, a0, a1);
-                const uint32_t f = __float_as_uint(__fmaf_rn(a0, T0, S23)) + __float_as_uint(__fmaf_rn(a1, T1, S23));
+                // both rays' fixed-point weights in one packed FMA (the same
+                // roundings as two scalar ones)
+                const float2 fw = unpk(fma2(pk(a0, a1), pk(T0, T1), S23P));
+                const uint32_t f = __float_as_uint(fw.x) + __float_as_uint(fw.y);
                 const uint32_t ws = __reduce_add_sync(0xffffffffu, f);
                 mine = off == myoff ? ws : mine;
                 T0 = __fmaf_rn(-a0, T0, T0);
