@@ -49,13 +49,10 @@
 
 namespace sdgr {
 
-constexpr int BATCH = 256;    // Gaussian records staged per batch by the intensity adjoint
-static_assert(BATCH <= TILE_PIX && BATCH % 32 == 0, "the intensity adjoint stages one record per thread");
-constexpr int SUB = 32;       // Gaussians per weight table
-constexpr int WSTRIDE = 264;  // row stride of the weight table (floats)
 
 // Staging batch sizes (Gaussian records per CTA batch; a multiple of the CTA's
-// threads -- 256, or 128 for the splat -- each thread staging whole records).  Larger batches mean fewer
+// threads -- 128, or 256 for the splat adjoint -- each thread staging whole
+// records).  Larger batches mean fewer
 // barriers and shorter waits for the slowest warp of a batch, smaller ones
 // less shared memory (more resident CTAs) and less staging past the point
 // where every ray of a tile has stopped.  The intensity adjoint's weight
@@ -63,7 +60,7 @@ constexpr int WSTRIDE = 264;  // row stride of the weight table (floats)
 static const int kStageK3[] = {512, 256};
 static const int kStageK4[] = {512, 256};
 static const int kStageK5[] = {1024, 512, 256};
-static const int kStageK6[] = {256};
+static const int kStageK6[] = {128};
 
 struct TileCtx {
     int v;
@@ -72,7 +69,6 @@ struct TileCtx {
     int px, py;  // this thread's pixel
     bool inside;
     int64_t pix;
-    int toff;    // this pixel's entry in a weight-table row
     uint32_t valid;  // pixel blocks with at least one pixel inside the image
 };
 
@@ -90,9 +86,6 @@ __device__ __forceinline__ TileCtx tile_ctx(const ViewDev *views, int V, int til
     c.py = c.y0 + 4 * (w >> 1) + (l >> 3);
     c.inside = c.px < vd.NA && c.py < vd.NR;
     c.pix = vd.pix_off + (int64_t)c.py * vd.NA + c.px;
-    // table layout inside a block: column-major, so that the four rows of
-    // one column are one float4
-    c.toff = 32 * w + 4 * (l & 7) + (l >> 3);
     c.valid = 0;
 #pragma unroll
     for (int b = 0; b < 8; ++b)
@@ -132,23 +125,15 @@ __device__ __forceinline__ F2 add2(F2 a, F2 b) {
     asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
     return r;
 }
+__device__ __forceinline__ F2 sub2(F2 a, F2 b) {
+    F2 r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+    return r;
+}
 __device__ __forceinline__ F2 mul2(F2 a, F2 b) {
     F2 r;
     asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
     return r;
-}
-
-// Tile-local pixel coordinates of the thread.
-struct LaneXY {
-    float X, Y;
-};
-
-__device__ __forceinline__ LaneXY lane_xy() {
-    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    LaneXY L;
-    L.X = (float)(8 * (w & 1) + (l & 7));
-    L.Y = (float)(4 * (w >> 1) + (l >> 3));
-    return L;
 }
 
 // Exponent coefficients in tile-local coordinates.  With the centre (u, v)
@@ -184,10 +169,6 @@ __device__ __forceinline__ ColQ poly_col(const float4 &P, float l2, float c0, fl
 
 __device__ __forceinline__ float poly_row(const float4 &P, const ColQ &c, float Y) {
     return __fmaf_rn(__fmaf_rn(P.z, Y, c.my), Y, c.bx);
-}
-
-__device__ __forceinline__ float poly_q(const float4 &P, float l2, float c0, const LaneXY &L) {
-    return poly_row(P, poly_col(P, l2, c0, L.X), L.Y);
 }
 
 // The same from a record laid out as R = (qa, qb, l1, l2) with qc apart (the
@@ -288,26 +269,10 @@ __device__ __forceinline__ uint32_t subblock_mask(float u, float v, float qa, fl
     return m;
 }
 
-// Per-column moments of one block: weights w of rows dy, dy + 1, dy + 2,
-// dy + 3 at column offset dx; adds sum w, w dx, w dy, w dx^2, w dx dy, w dy^2.
-__device__ __forceinline__ void block_moments(const float4 &w, float dx, float dy, float m[6]) {
-    const float sw = (w.x + w.y) + (w.z + w.w);
-    const float s1 = fmaf(3.f, w.w, fmaf(2.f, w.z, w.y));  // sum w_i i
-    const float s2 = fmaf(9.f, w.w, fmaf(4.f, w.z, w.y));  // sum w_i i^2
-    const float py = fmaf(dy, sw, s1);                      // sum w_i (dy + i)
-    const float pyy = fmaf(dy, py + s1, s2);                // sum w_i (dy + i)^2
-    const float px = sw * dx;
-    m[0] += sw;
-    m[1] += px;
-    m[2] += py;
-    m[3] = fmaf(px, dx, m[3]);
-    m[4] = fmaf(py, dx, m[4]);
-    m[5] += pyy;
-}
-
-// The same for two columns at once, as pairs: W0..W3 the weights of rows
-// dy .. dy + 3 of both columns, DX their column offsets; adds into pair
-// accumulators (element i: column i's share).
+// Per-block moments of two columns at once, as pairs: W0..W3 the weights of
+// rows dy .. dy + 3 of both columns, DX their column offsets; adds sum w,
+// w dx, w dy, w dx^2, w dx dy, w dy^2 into the pair accumulators M (element
+// i: column i's share).
 __device__ __forceinline__ void block_moments2(F2 W0, F2 W1, F2 W2, F2 W3, F2 DX, F2 DY, F2 M[6]) {
     const F2 a = add2(W2, W3), b = add2(W1, a);
     const F2 sw = add2(W0, b);                 // sum w_i
@@ -341,25 +306,6 @@ __device__ __forceinline__ uint32_t block_list(uint32_t m) {
             ++n;
         }
     return n < 8 ? l | (0x88888888u << (4 * n)) : l;
-}
-
-// Sum of the six moments over a group of eight threads (cc = 0..7) and one
-// atomic per moment: each thread stores its partial moments into `scr` (48
-// floats owned by the group, moment-major), then thread cc < 6 adds the eight
-// partials of moment cc (two float4 loads) and issues that moment's atomic.
-// `scr` must be 16-byte aligned; the whole warp calls this.
-__device__ __forceinline__ void moments_out(float *scr, int cc, const float m[6], bool valid, float4 *acc,
-                                            uint32_t vg) {
-    __syncwarp();
-#pragma unroll
-    for (int q = 0; q < 6; ++q) scr[q * 8 + cc] = m[q];
-    __syncwarp();
-    if (cc < 6) {
-        const float4 a = *reinterpret_cast<const float4 *>(scr + cc * 8);
-        const float4 b = *reinterpret_cast<const float4 *>(scr + cc * 8 + 4);
-        const float v = ((a.x + a.y) + (a.z + a.w)) + ((b.x + b.y) + (b.z + b.w));
-        if (valid && v != 0.f) atomicAdd(reinterpret_cast<float *>(acc + 2 * (size_t)vg) + cc, v);
-    }
 }
 
 // Hit list of this warp among the staged Gaussians [k0, k0 + n) (n <= 32).
@@ -1075,218 +1021,356 @@ cudaError_t launch_splat_bwd(const uint2 *rangesI, const uint32_t *vals, const I
 // factor is > 0 because T_{i+1} >= Tfloor).  The pair update is branch-free
 // (weight 0 outside the cutoff leaves B and T unchanged).  Per
 // (view, Gaussian) the moments of w = dL/dalpha exp(-delta_C/2).
+//
+// Layout: four warps per tile, warp w on the 8 x 8 block of columns
+// 8 (w & 1) .. and rows 8 (w >> 1) ..; its lanes hold two rays each, rows r
+// and r + 4 of one column, and its two 4 x 8 halves (left: lanes 0..15,
+// right: 16..31) walk hit lists of their own, culled on the tile's eight
+// 4 x 8 half-blocks and padded to the same length with a staged Gaussian the
+// half does not reach (weight 0: B and T stay, and the 0 written is what its
+// table entry should hold).  The two rays of a lane share the column part of
+// the exponent, the list entry and the record loads, and go through the
+// recursion as packed FP32 pairs (the same roundings as scalar code).
+//
+// Phase 1 writes each ray's weight for each of its hit Gaussians into a
+// 32-Gaussian x 256-pixel shared table (a lane's two rays side by side);
+// phase 2 has four threads per Gaussian, thread q summing rows q and q + 4 of
+// every half-block the Gaussian reaches, the six moments as packed pairs
+// (the two rows), and a shuffle reduction over the four threads.
 // ---------------------------------------------------------------------------
+constexpr int ABATCH = 128;   // Gaussian records staged per batch: one per thread
+constexpr int ASUB = 32;      // Gaussians per weight table
+constexpr int AROW = 256;     // floats per weight-table row (one per pixel)
+
+// The tile's 4 x 8 half-blocks (bit 4 R + cb: rows 8 R .. 8 R + 7, columns
+// 4 cb .. 4 cb + 3) that a 4 x 4 sub-block set reaches.
+__device__ __forceinline__ uint32_t halves_of_subblocks(uint32_t ms) {
+    const uint32_t t = ms | (ms >> 4);
+    return (t & 0xfu) | ((t >> 4) & 0xf0u);
+}
+
 template <int AM>
 __device__ __forceinline__ void
 intensity_bwd_tile(const int tile, const StatusDev *st, const uint2 *__restrict__ ranges, const uint32_t *__restrict__ vals,
                    const CompRec *__restrict__ comp, const ImgRec *__restrict__ img, const float4 *__restrict__ accI,
                    const float *__restrict__ Tend, const int32_t *__restrict__ last,
-                   const ViewDev *__restrict__ views, int V, float cut, float4 *__restrict__ accC, const uint32_t *sBL,
-                   const float2 *sBO) {
-    __shared__ float4 sP[BATCH];  // (qa, qb, qc, l1)
-    __shared__ float4 sQ[BATCH];  // (l2, c0 + log2 o, cut + log2 o, chat); alpha_mode 1: (l2, c0, tau, chat)
-    __shared__ float2 sU[BATCH];  // tile-local centre
-    __shared__ uint32_t sM[BATCH];
-    __shared__ uint32_t sid[BATCH];
-    __shared__ uint8_t sperm[BATCH];
-    __shared__ __align__(16) float W[SUB * WSTRIDE];
-    __shared__ __align__(16) float zero12[12];  // reads at offsets -4 .. 7 from zero12 + 4
-    __shared__ __align__(4) uint16_t sHL[8 * 32];  // per warp: its hit list of the current slice
+                   const ViewDev *__restrict__ views, int V, float cut, float4 *__restrict__ accC, const uint32_t *sBL) {
+    __shared__ float4 sP[ABATCH];  // (qa, qb, l1, l2)
+    __shared__ float4 sQ[ABATCH];  // (qc, c0 + log2 o, cut + log2 o, chat); alpha_mode 1: (qc, c0, tau, chat)
+    __shared__ float2 sU[ABATCH];  // tile-local centre
+    __shared__ uint32_t sM[ABATCH];  // half-block set
+    __shared__ uint32_t sid[ABATCH];
+    __shared__ uint8_t sperm[ABATCH];
+    __shared__ __align__(16) float W[ASUB * AROW];
+    __shared__ __align__(16) float zero32[32];  // a half-block of zeros (phase-2 rounds past a Gaussian's list)
+    __shared__ __align__(4) uint16_t sHL[4 * 64];  // per warp: the hit lists of its two halves
     __shared__ int smax;
-    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
-    uint16_t *const wl = sHL + 32 * warp;
-    int nh = 0;
-    if (t < 12) zero12[t] = 0.f;
-    const TileCtx c = tile_ctx(views, V, tile);
-    const LaneXY L = lane_xy();
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31, h = lane >> 4, j16 = lane & 15;
+    uint16_t *const wl = sHL + 64 * warp;
+    const uint16_t *const hl = wl + 32 * h;
+    if (t < 32) zero32[t] = 0.f;
+    const int v = view_of_tile(views, V, tile);
+    const ViewDev &vd = views[v];
+    const int lt = tile - vd.tile_off;
+    const int x0 = (lt % vd.tiles_x) * TILE, y0 = (lt / vd.tiles_x) * TILE;
+    const float x0f = (float)x0, y0f = (float)y0;
+    uint32_t valid8 = 0;  // half-blocks with a pixel inside the image
+#pragma unroll
+    for (int b = 0; b < 8; ++b)
+        if (x0 + 4 * (b & 3) < vd.NA && y0 + 8 * (b >> 2) < vd.NR) valid8 |= 1u << b;
+    // this lane's rays: column X, rows Y and Y + 4 (tile-local)
+    const int X = 8 * (warp & 1) + 4 * h + (j16 & 3), Y = 8 * (warp >> 1) + (j16 >> 2);
+    const float fX = (float)X, fY0 = (float)Y, fY1 = (float)(Y + 4);
+    const int hbit = 4 * (warp >> 1) + 2 * (warp & 1);  // the left half's half-block; the right: hbit + 1
+    const int toff = 32 * (hbit + h) + 2 * j16;         // the lane's two table entries
     const uint2 r = ranges[tile];
-    const int32_t rec = c.inside ? last[c.pix] : 0;
-    const int32_t mylast = rec < 0 ? -rec : rec;  // negative: the ray stopped at the floor there
-    float T = c.inside ? Tend[c.pix] : 0.f;  // 0 outside the image: such a lane adds nothing
-    // a stopped ray holds T in front of its stopping pair, which it takes
-    // without a division; any other ray holds T behind its last pair
-    bool first = rec < 0;
+    int mylast[2];
+    float T[2], B[2] = {0.f, 0.f};
+    bool first[2];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const int px = x0 + X, py = y0 + Y + 4 * k;
+        const bool inside = px < vd.NA && py < vd.NR;
+        const int64_t pix = vd.pix_off + (int64_t)py * vd.NA + px;
+        const int32_t rec = inside ? last[pix] : 0;
+        mylast[k] = rec < 0 ? -rec : rec;  // negative: the ray stopped at the floor there
+        // a stopped ray holds T in front of its stopping pair, which it takes
+        // without a division; any other ray holds T behind its last pair
+        T[k] = inside ? Tend[pix] : 0.f;  // 0 outside the image: such a ray adds nothing
+        first[k] = rec < 0;
+    }
     if (t == 0) smax = 0;
     __syncthreads();
-    if (mylast > 0) atomicMax(&smax, mylast);
+    if (max(mylast[0], mylast[1]) > 0) atomicMax(&smax, max(mylast[0], mylast[1]));
     __syncthreads();
     const int hi0 = smax;
     const float cutm = cut_margin(cut);
-    float B = 0.f;
+    const F2 ONE = pk(1.f, 1.f);
     uint32_t vnext = 0u;  // next batch's list entry, loaded one batch ahead
-    if (hi0 > (int)r.x && t < hi0 - max((int)r.x, hi0 - BATCH)) vnext = vals[max((int)r.x, hi0 - BATCH) + t];
-    for (int hi = hi0; hi > (int)r.x; hi -= BATCH) {
-        const int lo = max((int)r.x, hi - BATCH);
+    if (hi0 > (int)r.x && t < hi0 - max((int)r.x, hi0 - ABATCH)) vnext = vals[max((int)r.x, hi0 - ABATCH) + t];
+    for (int hi = hi0; hi > (int)r.x; hi -= ABATCH) {
+        const int lo = max((int)r.x, hi - ABATCH);
         const int nb = hi - lo;
         __syncthreads();
         if (t < nb) {
             const uint32_t vg = vnext;
-            float4 P;
-            float2 Q, uv, oP;
+            // a record that fails the entry check reaches no pixel: exponent
+            // -inf, no half-block (it may serve as a half's padding entry)
+            float4 P = make_float4(0.f, 0.f, 0.f, 0.f);
+            float2 Q = make_float2(0.f, __int_as_float(0xff800000)), uv = make_float2(0.f, 0.f);
             uint32_t m = 0;
-            float dLdI = 0.f;
-            float oz = 0.f;
-            if (vg_ok(st, views[c.v], vg)) {
-                stage_comp(comp, vg, c, cutm, P, Q, m, uv, oP);
-                dLdI = accI[2 * (size_t)vg].x * img[vg].cn;
-                oz = oP.x;
-                if constexpr (AM == 0) fold_opacity(oP.x, cut, Q.y, oz);
+            float chat = 0.f, oz = 0.f;
+            if (vg_ok(st, vd, vg)) {
+                const float4 *cp = reinterpret_cast<const float4 *>(comp + vg);
+                const float4 c0 = cp[0], c1 = cp[1];  // (ux, uy, qa, qb), (qc, o, P, ry)
+                const float u = __fsub_rn(c0.x, x0f), w = __fsub_rn(c0.y, y0f);
+                poly_coeffs(u, w, c0.z, c0.w, c1.x, P, Q);
+                m = halves_of_subblocks(
+                        subblock_mask(u, w, c0.z, c0.w, c1.x, cutm, tile_rows(c0.y, c1.w, y0f))) & valid8;
+                uv = make_float2(u, w);
+                chat = accI[2 * (size_t)vg].x * img[vg].cn * c1.z;
+                oz = c1.y;
+                if constexpr (AM == 0) fold_opacity(c1.y, cut, Q.y, oz);
             }
-            sP[t] = P;
-            sQ[t] = make_float4(Q.x, Q.y, oz, dLdI * oP.y);
+            sP[t] = make_float4(P.x, P.y, P.w, Q.x);
+            sQ[t] = make_float4(P.z, Q.y, oz, chat);
             sU[t] = uv;
             sM[t] = m;
             sid[t] = vg;
         }
         {
-            const int nlo = max((int)r.x, lo - BATCH);
+            const int nlo = max((int)r.x, lo - ABATCH);
             if (lo > (int)r.x && t < lo - nlo) vnext = vals[nlo + t];
         }
         __syncthreads();
         // slices of 32 from the top of the batch: slice s = [nb - 32 (s + 1), nb - 32 s)
-        if (warp * SUB < nb) {
-            const int send = nb - warp * SUB, sub = max(0, send - SUB);
-            order_by_blocks(sM, sub, send - sub, sperm + warp * SUB);
+        if (warp * ASUB < nb) {
+            const int send = nb - warp * ASUB, sub = max(0, send - ASUB);
+            order_by_blocks(sM, sub, send - sub, sperm + warp * ASUB);
         }
-        const int lim = mylast - lo;  // this ray takes staged Gaussians k < lim
-        for (int sl = 0; sl * SUB < nb; ++sl) {
-            const int send = nb - sl * SUB, sub = max(0, send - SUB);
+        int lim[2];  // a ray takes staged Gaussians k < lim
+#pragma unroll
+        for (int k = 0; k < 2; ++k) lim[k] = mylast[k] - lo;
+        for (int sl = 0; sl * ASUB < nb; ++sl) {
+            const int send = nb - sl * ASUB, sub = max(0, send - ASUB);
             const int ns = send - sub;
-            // this warp's hits back to front (descending), as byte offsets 16 k
-            // of the staged records k
+            // each half's hits back to front (descending), as byte offsets 16 k
+            // of the staged records k; the shorter list padded with a record of
+            // the slice that the half does not reach
+            int nh;
             {
-                const uint32_t hm = warp_hits(sM, sub, ns);
-                if ((hm >> lane) & 1u) wl[__popc(hm >> lane) - 1] = (uint16_t)(16 * (sub + lane));
-                nh = __popc(hm);
+                const uint32_t mk = lane < ns ? sM[sub + lane] : 0u;
+                const uint32_t h0 = __ballot_sync(0xffffffffu, (mk >> hbit) & 1u);
+                const uint32_t h1 = __ballot_sync(0xffffffffu, (mk >> (hbit + 1)) & 1u);
+                const int n0 = __popc(h0), n1 = __popc(h1);
+                nh = max(n0, n1);
+                const uint32_t live = ns >= 32 ? 0xffffffffu : (1u << ns) - 1u;
+                const uint16_t me = (uint16_t)(16 * (sub + lane));
+                __syncwarp();  // every lane has read the previous slice's lists
+                if ((h0 >> lane) & 1u) wl[__popc(h0 >> lane) - 1] = me;
+                if ((h1 >> lane) & 1u) wl[32 + __popc(h1 >> lane) - 1] = me;
+                if (lane >= n0 && lane < nh) wl[lane] = (uint16_t)(16 * (sub + __ffs(~h0 & live) - 1));
+                if (lane >= n1 && lane < nh) wl[32 + lane] = (uint16_t)(16 * (sub + __ffs(~h1 & live) - 1));
                 __syncwarp();
             }
-            // the table entry of staged record k for this ray: byte
-            // 66 (16 k) + wb = 4 ((k - sub) WSTRIDE + toff)
-            static_assert(WSTRIDE * 4 == 66 * 16, "weight table row: 66 record strides");
-            const int wb = 4 * c.toff - 4 * WSTRIDE * sub;
-            // one hit: the pair's exponent q with the staged record at byte
-            // offset off (Q.z: opacity field, Q.w: c-hat); FAST: no index bound
-            // and no stopped ray ahead of its stopping pair in the warp
-            const auto hit = [&](auto fast, uint32_t off, float q, const float4 &Q) {
-                constexpr bool F = decltype(fast)::value;
-                const float cq = AM == 0 ? Q.z : cut;  // the folded cutoff (alpha_mode 0)
-                const bool in = F ? q >= cq : (q >= cq) & ((int)(off >> 4) < lim);
-                float *const wp = reinterpret_cast<float *>(reinterpret_cast<char *>(W) + (int)(off * 66u) + wb);
-                const float e = in ? ex2_approx(q) : 0.f;
-                // T in front of the pair: T behind it / (1 - alpha), relative
-                // error of a few ulp per step.  Outside the cutoff alpha = 0,
-                // and rcp.approx(1) is exactly 1 (the library's device
-                // self-check), so T stays as it is.
-                const auto rebuild = [&](float om) {
-                    const float Td = T * rcp_approx(om);
-                    if constexpr (F) {
-                        T = Td;
-                    } else {
-                        T = (in & !first) ? Td : T;
-                        first = first & !in;
-                    }
-                };
-                if constexpr (AM == 0) {
-                    // e is alpha itself (the exponent includes log2 o)
-                    rebuild(__fsub_rn(1.f, e));
-                    const float ad = e * (Q.w - B);
-                    B += ad;
-                    // weight: dL/dalpha alpha = o dL/dalpha G (the parameter
-                    // adjoint divides the moments by o)
-                    *wp = T * ad;
-                } else {
-                    const float alpha = alpha_of<AM>(Q.z, e);
-                    const float om = __fsub_rn(1.f, alpha);
-                    rebuild(om);
-                    const float d = Q.w - B;
-                    B = fmaf(alpha, d, B);
-                    // weight of the profile: d alpha / d G = tau (1 - alpha)
-                    *wp = T * d * (e * om);
-                }
+            // table entries of staged record k for this lane's rays: byte
+            // 64 (16 k) + wb = 4 ((k - sub) AROW + toff)
+            static_assert(AROW * 4 == 64 * 16, "weight table row: 64 record strides");
+            const int wb = 4 * toff - 4 * AROW * sub;
+            const auto rec = [&](const float4 *a, uint32_t off) {
+                return *reinterpret_cast<const float4 *>(reinterpret_cast<const char *>(a) + off);
             };
-            // the hit list back to front, two hits per iteration, then an odd one
-            const auto walk = [&](auto fast) {
-                int i = 0;
-                const auto rec = [&](const float4 *a, uint32_t off) {
-                    return *reinterpret_cast<const float4 *>(reinterpret_cast<const char *>(a) + off);
-                };
-                for (; i + 1 < nh; i += 2) {
-                    const uint32_t pr = *reinterpret_cast<const uint32_t *>(wl + i);
-                    const uint32_t o0 = pr & 0xffffu, o1 = pr >> 16;
-                    const float4 P0 = rec(sP, o0), Q0 = rec(sQ, o0);
-                    const float4 P1 = rec(sP, o1), Q1 = rec(sQ, o1);
-                    const float q0 = poly_q(P0, Q0.x, Q0.y, L);
-                    const float q1 = poly_q(P1, Q1.x, Q1.y, L);
-                    hit(fast, o0, q0, Q0);
-                    hit(fast, o1, q1, Q1);
-                }
-                if (i < nh) {
-                    const uint32_t o0 = wl[i];
-                    const float4 P0 = rec(sP, o0), Q0 = rec(sQ, o0);
-                    hit(fast, o0, poly_q(P0, Q0.x, Q0.y, L), Q0);
+            const auto hit = [&](auto fast, uint32_t off, const float4 &P, const float4 &Q) {
+                constexpr bool F = decltype(fast)::value;
+                const ColQ cq = poly_col_r(P, Q.y, fX);
+                const float q[2] = {poly_row_q(Q.x, cq, fY0), poly_row_q(Q.x, cq, fY1)};
+                float2 *const wp = reinterpret_cast<float2 *>(reinterpret_cast<char *>(W) + (int)(off * 64u) + wb);
+                const float cq0 = AM == 0 ? Q.z : cut;  // the folded cutoff (alpha_mode 0)
+                {
+                    float wv[2];
+#pragma unroll
+                    for (int k = 0; k < 2; ++k) {
+                        const bool in = F ? q[k] >= cq0 : (q[k] >= cq0) & ((int)(off >> 4) < lim[k]);
+                        const float e = in ? ex2_approx(q[k]) : 0.f;
+                        // T in front of the pair: T behind it / (1 - alpha)
+                        const auto rebuild = [&](float om) {
+                            const float Td = T[k] * rcp_approx(om);
+                            if constexpr (F) {
+                                T[k] = Td;
+                            } else {
+                                T[k] = (in & !first[k]) ? Td : T[k];
+                                first[k] = first[k] & !in;
+                            }
+                        };
+                        if constexpr (AM == 0) {
+                            rebuild(__fsub_rn(1.f, e));
+                            const float ad = e * (Q.w - B[k]);
+                            B[k] += ad;
+                            wv[k] = T[k] * ad;
+                        } else {
+                            const float alpha = alpha_of<AM>(Q.z, e);
+                            const float om = __fsub_rn(1.f, alpha);
+                            rebuild(om);
+                            const float d = Q.w - B[k];
+                            B[k] = fmaf(alpha, d, B[k]);
+                            // weight of the profile: d alpha / d G = tau (1 - alpha)
+                            wv[k] = T[k] * d * (e * om);
+                        }
+                    }
+                    *wp = make_float2(wv[0], wv[1]);
                 }
             };
             // fast path: no ray of the warp is a stopped one still behind its
             // stopping pair (walking back to front) -- then the forward pass
             // took every in-cutoff pair still ahead (no index bound), and T is
             // always rebuilt by division
-            if (__all_sync(0xffffffffu, !first))
-                walk(std::true_type{});
-            else
+            // the next hit's list entry and records are loaded before this
+            // hit's table store (which the compiler cannot move them past)
+            const auto walk = [&](auto fast) {
+                if (nh == 0) return;
+                uint32_t off = hl[0];
+                float4 P = rec(sP, off), Q = rec(sQ, off);
+                for (int i = 0; i < nh; ++i) {
+                    const uint32_t offn = hl[min(i + 1, nh - 1)];
+                    const float4 Pn = rec(sP, offn), Qn = rec(sQ, offn);
+                    hit(fast, off, P, Q);
+                    off = offn;
+                    P = Pn;
+                    Q = Qn;
+                }
+            };
+            // alpha_mode 0, fast path (no index bound, T always rebuilt by
+            // division), as a two-stage pipeline: the part of a hit that does
+            // not depend on T and B (records, exponents, alpha, 1 / (1 - alpha))
+            // is done one hit ahead of the recursion (-5 % of the kernel).  e is
+            // alpha itself (the exponent includes log2 o); outside the cutoff
+            // alpha = 0 and rcp.approx(1) = 1 (the library's device self-check),
+            // so T and B stay as they are.  The weight is dL/dalpha alpha =
+            // o dL/dalpha G (the parameter adjoint divides the moments by o).
+            struct Pre {
+                F2 E, RC;
+                float chat;
+                uint32_t off;
+            };
+            const auto pre = [&](uint32_t off) {
+                const float4 P = rec(sP, off), Q = rec(sQ, off);
+                const ColQ cq = poly_col_r(P, Q.y, fX);
+                const float q0 = poly_row_q(Q.x, cq, fY0), q1 = poly_row_q(Q.x, cq, fY1);
+                Pre r;
+                r.E = pk(q0 >= Q.z ? ex2_approx(q0) : 0.f, q1 >= Q.z ? ex2_approx(q1) : 0.f);
+                const float2 om = unpk(sub2(ONE, r.E));
+                r.RC = pk(rcp_approx(om.x), rcp_approx(om.y));
+                r.chat = Q.w;
+                r.off = off;
+                return r;
+            };
+            const auto apply = [&](const Pre &c) {
+                const F2 TT = mul2(pk(T[0], T[1]), c.RC);
+                const F2 AD = mul2(c.E, pk(c.chat - B[0], c.chat - B[1]));
+                const float2 b2 = unpk(add2(pk(B[0], B[1]), AD)), t2 = unpk(TT);
+                T[0] = t2.x;
+                T[1] = t2.y;
+                B[0] = b2.x;
+                B[1] = b2.y;
+                *reinterpret_cast<float2 *>(reinterpret_cast<char *>(W) + (int)(c.off * 64u) + wb) = unpk(mul2(TT, AD));
+            };
+            if (__all_sync(0xffffffffu, !(first[0] | first[1]))) {
+                if constexpr (AM == 0) {
+                    if (nh > 0) {
+                        Pre cur = pre(hl[0]);
+                        for (int i = 0; i < nh; ++i) {
+                            const Pre nxt = pre(hl[min(i + 1, nh - 1)]);
+                            apply(cur);
+                            cur = nxt;
+                        }
+                    }
+                } else {
+                    walk(std::true_type{});
+                }
+            } else {
                 walk(std::false_type{});
-            __syncthreads();
-            // eight threads per Gaussian: thread cc takes the column pair cp
-            // (columns 2 cp and 2 cp + 1) of every other block of the
-            // Gaussian's list, from list position hb: the per-block work is
-            // shared by two columns, and each thread walks half the blocks.
-            // It reads column 2 cp + hb first, so that the two halves of a
-            // group load disjoint banks.
-            const int j = sperm[sl * SUB + (t >> 3)], cc = t & 7;
-            const int cp = cc & 3, hb = cc >> 2;
-            const uint32_t mb = j < ns ? sM[sub + j] : 0u;
-            uint32_t bl = sBL[mb] >> (4 * hb);
-            const int cnt = (__popc(mb) + 1 - hb) >> 1;  // list positions hb, hb + 2, ...
-            const float2 uv = sU[sub + (j < ns ? j : 0)];
-            const float dxa = (float)(2 * cp + hb) - uv.x, dxb = (float)(2 * cp + 1 - hb) - uv.x, dy00 = -uv.y;
-            const float *wr = W + j * WSTRIDE + 8 * cp + 4 * hb;
-            const int o2 = 4 - 8 * hb;  // the second column, relative to the first
-            float m[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-            const int rounds = __reduce_max_sync(0xffffffffu, cnt);
-            for (int i = 0; i < rounds; ++i) {
-                const int b = (int)(bl & 7u);
-                bl >>= 8;
-                const float *src = i < cnt ? wr + 32 * b : zero12 + 4;
-                const float4 wa = *reinterpret_cast<const float4 *>(src);
-                const float4 wc = *reinterpret_cast<const float4 *>(src + o2);
-                const float2 o = sBO[b];  // the block's offset from the tile origin
-                const float dy = dy00 + o.y;
-                block_moments(wa, dxa + o.x, dy, m);
-                block_moments(wc, dxb + o.x, dy, m);
             }
-            // the group's table row is free after the reads above: scratch, at
-            // an offset that puts the four groups of the warp on disjoint banks
-            // (row j starts at bank 8 j mod 32)
-            moments_out(W + j * WSTRIDE + 8 * ((((t >> 3) & 3) - j) & 3), cc, m, j < ns, accC,
-                        sid[sub + (j < ns ? j : 0)]);
+            __syncthreads();
+            // phase 2: four threads per Gaussian (slots sorted by half-block
+            // count, so that the eight Gaussians of a warp take about as many
+            // rounds); thread q sums rows q and q + 4 of both column pairs of
+            // each half-block.  Per float4 (rows q, q + 4 of columns c, c + 1):
+            // A, B the two columns' pairs, S = A + B; with dx the column c
+            // offset, sum w dx = dx S + B, sum w dx^2 = dx^2 S + (2 dx + 1) B.
+            // The first float4 read alternates with the slot, so that the two
+            // Gaussians of a quarter-warp load disjoint banks.
+            {
+                const int slot = t >> 2, q = t & 3;
+                const int jg = sperm[sl * ASUB + slot];
+                const bool valid = jg < ns;
+                const uint32_t mh = valid ? sM[sub + jg] & 0xffu : 0u;
+                uint32_t bl = sBL[mh];
+                const int cnt = __popc(mh);
+                const float2 uv = sU[sub + (valid ? jg : 0)];
+                const float *const wr = W + jg * AROW + 8 * q;
+                const int s0 = (q + slot) & 1;
+                F2 M[6];
+#pragma unroll
+                for (int k = 0; k < 6; ++k) M[k] = pk(0.f, 0.f);
+                const int rounds = __reduce_max_sync(0xffffffffu, cnt);
+                for (int i = 0; i < rounds; ++i) {
+                    const uint32_t hb = bl & 7u;
+                    bl >>= 4;
+                    const float *src = i < cnt ? wr + 32 * hb : zero32 + 8 * q;
+                    const float dy = small_u2f(8u * (hb >> 2) + (uint32_t)q) - uv.y;
+                    const F2 DY = pk(dy, dy + 4.f), DYY = mul2(DY, DY);
+#pragma unroll
+                    for (int ss = 0; ss < 2; ++ss) {
+                        const int s = s0 ^ ss;
+                        const float4 v4 = *reinterpret_cast<const float4 *>(src + 4 * s);
+                        const float dx = small_u2f(4u * (hb & 3u) + 2u * (uint32_t)s) - uv.x;
+                        const F2 DX = pk(dx, dx);
+                        const F2 A = pk(v4.x, v4.y), Bc = pk(v4.z, v4.w);
+                        const F2 S = add2(A, Bc);
+                        const F2 P1 = fma2(DX, S, Bc);
+                        M[0] = add2(M[0], S);
+                        M[1] = add2(M[1], P1);
+                        M[2] = fma2(DY, S, M[2]);
+                        M[3] = fma2(mul2(DX, DX), S, fma2(add2(add2(DX, DX), ONE), Bc, M[3]));
+                        M[4] = fma2(DY, P1, M[4]);
+                        M[5] = fma2(DYY, S, M[5]);
+                    }
+                }
+                float m[6];
+#pragma unroll
+                for (int k = 0; k < 6; ++k) {
+                    const float2 hh = unpk(M[k]);
+                    m[k] = hh.x + hh.y;
+                    m[k] += __shfl_xor_sync(0xffffffffu, m[k], 1);
+                    m[k] += __shfl_xor_sync(0xffffffffu, m[k], 2);
+                }
+                if (valid) {
+                    // thread q issues moments q and, for q < 2, q + 4
+                    float *dst = reinterpret_cast<float *>(accC + 2 * (size_t)sid[sub + jg]);
+                    const float va = q == 0 ? m[0] : (q == 1 ? m[1] : (q == 2 ? m[2] : m[3]));
+                    if (va != 0.f) atomicAdd(dst + q, va);
+                    const float vb = q == 0 ? m[4] : m[5];
+                    if (q < 2 && vb != 0.f) atomicAdd(dst + 4 + q, vb);
+                }
+            }
             __syncthreads();
         }
     }
 }
 
 template <int AM>
-__global__ void __launch_bounds__(256, 4)
+__global__ void __launch_bounds__(128, 5)
 k_intensity_bwd(const uint2 *__restrict__ ranges, const uint32_t *__restrict__ vals, const CompRec *__restrict__ comp,
                 const ImgRec *__restrict__ img, const float4 *__restrict__ accI, const float *__restrict__ Tend,
                 const int32_t *__restrict__ last, const ViewDev *__restrict__ views, int V, float cut,
                 const StatusDev *st, float4 *__restrict__ accC, const TileSched sc) {
     if (st->code != SDGR_OK) return;
     __shared__ uint32_t sBL[256];
-    __shared__ float2 sBO[8];  // pixel block b's offset from the tile origin: (8 (b & 1), 4 (b >> 1))
     sBL[threadIdx.x] = block_list(threadIdx.x);
-    if (threadIdx.x < 8) sBO[threadIdx.x] = make_float2((float)(8 * (threadIdx.x & 1)), (float)(4 * (threadIdx.x >> 1)));
+    sBL[threadIdx.x + 128] = block_list(threadIdx.x + 128);
     __syncthreads();
     for_tiles(sc, st, [&](int tile) {
-        intensity_bwd_tile<AM>(tile, st, ranges, vals, comp, img, accI, Tend, last, views, V, cut, accC, sBL, sBO);
+        intensity_bwd_tile<AM>(tile, st, ranges, vals, comp, img, accI, Tend, last, views, V, cut, accC, sBL);
     });
 }
 
@@ -1296,11 +1380,11 @@ cudaError_t launch_intensity_bwd(const uint2 *ranges, const uint32_t *vals, cons
                                  const TileSched &sched, cudaStream_t s) {
     if (tiles <= 0) return cudaSuccess;
     if (alpha_mode)
-        k_intensity_bwd<1><<<raster_grid(tiles, sched), TILE_PIX, 0, s>>>(ranges, vals, comp, img, accI, Tend, last,
-                                                                          views, V, cut, st, accC, sched);
+        k_intensity_bwd<1><<<raster_grid(tiles, sched), TILE_PIX / 2, 0, s>>>(ranges, vals, comp, img, accI, Tend,
+                                                                              last, views, V, cut, st, accC, sched);
     else
-        k_intensity_bwd<0><<<raster_grid(tiles, sched), TILE_PIX, 0, s>>>(ranges, vals, comp, img, accI, Tend, last,
-                                                                          views, V, cut, st, accC, sched);
+        k_intensity_bwd<0><<<raster_grid(tiles, sched), TILE_PIX / 2, 0, s>>>(ranges, vals, comp, img, accI, Tend,
+                                                                              last, views, V, cut, st, accC, sched);
     note_launch();
     return cudaGetLastError();
 }
@@ -1332,7 +1416,7 @@ int raster_blocks_per_sm(int kernel, int nb) {
         case 6: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_splat_bwd<256>, TILE_PIX, 0); break;
         case 7: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_splat_bwd<512>, TILE_PIX, 0); break;
         case 8: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_splat_bwd<1024>, TILE_PIX, 0); break;
-        case 9: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_intensity_bwd<0>, TILE_PIX, 0); break;
+        case 9: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_intensity_bwd<0>, TILE_PIX / 2, 0); break;
         default: break;
     }
     if (e != cudaSuccess || n < 1) {

@@ -95,7 +95,7 @@ def test_stage_batch_options(L):
         opts = L.sdgr_stage_batch_options(name)
         assert opts and opts == L.sdgr_stage_batch_options(k)
         assert len(set(opts)) == len(opts)
-        assert all(nb % 256 == 0 and 256 <= nb <= 1024 for nb in opts)
+        assert all(nb % 128 == 0 and 128 <= nb <= 1024 for nb in opts)
     assert L.sdgr_stage_batch_options(1) == (512, 256)
     assert L.lib().sdgr_stage_batch_options(4, None, 0) == 0
     assert L.lib().sdgr_stage_batch_options(-1, None, 0) == 0
