@@ -1242,7 +1242,7 @@ intensity_bwd_tile(const int tile, const StatusDev *st, const uint2 *__restrict_
             // alpha_mode 0, fast path (no index bound, T always rebuilt by
             // division), as a two-stage pipeline: the part of a hit that does
             // not depend on T and B (records, exponents, alpha, 1 / (1 - alpha))
-            // is done one hit ahead of the recursion (-5 % of the kernel).  e is
+            // is done two hits ahead of the recursion (-5 % of the kernel).  e is
             // alpha itself (the exponent includes log2 o); outside the cutoff
             // alpha = 0 and rcp.approx(1) = 1 (the library's device self-check),
             // so T and B stay as they are.  The weight is dL/dalpha alpha =
@@ -1277,11 +1277,12 @@ intensity_bwd_tile(const int tile, const StatusDev *st, const uint2 *__restrict_
             if (__all_sync(0xffffffffu, !(first[0] | first[1]))) {
                 if constexpr (AM == 0) {
                     if (nh > 0) {
-                        Pre cur = pre(hl[0]);
+                        Pre cur = pre(hl[0]), nxt = pre(hl[min(1, nh - 1)]);
                         for (int i = 0; i < nh; ++i) {
-                            const Pre nxt = pre(hl[min(i + 1, nh - 1)]);
+                            const Pre nn = pre(hl[min(i + 2, nh - 1)]);
                             apply(cur);
                             cur = nxt;
+                            nxt = nn;
                         }
                     }
                 } else {
