@@ -253,18 +253,22 @@ sdgr_status sdgr_device_selfcheck(uint32_t *flags, void *stream);
 
 /* Diagnostic: the sustained per-SM rate of the instruction kinds the raster
  * kernels are built from, measured on the current device -- the
- * denominators of their arithmetic roofline.  Writes rates[0..4], each in
- * thread-instructions per SM per SM clock cycle (read from the SM's cycle
- * counter, so independent of the clock frequency): [0] fma.rn.f32,
- * [1] ex2.approx.ftz.f32, [2] rcp.approx.ftz.f32 (each followed by a
- * dependent fma, which is not counted), [3] a stream of one ex2 per seven fma
- * and [4] one rcp per eight fma (all instructions counted; 8 rates[0] /
- * rates[3] - 7 and 9 rates[0] / rates[4] - 8 are what one ex2 and one rcp
- * cost inside an FP32 stream, in fma issue slots).
+ * denominators of their arithmetic roofline.  Writes
+ * rates[0 .. SDGR_PIPE_RATE_KINDS - 1], each in thread-instructions per SM per
+ * SM clock cycle (read from the SM's cycle counter, so independent of the
+ * clock frequency): [0] fma.rn.f32, [1] ex2.approx.ftz.f32,
+ * [2] rcp.approx.ftz.f32 (each followed by a dependent fma, which is not
+ * counted), [3] a stream of one ex2 per seven fma and [4] one rcp per eight
+ * fma (all instructions counted; 8 rates[0] / rates[3] - 7 and
+ * 9 rates[0] / rates[4] - 8 are what one ex2 and one rcp cost inside an FP32
+ * stream, in fma issue slots), [5] fma.rn.f32x2 (two FMAs each),
+ * [6] fma.rn.f32 and lop3.b32 alternating, [7] fma.rn.f32x2 and lop3.b32
+ * alternating (all instructions counted).
  * scratch: caller-owned device memory of at least SDGR_PIPE_RATES_SCRATCH
  * bytes, 16-byte aligned.  Synchronous (waits for `stream`; a few ms).
  * Errors: SDGR_ERR_INVALID (NULL or misaligned arguments), SDGR_ERR_CUDA. */
 #define SDGR_PIPE_RATES_SCRATCH 8192
+#define SDGR_PIPE_RATE_KINDS 8
 sdgr_status sdgr_pipe_rates(void *scratch, double *rates, void *stream);
 sdgr_status sdgr_set_stage_batch(sdgr_ws *ws, int32_t kernel, int32_t records);
 

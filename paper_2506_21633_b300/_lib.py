@@ -276,15 +276,17 @@ def sdgr_device_selfcheck(flags_ptr, stream=None):
 
 
 PIPE_RATES_SCRATCH = 8192
-PIPE_RATE_KINDS = ("ffma", "ex2", "rcp", "ex2_in_ffma_stream", "rcp_in_ffma_stream")
+PIPE_RATE_KINDS = ("ffma", "ex2", "rcp", "ex2_in_ffma_stream", "rcp_in_ffma_stream", "ffma2",
+                   "ffma_and_lop3", "ffma2_and_lop3")
 
 
 def sdgr_pipe_rates(scratch_ptr, stream=None):
     """Measured per-SM rates (thread-instructions per SM cycle) of fma, ex2,
-    rcp, and of streams of one ex2 per seven fma and one rcp per eight fma;
-    synchronous.
+    rcp, of streams of one ex2 per seven fma and one rcp per eight fma, of
+    fma.f32x2 (two FMAs each) and of fma or fma.f32x2 alternating with an
+    integer lop3; synchronous.
     scratch_ptr: device memory of PIPE_RATES_SCRATCH bytes."""
-    out = (ctypes.c_double * 5)()
+    out = (ctypes.c_double * len(PIPE_RATE_KINDS))()
     _check("sdgr_pipe_rates", lib().sdgr_pipe_rates(ctypes.c_void_p(scratch_ptr), out, ctypes.c_void_p(stream)))
     return dict(zip(PIPE_RATE_KINDS, (float(x) for x in out)))
 

@@ -568,17 +568,17 @@ sdgr_status sdgr_pipe_rates(void *scratch, double *rates, void *stream) {
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     float *sink = static_cast<float *>(scratch);
     unsigned long long *cyc = reinterpret_cast<unsigned long long *>(static_cast<char *>(scratch) + 4096);
-    static const int iters[5] = {4096, 1024, 1024, 2048, 2048};
-    for (int op = 0; op < 5; ++op) {
+    static const int iters[SDGR_PIPE_RATE_KINDS] = {4096, 1024, 1024, 2048, 2048, 4096, 2048, 2048};
+    for (int op = 0; op < SDGR_PIPE_RATE_KINDS; ++op) {
         CK(cudaMemsetAsync(cyc, 0, sizeof(*cyc), s));
         int bps = 0;
         CK(launch_pipe_rate(op, iters[op], sink, cyc, &bps, sms, s));
         CK(cudaStreamSynchronize(s));
         unsigned long long c = 0;
         CK(cudaMemcpy(&c, cyc, sizeof(c), cudaMemcpyDeviceToHost));
-        // instructions counted per thread and iteration: 8, or 9 for the rcp
-        // stream (its rcp's fma included)
-        const double per_iter = op == 4 ? 9.0 : 8.0;
+        // instructions counted per thread and iteration: 8, 9 for the rcp
+        // stream (its rcp's fma included), 16 for the alternating streams
+        const double per_iter = op == 4 ? 9.0 : (op >= 6 ? 16.0 : 8.0);
         rates[op] = c ? (double)bps * 1024.0 * iters[op] * per_iter / (double)c : 0.0;
     }
     return SDGR_OK;

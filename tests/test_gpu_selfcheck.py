@@ -29,3 +29,10 @@ def test_pipe_rates_plausible():
     assert 4.0 <= r["ex2"] <= r["ffma"] / 2 and 4.0 <= r["rcp"] <= r["ffma"] / 2
     for k in ("ex2_in_ffma_stream", "rcp_in_ffma_stream"):
         assert 0.3 * r["ffma"] <= r[k] <= 1.02 * r["ffma"], (k, r)
+    # a packed instruction does two FMAs: the FMA rate stays at most the
+    # lanes' (two per instruction), the instruction rate about half of fma's
+    assert 0.3 * r["ffma"] <= r["ffma2"] and 2 * r["ffma2"] <= 1.02 * r["ffma"] + 2.0, r
+    # beside integer work, more FMAs per cycle go through packed than scalar
+    # (half of each alternating stream is FMA instructions: one FMA or two)
+    assert r["ffma_and_lop3"] <= 128.5 and r["ffma2_and_lop3"] <= 128.5, r
+    assert r["ffma2_and_lop3"] >= r["ffma_and_lop3"] / 2, r
