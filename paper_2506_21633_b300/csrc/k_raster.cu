@@ -1360,7 +1360,10 @@ intensity_bwd_tile(const int tile, const StatusDev *st, const uint2 *__restrict_
 }
 
 template <int AM>
-__global__ void __launch_bounds__(128, 5)
+// Four resident CTAs per SM (106 registers): faster than five at 94
+// registers (19.95-20.06 against 20.35 ms) and than three (23.0); the walk
+// pipelined three hits ahead instead of two was slower (20.5).
+__global__ void __launch_bounds__(128, 4)
 k_intensity_bwd(const uint2 *__restrict__ ranges, const uint32_t *__restrict__ vals, const CompRec *__restrict__ comp,
                 const ImgRec *__restrict__ img, const float4 *__restrict__ accI, const float *__restrict__ Tend,
                 const int32_t *__restrict__ last, const ViewDev *__restrict__ views, int V, float cut,
