@@ -47,6 +47,32 @@ __device__ __forceinline__ uint32_t probe_lop3(uint32_t a) {
 template <int OP>
 __global__ void __launch_bounds__(1024) k_pipe_rate(int iters, float *sink, unsigned long long *cycles) {
     float a[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) a[j] = 0.5f + 0.01f * (float)(threadIdx.x & 7) + 0.001f * (float)j;
+    __syncthreads();
+    const long long t0 = clock64();
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            if (OP == 0 || (OP >= 3 && j >= 1)) a[j] = probe_fma(a[j]);
+            else if (OP == 1 || OP == 3) a[j] = probe_ex2(a[j]);
+            else a[j] = probe_fma(probe_rcp(a[j]));
+        }
+    }
+    const long long t1 = clock64();
+    __syncthreads();
+    float s = 0.f;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) s += a[j];
+    if (s == -1.f) sink[threadIdx.x] = s;  // never true: keeps the chains alive
+    if (threadIdx.x == 0) atomicMax(cycles, (unsigned long long)(t1 - t0));
+}
+
+// The packed and mixed kinds (5..7) in a kernel of their own, so that the
+// code of the scalar kinds above stays as it was measured.
+template <int OP>
+__global__ void __launch_bounds__(1024) k_pipe_rate_pk(int iters, float *sink, unsigned long long *cycles) {
+    float a[8];
     uint64_t p[8];
     uint32_t g[8];
 #pragma unroll
@@ -68,15 +94,9 @@ __global__ void __launch_bounds__(1024) k_pipe_rate(int iters, float *sink, unsi
             } else if (OP == 6) {
                 a[j] = probe_fma(a[j]);
                 g[j] = probe_lop3(g[j]);
-            } else if (OP == 7) {
+            } else {
                 p[j] = probe_fma2(p[j], B2, C2);
                 g[j] = probe_lop3(g[j]);
-            } else if (OP == 0 || (OP >= 3 && j >= 1)) {
-                a[j] = probe_fma(a[j]);
-            } else if (OP == 1 || OP == 3) {
-                a[j] = probe_ex2(a[j]);
-            } else {
-                a[j] = probe_fma(probe_rcp(a[j]));
             }
         }
     }
@@ -97,7 +117,7 @@ cudaError_t launch_pipe_rate(int op, int iters, float *sink, unsigned long long 
                              int sms, cudaStream_t s) {
     static void (*const kern[8])(int, float *, unsigned long long *) = {
         k_pipe_rate<0>, k_pipe_rate<1>, k_pipe_rate<2>, k_pipe_rate<3>,
-        k_pipe_rate<4>, k_pipe_rate<5>, k_pipe_rate<6>, k_pipe_rate<7>};
+        k_pipe_rate<4>, k_pipe_rate_pk<5>, k_pipe_rate_pk<6>, k_pipe_rate_pk<7>};
     if (op < 0 || op > 7) return cudaErrorInvalidValue;
     int n = 0;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern[op], 1024, 0);
