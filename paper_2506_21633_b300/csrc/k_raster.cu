@@ -1310,6 +1310,13 @@ intensity_bwd_tile(const int tile, const StatusDev *st, const uint2 *__restrict_
                 const float2 uv = sU[sub + (valid ? jg : 0)];
                 const float *const wr = W + jg * AROW + 8 * q;
                 const int s0 = (q + slot) & 1;
+                // column offsets from the centre of the thread's column pairs
+                // in half-block column band 0 (the band's 4 cb is added per
+                // round), and of its rows in half-block row 0
+                const F2 DXB0 = pk((float)(2 * s0) - uv.x, (float)(2 * s0) - uv.x);
+                const F2 DXB1 = pk((float)(2 - 2 * s0) - uv.x, (float)(2 - 2 * s0) - uv.x);
+                const F2 DYB = pk((float)q - uv.y, (float)(q + 4) - uv.y);
+                const F2 TWO = pk(2.f, 2.f);
                 F2 M[6];
 #pragma unroll
                 for (int k = 0; k < 6; ++k) M[k] = pk(0.f, 0.f);
@@ -1318,21 +1325,20 @@ intensity_bwd_tile(const int tile, const StatusDev *st, const uint2 *__restrict_
                     const uint32_t hb = bl & 7u;
                     bl >>= 4;
                     const float *src = i < cnt ? wr + 32 * hb : zero32 + 8 * q;
-                    const float dy = small_u2f(8u * (hb >> 2) + (uint32_t)q) - uv.y;
-                    const F2 DY = pk(dy, dy + 4.f), DYY = mul2(DY, DY);
+                    const float ox = small_u2f(4u * (hb & 3u)), oy = small_u2f(8u * (hb >> 2));
+                    const F2 DY = add2(DYB, pk(oy, oy)), DYY = mul2(DY, DY);
+                    const F2 OX = pk(ox, ox);
 #pragma unroll
                     for (int ss = 0; ss < 2; ++ss) {
-                        const int s = s0 ^ ss;
-                        const float4 v4 = *reinterpret_cast<const float4 *>(src + 4 * s);
-                        const float dx = small_u2f(4u * (hb & 3u) + 2u * (uint32_t)s) - uv.x;
-                        const F2 DX = pk(dx, dx);
+                        const float4 v4 = *reinterpret_cast<const float4 *>(src + 4 * (s0 ^ ss));
+                        const F2 DX = add2(ss ? DXB1 : DXB0, OX);
                         const F2 A = pk(v4.x, v4.y), Bc = pk(v4.z, v4.w);
                         const F2 S = add2(A, Bc);
                         const F2 P1 = fma2(DX, S, Bc);
                         M[0] = add2(M[0], S);
                         M[1] = add2(M[1], P1);
                         M[2] = fma2(DY, S, M[2]);
-                        M[3] = fma2(mul2(DX, DX), S, fma2(add2(add2(DX, DX), ONE), Bc, M[3]));
+                        M[3] = fma2(mul2(DX, DX), S, fma2(fma2(TWO, DX, ONE), Bc, M[3]));
                         M[4] = fma2(DY, P1, M[4]);
                         M[5] = fma2(DYY, S, M[5]);
                     }
