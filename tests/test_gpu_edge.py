@@ -11,7 +11,11 @@ maximum, gradients 1e-3 per parameter group):
 - one-row and one-column images;
 - an empty scene inside a multi-scene batch;
 - a Gaussian with NaN parameters: the call completes, the status stays OK and
-  the other Gaussians' images and gradients are those without it."""
+  the other Gaussians' images and gradients are those without it;
+- image sizes that cut the tiles' 4 x 8 half-blocks (the intensity adjoint's
+  culling unit) and small Gaussians that reach only one half of a warp's
+  block, so that the two halves' hit lists differ in length and the shorter
+  one is padded."""
 import math
 
 import numpy as np
@@ -119,3 +123,12 @@ def test_nan_gaussian_stays_local():
     keep = np.delete(g_bad, 123, axis=0)
     assert np.all(np.isfinite(keep))
     assert_grads(keep, g_ok, tol=1e-4)
+
+
+def test_ragged_half_blocks_and_one_sided_hits():
+    # small Gaussians (a few pixels) scattered over a view whose sides are not
+    # multiples of 4, 8 or 16: most reach one 4-column half of a warp's block
+    params = sc.vehicle_box_scene(600, seed=13, extent=(1.2, 1.2, 0.4), log_s_mean=math.log(0.02),
+                                  center=(0, 0, 0))
+    views = [sc.make_view(25.0, 45.0, 0.03, 0.03, 37, 29), sc.make_view(160.0, 35.0, 0.03, 0.03, 45, 51)]
+    _parity(params, views, 14)
