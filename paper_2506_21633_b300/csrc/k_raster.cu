@@ -3,46 +3,45 @@
 // Section II-A-2, eq. I_i) and the layover splat on the imaging plane
 // (Section II-A-3, eq. S_{n,m}), and their adjoints (Section II-B-1/2).
 //
-// A CTA works on one 16x16 tile at a time.  The adjoints run eight warps,
-// one thread per pixel (ray); warp w covers the 8x4 pixel block with columns
-// 8 (w & 1) .. +7 and rows 4 (w >> 1) .. +3.  The intensity pass and the
-// splat run four warps; warp w covers the 8x8 block with columns 8 (w & 1) ..
-// +7 and rows 8 (w >> 1) .. +7, two rays (pixels) per lane, rows r and r + 4.
+// A CTA works on one 16x16 tile at a time.  The intensity pass, the splat
+// and the intensity adjoint run four warps; warp w covers the 8x8 block with
+// columns 8 (w & 1) .. +7 and rows 8 (w >> 1) .. +7, two rays (pixels) per
+// lane in one column.  The splat adjoint runs eight warps, Gaussian-parallel.
 // Which tiles a CTA takes follows the launch's schedule (for_tiles): one CTA
 // per tile, one per item of the longest-first work list, or resident CTAs
 // pulling items.  The tile's instance list is staged through shared memory in
 // batches (the staging batch of each kernel, a tuning knob).
 //
 // Culling: when a batch is staged, each Gaussian gets the set of the tile's
-// eight 8x4 pixel blocks that its K-ellipse reaches (found from the ellipse's
-// exact horizontal extent over each band of four rows; an 8x8 block is the
-// union of two; the splat tests the sixteen 4x4 sub-blocks instead).  A warp
-// walks only the Gaussians whose set holds its block: per 32 staged Gaussians
-// one ballot gives the warp its hit list (the splat: one per half-warp), which
-// it visits in list order (front to back for the intensity pass, back to
-// front for its adjoint).  The intensity pass
-// and its adjoint first write the list out as byte indices (one popc per lane)
-// and walk that: a shared load per hit instead of a bit scan and a mask
-// update (-7 % and -5 % of their time).
+// pixel blocks that its K-ellipse reaches (found from the ellipse's exact
+// horizontal extent over each band of four rows): eight 8x4 blocks (the
+// intensity pass takes an 8x8 block as the union of two, the splat adjoint
+// walks them), or sixteen 4x4 sub-blocks (the splat; the intensity adjoint
+// merges them into eight 4x8 half-blocks).  A warp, or in the splat and the
+// intensity adjoint each half of it (the left and right four columns of its
+// block), walks only the Gaussians whose set holds its block: per 32 staged
+// Gaussians one ballot gives it its hit list, which it visits in list order
+// (front to back for the intensity pass, back to front for its adjoint),
+// written out as byte indices (one popc per lane): a shared load per hit
+// instead of a bit scan and a mask update (-7 % and -5 % of the intensity
+// pass and its adjoint when they were introduced).
 //
 // Exponent: in a tile, a pixel's exponent of Gaussian i is a quadratic in the
 // pixel's tile-local coordinates (X, Y); the six coefficients are formed when
 // the batch is staged, so a pair costs five FMAs on per-thread constants
 // (Horner form, column part first: the two rays of a lane share a column, so
-// the intensity pass and the splat pay seven FMAs for two).
+// a lane pays seven FMAs for two).
 //
 // Sums over the tile's pixels per Gaussian.  The intensity pass needs only
 // sum_rays alpha T (non-negative, each term <= 1): one redux.sync per hit on
 // 2^-23 fixed point, kept in a register of one lane of the warp and added to
-// a 32-bit shared slot once per 32 staged Gaussians.  The intensity adjoint needs
-// six signed moments and uses a two-phase transpose: in phase 1 every pixel
-// writes its weight for each of its hit Gaussians into a 32 x 256 shared-
-// memory table; in phase 2 eight threads per Gaussian read the table's entries
-// of that Gaussian's hit blocks (one float4 per thread per block: four rows of
-// one column); the eight partial sums meet in shared memory, one thread per
-// moment adds them and issues its atomic.  Entries of
-// blocks that a Gaussian does not reach are never written and never read.  The
-// splat adjoint is Gaussian-parallel over the same hit blocks.
+// a 32-bit shared slot once per 32 staged Gaussians.  The intensity adjoint
+// needs six signed moments and uses a two-phase transpose: in phase 1 every
+// ray writes its weight for each of its hit Gaussians into a 32 x 256 shared-
+// memory table; in phase 2 four threads per Gaussian read the table's entries
+// of that Gaussian's half-blocks and sum them as packed pairs, then meet by
+// shuffles.  Entries of half-blocks that a Gaussian does not reach are never
+// read.  The splat adjoint is Gaussian-parallel over its hit blocks.
 #include <type_traits>
 
 #include "sdgr_internal.cuh"
