@@ -1185,44 +1185,39 @@ intensity_bwd_tile(const int tile, const StatusDev *st, const uint2 *__restrict_
                 const float q[2] = {poly_row_q(Q.x, cq, fY0), poly_row_q(Q.x, cq, fY1)};
                 float2 *const wp = reinterpret_cast<float2 *>(reinterpret_cast<char *>(W) + (int)(off * 64u) + wb);
                 const float cq0 = AM == 0 ? Q.z : cut;  // the folded cutoff (alpha_mode 0)
-                {
-                    float wv[2];
+                float wv[2];
 #pragma unroll
-                    for (int k = 0; k < 2; ++k) {
-                        const bool in = F ? q[k] >= cq0 : (q[k] >= cq0) & ((int)(off >> 4) < lim[k]);
-                        const float e = in ? ex2_approx(q[k]) : 0.f;
-                        // T in front of the pair: T behind it / (1 - alpha)
-                        const auto rebuild = [&](float om) {
-                            const float Td = T[k] * rcp_approx(om);
-                            if constexpr (F) {
-                                T[k] = Td;
-                            } else {
-                                T[k] = (in & !first[k]) ? Td : T[k];
-                                first[k] = first[k] & !in;
-                            }
-                        };
-                        if constexpr (AM == 0) {
-                            rebuild(__fsub_rn(1.f, e));
-                            const float ad = e * (Q.w - B[k]);
-                            B[k] += ad;
-                            wv[k] = T[k] * ad;
+                for (int k = 0; k < 2; ++k) {
+                    const bool in = F ? q[k] >= cq0 : (q[k] >= cq0) & ((int)(off >> 4) < lim[k]);
+                    const float e = in ? ex2_approx(q[k]) : 0.f;
+                    // T in front of the pair: T behind it / (1 - alpha)
+                    const auto rebuild = [&](float om) {
+                        const float Td = T[k] * rcp_approx(om);
+                        if constexpr (F) {
+                            T[k] = Td;
                         } else {
-                            const float alpha = alpha_of<AM>(Q.z, e);
-                            const float om = __fsub_rn(1.f, alpha);
-                            rebuild(om);
-                            const float d = Q.w - B[k];
-                            B[k] = fmaf(alpha, d, B[k]);
-                            // weight of the profile: d alpha / d G = tau (1 - alpha)
-                            wv[k] = T[k] * d * (e * om);
+                            T[k] = (in & !first[k]) ? Td : T[k];
+                            first[k] = first[k] & !in;
                         }
+                    };
+                    if constexpr (AM == 0) {
+                        rebuild(__fsub_rn(1.f, e));
+                        const float ad = e * (Q.w - B[k]);
+                        B[k] += ad;
+                        wv[k] = T[k] * ad;
+                    } else {
+                        const float alpha = alpha_of<AM>(Q.z, e);
+                        const float om = __fsub_rn(1.f, alpha);
+                        rebuild(om);
+                        const float d = Q.w - B[k];
+                        B[k] = fmaf(alpha, d, B[k]);
+                        // weight of the profile: d alpha / d G = tau (1 - alpha)
+                        wv[k] = T[k] * d * (e * om);
                     }
-                    *wp = make_float2(wv[0], wv[1]);
                 }
+                *wp = make_float2(wv[0], wv[1]);
             };
-            // fast path: no ray of the warp is a stopped one still behind its
-            // stopping pair (walking back to front) -- then the forward pass
-            // took every in-cutoff pair still ahead (no index bound), and T is
-            // always rebuilt by division
+            // the hit list walked one hit at a time (stopped rays, alpha_mode 1);
             // the next hit's list entry and records are loaded before this
             // hit's table store (which the compiler cannot move them past)
             const auto walk = [&](auto fast) {
@@ -1273,6 +1268,10 @@ intensity_bwd_tile(const int tile, const StatusDev *st, const uint2 *__restrict_
                 B[1] = b2.y;
                 *reinterpret_cast<float2 *>(reinterpret_cast<char *>(W) + (int)(c.off * 64u) + wb) = unpk(mul2(TT, AD));
             };
+            // fast path: no ray of the warp is a stopped one still behind its
+            // stopping pair (walking back to front) -- then the forward pass
+            // took every in-cutoff pair still ahead (no index bound), and T is
+            // always rebuilt by division
             if (__all_sync(0xffffffffu, !(first[0] | first[1]))) {
                 if constexpr (AM == 0) {
                     if (nh > 0) {
