@@ -9,7 +9,11 @@ batch with the default (persistent, longest-first) schedule.
   one view only equals the oracle's gradient of that view (the other 63 views
   must contribute nothing), 1e-3 per parameter group;
 - one 2048^2 view (the largest image size the server accepts) of a 40 000-
-  Gaussian scene, against the oracle."""
+  Gaussian scene, against the oracle;
+- the Beer-Lambert opacity (alpha_mode 1), whose intensity adjoint walks each
+  hit list one hit at a time: the full scene, eight of its views in one
+  batch, the gradient with a non-zero upstream image on one view against the
+  oracle's gradient of that view."""
 import math
 
 import numpy as np
@@ -76,3 +80,28 @@ def test_largest_image_2048():
     assert_images(ims, ref)
     refI = p64[:, 7] * A[0]
     assert np.abs(inten - refI).max() <= IMG_TOL * np.abs(refI).max()
+
+
+def test_config3_beer_lambert_gradient_one_view():
+    import torch
+    from paper_2506_21633_b300.render import Renderer
+    params, views = sc.config3()
+    views = views[:8]
+    p32, p64 = f32(params)
+    r = Renderer(alpha_mode=1)
+    r.prepare(torch.from_numpy(p32).cuda(), views)
+    ims = r.forward()
+    rng = np.random.default_rng(12)
+    k = 3
+    G = [np.zeros((v["NR"], v["NA"])) for v in views]
+    G[k] = rng.normal(size=G[k].shape)
+    g = torch.from_numpy(np.concatenate([x.ravel() for x in G]).astype(np.float32)).cuda()
+    grads = r.backward(g)
+    torch.cuda.synchronize()
+    cfg = oracle.cfg(alpha_mode=1)
+    ref_img = oracle.render(p64, [views[k]], cfg, culled=True)[0]
+    n0 = sum(v["NR"] * v["NA"] for v in views[:k])
+    img_k = ims[n0:n0 + views[k]["NR"] * views[k]["NA"]].cpu().numpy().astype(np.float64)
+    assert_images([img_k.reshape(views[k]["NR"], views[k]["NA"])], ref_img, tol=IMG_TOL)
+    ref = oracle.grad(p64, [views[k]], [G[k]], cfg, culled=True)[0]
+    assert_grads(grads.cpu().numpy().astype(np.float64), ref)
